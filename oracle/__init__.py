@@ -1,0 +1,224 @@
+"""ctypes wrapper of the FP64 CPU oracle (``pflbm_oracle.c``).
+
+TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU-baseline
+and reference legs of ``bench.py`` import this package. It shares no code with
+the CUDA library and imports nothing from it.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build_oracle
+
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_u16p = ctypes.POINTER(ctypes.c_uint16)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+FLUID, BOUNDARY, GHOST, INTERIOR = 0, 1, 2, 3
+
+
+class Wall(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("px", ctypes.c_double), ("py", ctypes.c_double),
+                ("nx_", ctypes.c_double), ("ny_", ctypes.c_double), ("r", ctypes.c_double),
+                ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
+                ("exclude", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = ctypes.CDLL(path)
+        L.or_lattice.argtypes = [_ip, _ip, _dp, _ip]
+        L.or_feq.argtypes = [ctypes.c_double] * 4 + [_dp]
+        L.or_geq.argtypes = [ctypes.c_double] * 3 + [_dp]
+        L.or_force.argtypes = [ctypes.c_double] * 7 + [_dp]
+        L.or_source.argtypes = [ctypes.c_double, _dp]
+        L.or_velocity_pressure.argtypes = [_dp] + [ctypes.c_double] * 5 + [_dp] * 3
+        L.or_stencil.argtypes = [_dp, _dp, _dp, _dp]
+        L.or_create.restype = ctypes.c_void_p
+        L.or_create.argtypes = ([ctypes.c_int] * 3 + [_u8p, ctypes.c_double, _dp]
+                                + [ctypes.c_double] * 7)
+        L.or_destroy.argtypes = [ctypes.c_void_p]
+        L.or_params.argtypes = [ctypes.c_void_p, _dp]
+        L.or_geometry.argtypes = [ctypes.c_void_p, _u8p, _u8p, _dp, _dp, _u16p, _u16p]
+        L.or_init_droplet.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 3
+        L.or_init_phi.argtypes = [ctypes.c_void_p, _dp]
+        L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+        L.or_get.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+        L.or_mass.restype = ctypes.c_double
+        L.or_mass.argtypes = [ctypes.c_void_p]
+        L.or_budget.argtypes = [ctypes.c_void_p, _dp]
+        L.or_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+        L.or_steps.restype = ctypes.c_long
+        L.or_steps.argtypes = [ctypes.c_void_p]
+        L.or_contact_angle.restype = ctypes.c_int
+        L.or_contact_angle.argtypes = [_dp, _u8p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(Wall), _dp, _dp]
+        L.or_circle_fit.restype = ctypes.c_int
+        L.or_circle_fit.argtypes = [_dp, _dp, ctypes.c_int, _dp]
+        _lib = L
+    return _lib
+
+
+def _p(a, t=_dp):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def lattice():
+    cx = np.zeros(9, np.int32)
+    cy = np.zeros(9, np.int32)
+    w = np.zeros(9)
+    opp = np.zeros(9, np.int32)
+    lib().or_lattice(_p(cx, _ip), _p(cy, _ip), _p(w), _p(opp, _ip))
+    return cx, cy, w, opp
+
+
+def feq(p, rho, ux, uy):
+    out = np.zeros(9)
+    lib().or_feq(p, rho, ux, uy, _p(out))
+    return out
+
+
+def geq(phi, mu, alpha):
+    out = np.zeros(9)
+    lib().or_geq(phi, mu, alpha, _p(out))
+    return out
+
+
+def force(tau_f, ux, uy, drx, dry, Fx, Fy):
+    out = np.zeros(9)
+    lib().or_force(tau_f, ux, uy, drx, dry, Fx, Fy, _p(out))
+    return out
+
+
+def source(s):
+    out = np.zeros(9)
+    lib().or_source(s, _p(out))
+    return out
+
+
+def velocity_pressure(f, rho, drx, dry, Fx, Fy):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    ux, uy, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().or_velocity_pressure(_p(f), rho, drx, dry, Fx, Fy,
+                               ctypes.byref(ux), ctypes.byref(uy), ctypes.byref(p))
+    return ux.value, uy.value, p.value
+
+
+def stencil(v3x3):
+    v = np.ascontiguousarray(v3x3, dtype=np.float64)
+    gx, gy, lap = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().or_stencil(_p(v), ctypes.byref(gx), ctypes.byref(gy), ctypes.byref(lap))
+    return gx.value, gy.value, lap.value
+
+
+def circle_fit(x, y):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    c = np.zeros(3)
+    rc = lib().or_circle_fit(_p(x), _p(y), len(x), _p(c))
+    if rc:
+        raise ValueError("circle fit failed")
+    return c
+
+
+def contact_angle(phi, cls, wall: dict):
+    """Fit the phi = 1/2 contour and return (theta_deg, circle, n_points)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    cls = np.ascontiguousarray(cls, dtype=np.uint8)
+    ny, nx = phi.shape
+    w = Wall(type=wall.get("type", 0), px=wall.get("px", 0.0), py=wall.get("py", 0.0),
+             nx_=wall.get("nx", 0.0), ny_=wall.get("ny", 1.0), r=wall.get("r", 0.0),
+             x_lo=wall.get("x_lo", -1e300), x_hi=wall.get("x_hi", 1e300),
+             exclude=wall.get("exclude", 0.0))
+    th = ctypes.c_double()
+    c = np.zeros(3)
+    n = lib().or_contact_angle(_p(phi), _p(cls, _u8p), nx, ny, ctypes.byref(w),
+                               ctypes.byref(th), _p(c))
+    return th.value, c, n
+
+
+class Oracle:
+    """Whole-domain FP64 solver (see pflbm_oracle.h)."""
+
+    def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
+                 rho_l=1.0, rho_g=0.1, tau_g=0.0, theta_field=None, wrap_y=False):
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        self.ny, self.nx = solid.shape
+        self.W = W
+        tf = None
+        if theta_field is not None:
+            tf = np.ascontiguousarray(theta_field, dtype=np.float64)
+            assert tf.shape == solid.shape
+        self._h = lib().or_create(self.nx, self.ny, int(wrap_y), _p(solid, _u8p),
+                                  float(theta_deg), _p(tf), sigma, W, M, tau_f,
+                                  rho_l, rho_g, tau_g)
+        if not self._h:
+            raise ValueError("or_create rejected the arguments")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_destroy(h)
+            self._h = None
+
+    @property
+    def params(self):
+        out = np.zeros(4)
+        lib().or_params(self._h, _p(out))
+        return dict(beta=out[0], kappa=out[1], tau_g=out[2], alpha=out[3])
+
+    def geometry(self):
+        shp = (self.ny, self.nx)
+        cls = np.zeros(shp, np.uint8)
+        zeta = np.zeros(shp, np.uint8)
+        eps = np.zeros(shp)
+        av = np.zeros(shp)
+        un = np.zeros(shp, np.uint16)
+        db = np.zeros(shp, np.uint16)
+        lib().or_geometry(self._h, _p(cls, _u8p), _p(zeta, _u8p), _p(eps), _p(av),
+                          _p(un, _u16p), _p(db, _u16p))
+        return dict(cls=cls, zeta=zeta, eps=eps, av=av, unknown=un, doubly=db)
+
+    def init_droplet(self, x0, y0, R):
+        lib().or_init_droplet(self._h, x0, y0, R)
+
+    def init_phi(self, phi):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        lib().or_init_phi(self._h, _p(phi))
+
+    def step(self, n=1):
+        lib().or_step(self._h, int(n))
+
+    def get(self):
+        shp = (self.ny, self.nx)
+        phi = np.zeros(shp)
+        u = np.zeros(shp + (2,))
+        p = np.zeros(shp)
+        lib().or_get(self._h, _p(phi), _p(u), _p(p))
+        return phi, u, p
+
+    def mass(self):
+        return lib().or_mass(self._h)
+
+    def budget(self):
+        out = np.zeros(4)
+        lib().or_budget(self._h, _p(out))
+        return out
+
+    def state(self):
+        N = self.nx * self.ny
+        f = np.zeros((9, self.ny, self.nx))
+        g = np.zeros((9, self.ny, self.nx))
+        sp = np.zeros((self.ny, self.nx))
+        lib().or_state(self._h, _p(f), _p(g), _p(sp))
+        return f, g, sp
+
+    @property
+    def steps(self):
+        return lib().or_steps(self._h)
