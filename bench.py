@@ -1,0 +1,287 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the fused time step.
+
+Workload (default): 4096 x 2048 lattice, flat bottom wall, 64 droplets of
+radius U[30, 60] at random x, per-node contact angle U[30, 150] deg (seed
+2312), rho_l / rho_g = 10, FP32 storage and arithmetic. One bench step is one
+time step of the whole lattice (all of: order parameter, ghost fill,
+stencils, chemical potential with the wetting term, forces, moments, both
+collisions, streaming with bounce-back). The state (1.2 GB) is far larger
+than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--precision fp32|fp64] [--workload many_flat|flat|incline|cylinder]
+
+Prints one JSON line (rank 0). Under torchrun each rank runs an independent
+replica of the workload (the solver does not shard: replicas only).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# algorithmic bytes per lattice update of the fused step: every f_i and g_i
+# read once and written once, the u.grad(phi) history read and written once,
+# one node byte (the wetting coefficient is read on wall layers only)
+BYTES_PER_LU = {"fp64": 2 * 9 * 2 * 8 + 2 * 8 + 1, "fp32": 2 * 9 * 2 * 4 + 2 * 4 + 1}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_case(name):
+    from paper_2312_00369_gb300 import workloads as wl
+    if name == "many_flat":
+        return wl.many_droplets_flat(nx=4096, ny=2048, n_drops=64, seed=2312)
+    if name == "flat":
+        return wl.droplet_on_flat_wall()
+    if name == "incline":
+        return wl.droplet_on_incline(theta=60.0)
+    if name == "cylinder":
+        return wl.droplet_on_cylinder()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(case, seconds=12.0):
+    """Time the FP64 CPU oracle (single thread, as it stands) on a bounded
+    512 x 256 sample of the workload; returns (MLUPS, description)."""
+    import oracle
+    from paper_2312_00369_gb300 import workloads as wl
+    if case.name == "many_flat":
+        sub = wl.many_droplets_flat(nx=512, ny=256, n_drops=8, seed=2312)
+    else:
+        sub = case
+    o = oracle.Oracle(sub.solid, theta_deg=sub.theta_deg, theta_field=sub.theta_field,
+                      **sub.physical())
+    for d in sub.droplets:
+        o.init_droplet(*d)
+    n = sub.nx * sub.ny
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(5)
+        steps += 5
+    dt = time.perf_counter() - t0
+    return n * steps / dt / 1e6, f"{sub.nx}x{sub.ny} lattice of the same generator, {steps} steps"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    case = make_case(args.workload)
+    mlups, desc = oracle_sample(case, seconds=max(3.0, min(20.0, 2.0 * args.steps)))
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": case.name, "nx": case.nx, "ny": case.ny},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default="many_flat")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2312_00369_gb300.pflbm import Solver, lib
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    case = make_case(args.workload)
+    N = case.nx * case.ny
+    stream = torch.cuda.Stream(device=local)
+    lib()
+
+    # ---------------- device-resident throughput ----------------
+    with torch.cuda.stream(stream):
+        s = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
+                   precision=args.precision, device=local, stream=stream, **case.physical())
+        for d in case.droplets:
+            s.init_droplet(*d)
+        s.step(args.warmup)
+        s.check()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(args.steps)          # K launches of the fused step kernel
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        s.check()
+    ms_t = torch.tensor([ms], device=f"cuda:{local}")
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_per_step = ms / args.steps
+    value = world * N * args.steps / (ms * 1e-3) / 1e6
+
+    peak, peak_kind = load_peaks()
+    bpl = BYTES_PER_LU[args.precision]
+    achieved = bpl * N / (ms_per_step * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            t = json.load(open(tfile))
+            key = f"{args.workload}:{args.precision}"
+            traffic = t.get(key)
+        except Exception:
+            traffic = None
+    s.close()
+
+    # ---------------- end to end through the C ABI with host buffers --------
+    e2e_steps = args.e2e_steps
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        s2 = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
+                    precision=args.precision, device=local, stream=stream, **case.physical())
+        for d in case.droplets:
+            s2.init_droplet(*d)
+        s2.step(e2e_steps)
+        phi, u, p = s2.get()
+        s2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+    h2d = case.solid.nbytes + (case.theta_field.nbytes if case.theta_field is not None else 0)
+    d2h = phi.nbytes + u.nbytes + p.nbytes
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups_cpu, desc = oracle_sample(case)
+        cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": case.name, "nx": case.nx, "ny": case.ny,
+                       "droplets": len(case.droplets), "precision": args.precision,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state 1.2 GB > L2, no flush needed" if case.name == "many_flat"
+                       else "small lattice: L2-resident"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "bytes_per_lu": bpl},
+            "hbm_roofline_mlups": peak * 1e9 / bpl / 1e6,
+            "e2e": {"value": world * N * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                    "steps_per_solve": e2e_steps,
+                    "includes": "create (mask upload, geometry), droplet init, steps, get"},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * pflbm.h -- C ABI of the GB300 (sm_103a) phase-field lattice Boltzmann
+ * library for droplets on wetting walls, after arXiv 2312.00369 (Ju, Guo,
+ * Yan, Sun): a Cahn-Hilliard phase lattice g_i and a pressure-based
+ * hydrodynamic lattice f_i on D2Q9, coupled by the surface-tension force
+ * mu grad(phi), with the liquid-solid surface energy folded into the chemical
+ * potential (Eq. chemical_potencial2) and a zero-normal-gradient ghost average
+ * on solid nodes (Sec. 2.2.2).
+ *
+ * General conventions
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3. Fields are row-major [ny][nx],
+ *    node (x, y) at index y*nx + x. x is periodic; rows 0, 1, ny-2 and ny-1
+ *    must be solid (so every node that collides has all 8 neighbours).
+ *  - Every call returns a status (PFLBM_OK = 0 or a negative code); no C++
+ *    exception crosses the ABI. pflbm_last_error() gives a text for the last
+ *    failure of the calling thread.
+ *  - Host arrays passed in are copied and never retained; output buffers are
+ *    owned by the caller. A handle is not thread-safe: use one handle from one
+ *    thread at a time. All device work of a handle runs on its stream.
+ *  - Parameters follow the paper's statement of the problem: contact angle
+ *    theta (Eq. b1), surface tension sigma and interface width W (Eq.
+ *    initialphi), mobility M (Eq. mobility), relaxation time tau_f with
+ *    nu = c_s^2 (tau_f - 1/2), densities rho_l (phi = 1) and rho_g (phi = 0)
+ *    (Sec. 2.1.1). Derived: beta = 12 sigma / W, kappa = 3 sigma W / 2 (the
+ *    unique pair for which the tanh profile of width W is the flat-interface
+ *    equilibrium and sigma = sqrt(2 kappa beta)/6), tau_g = 1 unless given,
+ *    alpha = M / (c_s^2 (tau_g - 1/2)).
+ */
+#ifndef PFLBM_H
+#define PFLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pflbm pflbm_t; /* opaque, owned by the library */
+
+enum pflbm_status {
+    PFLBM_OK = 0,
+    PFLBM_EINVAL = -1,   /* invalid argument or handle                       */
+    PFLBM_ENOMEM = -2,   /* device allocation failed                         */
+    PFLBM_EBADMASK = -3, /* rows 0, 1, ny-2, ny-1 of the mask are not solid  */
+    PFLBM_ENUMERIC = -4, /* NaN or |u| >= 0.3 seen on the device             */
+    PFLBM_ETIMEOUT = -5, /* a bounded device wait gave up                    */
+    PFLBM_ECUDA = -6     /* a CUDA runtime call failed                       */
+};
+
+/* Storage precision of the populations. Collision and stencils run in FP64
+ * for PFLBM_FP64 and in FP32 otherwise; the 16-bit modes store f_i and
+ * g_i (i != 0) as deviations from w_i times an equilibrium reference. */
+enum pflbm_precision { PFLBM_FP64 = 0, PFLBM_FP32 = 1, PFLBM_BF16 = 2, PFLBM_FP16 = 3 };
+
+/* Node classes (Sec. 2.2.2-2.2.3): fluid (zeta = 1, epsilon = 1); boundary =
+ * solid with a non-solid 8-neighbour (zeta = 1, epsilon = 0: collides and
+ * streams, bounce-back); ghost = other solid with a zeta = 1 neighbour
+ * (zeta = 0, phi = zeta-weighted neighbour mean); interior = other solid. */
+enum pflbm_node_class { PFLBM_FLUID = 0, PFLBM_BOUNDARY = 1, PFLBM_GHOST = 2, PFLBM_INTERIOR = 3 };
+
+typedef struct {
+    int nx, ny;
+    const uint8_t* solid_mask;     /* [ny][nx], 1 = solid; copied             */
+    double theta_deg;              /* uniform contact angle (degrees)         */
+    const float* theta_field_deg;  /* optional [ny][nx] angle field; copied   */
+    double sigma, W, M, tau_f, rho_l, rho_g;
+    double tau_g;                  /* <= 0: 1.0                               */
+    int precision;                 /* enum pflbm_precision                    */
+    int device;                    /* CUDA ordinal; < 0: the current device   */
+    void* stream;                  /* cudaStream_t; NULL: a stream created and
+                                      owned by the handle                     */
+    /* Optional device allocator (e.g. a framework's caching allocator).
+     * Both NULL: cudaMalloc / cudaFree. alloc returns NULL on failure. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* ctx);
+    void* alloc_ctx;
+} pflbm_params_t;
+
+/* Flat, inclined or circular wall for the contact-angle fit. type 0: the
+ * straight wall through (px, py) with unit normal (nx, ny) pointing into the
+ * fluid; type 1: a circular solid of centre (px, py) and radius r. Only the
+ * phi = 1/2 crossings between fluid nodes with x_lo <= x < x_hi and farther
+ * than `exclude` from the wall are fitted. */
+typedef struct {
+    int type;
+    double px, py, nx, ny, r;
+    double x_lo, x_hi;
+    double exclude;
+} pflbm_wall_t;
+
+/* Fill p with defaults: theta 90, sigma 0.01, W 4, M 0.1, tau_f 0.8,
+ * rho_l 1, rho_g 0.1, tau_g 1, FP32, current device, own stream. */
+void pflbm_params_default(pflbm_params_t* p);
+
+/* Create a solver from the problem statement of Sec. 3 (lattice, solid mask,
+ * theta, sigma, W, M, tau_f, rho_l, rho_g), FP32 storage. Classifies the
+ * nodes and computes a_v = |grad epsilon| (Eq. avvv) on the device.
+ * Errors: EINVAL (sizes, parameters: W > 0, M > 0, tau_f > 1/2, densities
+ * > 0, sigma >= 0), EBADMASK, ENOMEM, ECUDA. *out is NULL on failure. */
+int pflbm_create(pflbm_t** out, int nx, int ny, const uint8_t* solid_mask, double theta_deg,
+                 double sigma, double W, double M, double tau_f, double rho_l, double rho_g);
+/* Same with every option (precision, tau_g, angle field, device, stream,
+ * allocator). */
+int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* p);
+/* Release every device buffer of the handle (NULL is ignored). */
+void pflbm_destroy(pflbm_t* h);
+
+/* Replace the contact-angle field (degrees, [ny][nx], copied). Takes effect
+ * from the next step. */
+int pflbm_set_theta_field(pflbm_t* h, const float* theta_deg);
+
+/* Initial droplet of Eq. initialphi, phi = 1/2 + 1/2 tanh(2 (R - r) / W)
+ * with r the x-periodic distance to (x0, y0). The first call after create or
+ * after a step replaces phi; further calls keep the pointwise maximum. Sets
+ * u = 0, p = 0 (f_i = 0) and g_i = g_i^eq(phi, mu) (Eq. H_i). Asynchronous. */
+int pflbm_init_droplet(pflbm_t* h, double x0, double y0, double R);
+/* General initial field phi [ny][nx] (host, copied; values on zeta = 0 nodes
+ * are ignored); same initial populations as above. */
+int pflbm_init_phi(pflbm_t* h, const double* phi);
+
+/* n time steps (Eqs. BGK-NS, BGK with the chemical potential of Eq.
+ * chemical_potencial2, streaming and modified bounce-back, Sec. 2.2.2).
+ * Asynchronous on the handle's stream; returns ENUMERIC if an earlier step
+ * reported a NaN or |u| >= 0.3 (the flag is read back without blocking). */
+int pflbm_step(pflbm_t* h, int64_t n);
+
+/* Macroscopic fields of the current state (synchronous). phi [ny][nx] (ghost
+ * nodes: the ghost average; interior nodes: 0), u [ny][nx][2] (ux, uy),
+ * p [ny][nx] (u = p = 0 on zeta = 0 nodes). Any pointer may be NULL.
+ * Caller-owned host buffers. */
+int pflbm_get(pflbm_t* h, double* phi, double* u, double* p);
+/* Same into caller-owned DEVICE buffers (no host copy, asynchronous). */
+int pflbm_get_device(pflbm_t* h, double* phi, double* u, double* p);
+
+/* FP64 sum of phi = sum_i g_i over zeta = 1 nodes (synchronous). */
+int pflbm_mass(pflbm_t* h, double* out);
+
+/* Contact angle (degrees) from a circle fitted to the phi = 1/2 crossings,
+ * measured through the liquid against the given wall (synchronous; FP64 on
+ * the device). circle (may be NULL) receives {centre x, centre y, R};
+ * npoints (may be NULL) the number of fitted points. EINVAL if fewer than
+ * 3 points. */
+int pflbm_contact_angle(pflbm_t* h, const pflbm_wall_t* wall, double* theta_deg, double* circle,
+                        int* npoints);
+
+/* Geometry read-back (synchronous): node class, unknown-link mask (bit i set
+ * when zeta(x - c_i) = 0 at a zeta = 1 node), doubly-unknown mask (also
+ * zeta(x + c_i) = 0), a_v. Any pointer may be NULL. Bit order: the library's
+ * velocity order from pflbm_lattice. */
+int pflbm_geometry(pflbm_t* h, uint8_t* cls, uint16_t* unknown, uint16_t* doubly, double* av);
+/* The library's D2Q9 velocity order (cx[i], cy[i], i = 0..8). */
+void pflbm_lattice(int cx[9], int cy[9]);
+
+/* Synchronise the handle's stream and report ENUMERIC / ECUDA if any. */
+int pflbm_check(pflbm_t* h);
+/* Steps taken since the last initialisation. */
+int64_t pflbm_steps(const pflbm_t* h);
+
+/* Device bytes a handle of this size and precision allocates. */
+size_t pflbm_footprint_bytes(int nx, int ny, int precision);
+
+/* Checkpoint: *len in: capacity of buf, out: bytes needed/written. buf may be
+ * NULL to query the size. The blob holds the populations, the u.grad(phi)
+ * history, the step count and the parameters; load requires a handle of the
+ * same size and precision. Both synchronous. */
+int pflbm_save(pflbm_t* h, void* buf, size_t* len);
+int pflbm_load(pflbm_t* h, const void* buf, size_t len);
+
+/* Text of the calling thread's last error ("" if none). */
+const char* pflbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFLBM_H */

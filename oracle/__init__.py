@@ -48,6 +48,10 @@ def lib():
         L.or_geometry.argtypes = [ctypes.c_void_p, _u8p, _u8p, _dp, _dp, _u16p, _u16p]
         L.or_init_droplet.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 3
         L.or_init_phi.argtypes = [ctypes.c_void_p, _dp]
+        L.or_droplet_phi.restype = ctypes.c_double
+        L.or_droplet_phi.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int]
+        L.or_droplet_phi_points.argtypes = ([_dp, _dp, ctypes.c_long] + [ctypes.c_double] * 4
+                                            + [ctypes.c_int, ctypes.c_int, _dp])
         L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
         L.or_get.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
         L.or_mass.restype = ctypes.c_double
@@ -115,6 +119,21 @@ def stencil(v3x3):
     gx, gy, lap = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     lib().or_stencil(_p(v), ctypes.byref(gx), ctypes.byref(gy), ctypes.byref(lap))
     return gx.value, gy.value, lap.value
+
+
+def droplet_phi(x, y, x0, y0, R, W, nx_period=0, out=None):
+    """Eq. initialphi at points (x, y) (arrays of one shape), x-periodic with
+    nx_period; with ``out`` given, the pointwise maximum with ``out``."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    assert x.shape == y.shape
+    combine = out is not None
+    if out is None:
+        out = np.empty(x.shape)
+    assert out.flags["C_CONTIGUOUS"] and out.dtype == np.float64
+    lib().or_droplet_phi_points(_p(x), _p(y), x.size, x0, y0, R, W, int(nx_period),
+                                int(combine), _p(out))
+    return out
 
 
 def circle_fit(x, y):

@@ -545,6 +545,23 @@ void or_init_droplet(or_solver* s, double x0, double y0, double R)
     init_populations(s);
 }
 
+double or_droplet_phi(double x, double y, double x0, double y0, double R, double W, int nx_period)
+{
+    double dx = periodic_delta(x - x0, nx_period, nx_period > 0);
+    double dy = y - y0;
+    double r = sqrt(dx * dx + dy * dy);
+    return 0.5 + 0.5 * tanh(2.0 * (R - r) / W);
+}
+
+void or_droplet_phi_points(const double* x, const double* y, long n, double x0, double y0,
+                           double R, double W, int nx_period, int combine, double* out)
+{
+    for (long k = 0; k < n; ++k) {
+        double v = or_droplet_phi(x[k], y[k], x0, y0, R, W, nx_period);
+        if (!combine || v > out[k]) out[k] = v;
+    }
+}
+
 void or_init_phi(or_solver* s, const double* phi)
 {
     for (long k = 0; k < s->N; ++k) s->phi[k] = s->zeta[k] ? phi[k] : 0.0;

@@ -74,6 +74,12 @@ void or_geometry(const or_solver* s, uint8_t* cls, uint8_t* zeta, double* eps,
 /* Initial droplet, Eq. initialphi. The first call after create or after a step
  * replaces phi; later calls keep the pointwise maximum. */
 void or_init_droplet(or_solver* s, double x0, double y0, double R);
+/* Eq. initialphi at one point, with the x-periodic distance of period
+ * nx_period (0: no wrap). */
+double or_droplet_phi(double x, double y, double x0, double y0, double R, double W, int nx_period);
+/* The same at n points; out[k] = max(out[k], phi) when combine != 0. */
+void or_droplet_phi_points(const double* x, const double* y, long n, double x0, double y0,
+                           double R, double W, int nx_period, int combine, double* out);
 /* General initial field (values on zeta=1 nodes are used). */
 void or_init_phi(or_solver* s, const double* phi);
 /* n time steps. */

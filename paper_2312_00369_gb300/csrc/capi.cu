@@ -1,0 +1,591 @@
+// capi.cu -- the extern "C" entry points of libpflbm.so (declared and
+// documented in include/pflbm.h): argument checks, device memory, streams,
+// error codes. Every computation runs in the kernels of geometry.cu, step.cu
+// and diag.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pflbm_internal.cuh"
+
+namespace pfk {
+size_t mass_scratch_doubles();
+}
+
+using namespace pfk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(PFLBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int dalloc(pflbm_t* h, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (h->alloc_fn) {
+        *p = h->alloc_fn(bytes, h->alloc_ctx);
+        if (!*p) return fail(PFLBM_ENOMEM, "allocator callback returned NULL");
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return fail(PFLBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    h->bytes_allocated += bytes;
+    return PFLBM_OK;
+}
+
+void dfree(pflbm_t* h, void* p, size_t bytes)
+{
+    if (!p) return;
+    if (h->free_fn)
+        h->free_fn(p, bytes, h->alloc_ctx);
+    else
+        cudaFree(p);
+}
+
+int pitch_of(int nx) { return (nx + 63) / 64 * 64; }
+
+struct Sizes {
+    size_t N, pop, sprev, wet, red, pts;
+    int pts_cap;
+};
+
+Sizes sizes_of(int nx, int ny, int precision)
+{
+    Sizes s{};
+    int pitch = pitch_of(nx);
+    s.N = (size_t)ny * pitch;
+    s.pop = pop_bytes(ny, pitch, precision);
+    size_t cs = precision == PFLBM_FP64 ? 8 : 4;
+    s.sprev = s.N * cs;
+    s.wet = s.N * cs;
+    s.red = mass_scratch_doubles() * sizeof(double);
+    long long cap = 2LL * nx * ny;
+    if (cap > (1 << 22)) cap = 1 << 22;
+    s.pts_cap = (int)cap;
+    s.pts = (size_t)s.pts_cap * 2 * sizeof(double);
+    return s;
+}
+
+bool valid_params(const pflbm_params_t* p, std::string& why)
+{
+    if (p->nx < 3 || p->ny < 5) { why = "nx must be >= 3 and ny >= 5"; return false; }
+    if ((long long)p->nx * p->ny > (1LL << 31)) { why = "lattice too large"; return false; }
+    if (!p->solid_mask) { why = "solid_mask is NULL"; return false; }
+    if (!(p->W > 0) || !(p->M > 0) || !(p->tau_f > 0.5) || !(p->rho_l > 0) || !(p->rho_g > 0) ||
+        !(p->sigma >= 0) || !std::isfinite(p->theta_deg)) {
+        why = "need W > 0, M > 0, tau_f > 1/2, rho_l > 0, rho_g > 0, sigma >= 0, finite theta";
+        return false;
+    }
+    if (p->tau_g > 0 && !(p->tau_g > 0.5)) { why = "tau_g must be > 1/2"; return false; }
+    if (p->precision < PFLBM_FP64 || p->precision > PFLBM_FP32) {
+        why = "precision not supported by this build";
+        return false;
+    }
+    if ((p->alloc == nullptr) != (p->free == nullptr)) { why = "alloc and free must be given together"; return false; }
+    return true;
+}
+
+void release(pflbm_t* h)
+{
+    if (!h) return;
+    Sizes s = sizes_of(h->nx, h->ny, h->precision);
+    DeviceGuard g(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    dfree(h, h->cls, s.N);
+    dfree(h, h->solid, s.N);
+    dfree(h, h->theta, s.N * sizeof(float));
+    dfree(h, h->wet, s.wet);
+    dfree(h, h->av, s.N * sizeof(double));
+    dfree(h, h->pop[0], s.pop);
+    dfree(h, h->pop[1], s.pop);
+    dfree(h, h->sprev, s.sprev);
+    dfree(h, h->phi0, s.N * sizeof(double));
+    dfree(h, h->mu0, s.N * sizeof(double));
+    dfree(h, h->red, s.red);
+    dfree(h, h->pts, s.pts);
+    dfree(h, h->out, h->out_bytes);
+    dfree(h, h->dstatus, sizeof(int) * 4);
+    if (h->hstatus) cudaFreeHost(h->hstatus);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int check_handle(const pflbm_t* h)
+{
+    if (!h) return fail(PFLBM_EINVAL, "NULL handle");
+    return PFLBM_OK;
+}
+
+int read_status(pflbm_t* h)
+{
+    if (h->hstatus && h->hstatus[0] != 0) {
+        return fail(PFLBM_ENUMERIC, "NaN or |u| >= 0.3 detected on the device");
+    }
+    return PFLBM_OK;
+}
+
+int post_status_copy(pflbm_t* h)
+{
+    CK(cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    return PFLBM_OK;
+}
+
+int ensure_out(pflbm_t* h)
+{
+    if (h->out) return PFLBM_OK;
+    size_t bytes = (size_t)h->nx * h->ny * 4 * sizeof(double);
+    void* p = nullptr;
+    int rc = dalloc(h, &p, bytes);
+    if (rc) return rc;
+    h->out = (double*)p;
+    h->out_bytes = bytes;
+    return PFLBM_OK;
+}
+
+}  // namespace
+
+namespace pfk {
+size_t elem_size(int precision)
+{
+    switch (precision) {
+        case PFLBM_FP64: return 8;
+        case PFLBM_FP32: return 4;
+        default: return 2;
+    }
+}
+size_t pop_bytes(int ny, int pitch, int precision) { return (size_t)18 * ny * pitch * elem_size(precision); }
+}  // namespace pfk
+
+extern "C" {
+
+void pflbm_params_default(pflbm_params_t* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->theta_deg = 90.0;
+    p->sigma = 0.01;
+    p->W = 4.0;
+    p->M = 0.1;
+    p->tau_f = 0.8;
+    p->rho_l = 1.0;
+    p->rho_g = 0.1;
+    p->tau_g = 1.0;
+    p->precision = PFLBM_FP32;
+    p->device = -1;
+}
+
+void pflbm_lattice(int cxo[9], int cyo[9])
+{
+    for (int i = 0; i < 9; ++i) {
+        if (cxo) cxo[i] = cx(i);
+        if (cyo) cyo[i] = cy(i);
+    }
+}
+
+const char* pflbm_last_error(void) { return g_last_error.c_str(); }
+
+size_t pflbm_footprint_bytes(int nx, int ny, int precision)
+{
+    if (nx < 1 || ny < 1) return 0;
+    Sizes s = sizes_of(nx, ny, precision);
+    return 2 * s.pop + s.sprev + s.wet + s.N * (1 + 1 + 8 + 8 + 8) + s.red + s.pts + 16 +
+           (size_t)nx * ny * 4 * sizeof(double);
+}
+
+int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
+{
+    if (!out || !prm) return fail(PFLBM_EINVAL, "NULL argument");
+    *out = nullptr;
+    std::string why;
+    if (!valid_params(prm, why)) return fail(PFLBM_EINVAL, why);
+    const int nx = prm->nx, ny = prm->ny;
+    for (int x = 0; x < nx; ++x) {
+        if (!prm->solid_mask[x] || !prm->solid_mask[nx + x] || !prm->solid_mask[(size_t)(ny - 2) * nx + x] ||
+            !prm->solid_mask[(size_t)(ny - 1) * nx + x])
+            return fail(PFLBM_EBADMASK, "rows 0, 1, ny-2 and ny-1 of the solid mask must be solid");
+    }
+    if (prm->theta_field_deg) {
+        for (size_t k = 0; k < (size_t)nx * ny; ++k)
+            if (!std::isfinite(prm->theta_field_deg[k])) return fail(PFLBM_EINVAL, "theta field has a non-finite value");
+    }
+    pflbm_t* h = new (std::nothrow) pflbm();
+    if (!h) return fail(PFLBM_ENOMEM, "host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->pitch = pitch_of(nx);
+    h->precision = prm->precision;
+    h->alloc_fn = prm->alloc;
+    h->free_fn = prm->free;
+    h->alloc_ctx = prm->alloc_ctx;
+    h->theta_uniform = prm->theta_deg;
+    int dev = prm->device;
+    if (dev < 0) {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+    }
+    h->device = dev;
+    DeviceGuard guard(dev);
+    // derived parameters (Eqs. b1, initialphi, mobility)
+    Params& q = h->prm;
+    q.sigma = prm->sigma;
+    q.W = prm->W;
+    q.M = prm->M;
+    q.beta = 12.0 * prm->sigma / prm->W;
+    q.kappa = 1.5 * prm->sigma * prm->W;
+    q.tau_f = prm->tau_f;
+    q.tau_g = prm->tau_g > 0 ? prm->tau_g : 1.0;
+    q.alpha = prm->M / ((1.0 / 3.0) * (q.tau_g - 0.5));
+    q.rho_l = prm->rho_l;
+    q.rho_g = prm->rho_g;
+
+    if (prm->stream) {
+        h->stream = (cudaStream_t)prm->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaStreamCreate"); }
+        h->own_stream = true;
+    }
+    Sizes s = sizes_of(nx, ny, h->precision);
+    int rc = PFLBM_OK;
+    void* p;
+#define ALLOC(field, bytes)                                   \
+    do {                                                      \
+        rc = dalloc(h, &p, (bytes));                          \
+        if (rc) { release(h); return rc; }                    \
+        h->field = (decltype(h->field))p;                     \
+    } while (0)
+    ALLOC(cls, s.N);
+    ALLOC(solid, s.N);
+    ALLOC(wet, s.wet);
+    ALLOC(av, s.N * sizeof(double));
+    ALLOC(pop[0], s.pop);
+    ALLOC(pop[1], s.pop);
+    ALLOC(sprev, s.sprev);
+    ALLOC(phi0, s.N * sizeof(double));
+    ALLOC(mu0, s.N * sizeof(double));
+    ALLOC(red, s.red);
+    ALLOC(pts, s.pts);
+    ALLOC(dstatus, sizeof(int) * 4);
+    if (prm->theta_field_deg) ALLOC(theta, s.N * sizeof(float));
+#undef ALLOC
+    h->pts_cap = s.pts_cap;
+    if (cudaMallocHost((void**)&h->hstatus, sizeof(int) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        h->hstatus = nullptr;
+        release(h);
+        return fail(PFLBM_ENOMEM, "cudaMallocHost failed");
+    }
+    h->hstatus[0] = 0;
+#define CKR(call)                                                 \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) { int r_ = cuda_fail(e_, #call); release(h); return r_; } \
+    } while (0)
+    CKR(cudaMemsetAsync(h->pop[0], 0, s.pop, h->stream));
+    CKR(cudaMemsetAsync(h->pop[1], 0, s.pop, h->stream));
+    CKR(cudaMemsetAsync(h->sprev, 0, s.sprev, h->stream));
+    CKR(cudaMemsetAsync(h->phi0, 0, s.N * sizeof(double), h->stream));
+    CKR(cudaMemsetAsync(h->solid, 1, s.N, h->stream));
+    CKR(cudaMemsetAsync(h->dstatus, 0, sizeof(int) * 4, h->stream));
+    CKR(cudaMemcpy2DAsync(h->solid, h->pitch, prm->solid_mask, nx, nx, ny, cudaMemcpyHostToDevice, h->stream));
+    if (prm->theta_field_deg)
+        CKR(cudaMemcpy2DAsync(h->theta, h->pitch * sizeof(float), prm->theta_field_deg, nx * sizeof(float),
+                              nx * sizeof(float), ny, cudaMemcpyHostToDevice, h->stream));
+    CKR(launch_classify(h));
+    CKR(launch_wet(h));
+    CKR(cudaStreamSynchronize(h->stream));
+#undef CKR
+    *out = h;
+    return PFLBM_OK;
+}
+
+int pflbm_create(pflbm_t** out, int nx, int ny, const uint8_t* solid_mask, double theta_deg, double sigma,
+                 double W, double M, double tau_f, double rho_l, double rho_g)
+{
+    pflbm_params_t p;
+    pflbm_params_default(&p);
+    p.nx = nx;
+    p.ny = ny;
+    p.solid_mask = solid_mask;
+    p.theta_deg = theta_deg;
+    p.sigma = sigma;
+    p.W = W;
+    p.M = M;
+    p.tau_f = tau_f;
+    p.rho_l = rho_l;
+    p.rho_g = rho_g;
+    return pflbm_create_ex(out, &p);
+}
+
+void pflbm_destroy(pflbm_t* h) { release(h); }
+
+int pflbm_set_theta_field(pflbm_t* h, const float* theta_deg)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!theta_deg) return fail(PFLBM_EINVAL, "NULL theta field");
+    for (size_t k = 0; k < (size_t)h->nx * h->ny; ++k)
+        if (!std::isfinite(theta_deg[k])) return fail(PFLBM_EINVAL, "theta field has a non-finite value");
+    DeviceGuard g(h->device);
+    if (!h->theta) {
+        void* p;
+        if (int rc = dalloc(h, &p, (size_t)h->ny * h->pitch * sizeof(float))) return rc;
+        h->theta = (float*)p;
+    }
+    CK(cudaMemcpy2DAsync(h->theta, h->pitch * sizeof(float), theta_deg, h->nx * sizeof(float),
+                         h->nx * sizeof(float), h->ny, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_wet(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return PFLBM_OK;
+}
+
+int pflbm_init_droplet(pflbm_t* h, double x0, double y0, double R)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(R)) return fail(PFLBM_EINVAL, "non-finite droplet");
+    DeviceGuard g(h->device);
+    CK(launch_init_phi_droplet(h, x0, y0, R, h->replace_phi ? 1 : 0));
+    h->replace_phi = false;
+    CK(launch_init_populations(h));
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    if (h->hstatus) h->hstatus[0] = 0;
+    h->steps = 0;
+    return PFLBM_OK;
+}
+
+int pflbm_init_phi(pflbm_t* h, const double* phi)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!phi) return fail(PFLBM_EINVAL, "NULL phi");
+    DeviceGuard g(h->device);
+    CK(cudaMemcpy2DAsync(h->phi0, h->pitch * sizeof(double), phi, h->nx * sizeof(double), h->nx * sizeof(double),
+                         h->ny, cudaMemcpyHostToDevice, h->stream));
+    h->replace_phi = false;
+    CK(launch_init_populations(h));
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));   // phi is a caller buffer: done with it on return
+    if (h->hstatus) h->hstatus[0] = 0;
+    h->steps = 0;
+    return PFLBM_OK;
+}
+
+int pflbm_step(pflbm_t* h, int64_t n)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (n < 0) return fail(PFLBM_EINVAL, "negative step count");
+    if (int rc = read_status(h)) return rc;
+    DeviceGuard g(h->device);
+    for (int64_t t = 0; t < n; ++t) {
+        CK(launch_step(h));
+        h->steps += 1;
+    }
+    if (n > 0) {
+        h->replace_phi = true;
+        if (int rc = post_status_copy(h)) return rc;
+    }
+    return PFLBM_OK;
+}
+
+int pflbm_get_device(pflbm_t* h, double* phi, double* u, double* p)
+{
+    if (int rc = check_handle(h)) return rc;
+    DeviceGuard g(h->device);
+    CK(launch_macro(h, phi, u, p));
+    return PFLBM_OK;
+}
+
+int pflbm_get(pflbm_t* h, double* phi, double* u, double* p)
+{
+    if (int rc = check_handle(h)) return rc;
+    DeviceGuard g(h->device);
+    if (int rc = ensure_out(h)) return rc;
+    size_t N = (size_t)h->nx * h->ny;
+    double* dphi = h->out;
+    double* du = h->out + N;
+    double* dp = h->out + 3 * N;
+    CK(launch_macro(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr));
+    if (phi) CK(cudaMemcpyAsync(phi, dphi, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK(cudaMemcpyAsync(u, du, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (p) CK(cudaMemcpyAsync(p, dp, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
+int pflbm_mass(pflbm_t* h, double* out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(PFLBM_EINVAL, "NULL out");
+    DeviceGuard g(h->device);
+    double* d = h->red + mass_scratch_doubles() - 8;
+    CK(launch_mass(h, d));
+    CK(cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
+int pflbm_contact_angle(pflbm_t* h, const pflbm_wall_t* wall, double* theta_deg, double* circle, int* npoints)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!wall || !theta_deg) return fail(PFLBM_EINVAL, "NULL argument");
+    if (wall->type != 0 && wall->type != 1) return fail(PFLBM_EINVAL, "wall type must be 0 or 1");
+    if (wall->type == 1 && !(wall->r > 0)) return fail(PFLBM_EINVAL, "circular wall needs r > 0");
+    DeviceGuard g(h->device);
+    if (int rc = ensure_out(h)) return rc;
+    double* dphi = h->out;
+    double* dres = h->out + 3 * (size_t)h->nx * h->ny;   // the p slot, unused here
+    CK(launch_macro(h, dphi, nullptr, nullptr));
+    CK(launch_contact_angle(h, wall, dphi, dres));
+    double res[5];
+    CK(cudaMemcpyAsync(res, dres, sizeof(res), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *theta_deg = res[0];
+    if (circle) { circle[0] = res[1]; circle[1] = res[2]; circle[2] = res[3]; }
+    if (npoints) *npoints = (int)res[4];
+    if (res[4] < 3 || !std::isfinite(res[0])) return fail(PFLBM_EINVAL, "fewer than 3 contour points to fit");
+    return read_status(h);
+}
+
+int pflbm_geometry(pflbm_t* h, uint8_t* cls, uint16_t* unknown, uint16_t* doubly, double* av)
+{
+    if (int rc = check_handle(h)) return rc;
+    DeviceGuard g(h->device);
+    size_t N = (size_t)h->nx * h->ny;
+    if (cls) {
+        // class bits only
+        uint8_t* tmp = (uint8_t*)std::malloc((size_t)h->ny * h->pitch);
+        if (!tmp) return fail(PFLBM_ENOMEM, "host allocation failed");
+        cudaError_t e = cudaMemcpyAsync(tmp, h->cls, (size_t)h->ny * h->pitch, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { std::free(tmp); return cuda_fail(e, "geometry read-back"); }
+        for (int y = 0; y < h->ny; ++y)
+            for (int x = 0; x < h->nx; ++x) cls[(size_t)y * h->nx + x] = tmp[(size_t)y * h->pitch + x] & CLS_MASK;
+        std::free(tmp);
+    }
+    if (av)
+        CK(cudaMemcpy2DAsync(av, h->nx * sizeof(double), h->av, h->pitch * sizeof(double), h->nx * sizeof(double),
+                             h->ny, cudaMemcpyDeviceToHost, h->stream));
+    if (unknown || doubly) {
+        if (int rc = ensure_out(h)) return rc;
+        uint16_t* du = (uint16_t*)h->out;
+        uint16_t* dd = du + N;
+        CK(launch_links(h, du, dd));
+        if (unknown) CK(cudaMemcpyAsync(unknown, du, N * 2, cudaMemcpyDeviceToHost, h->stream));
+        if (doubly) CK(cudaMemcpyAsync(doubly, dd, N * 2, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return PFLBM_OK;
+}
+
+int pflbm_check(pflbm_t* h)
+{
+    if (int rc = check_handle(h)) return rc;
+    DeviceGuard g(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(h->hstatus, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    return read_status(h);
+}
+
+int64_t pflbm_steps(const pflbm_t* h) { return h ? h->steps : -1; }
+
+namespace {
+struct Blob {
+    uint64_t magic;
+    int32_t version, nx, ny, precision;
+    int64_t steps;
+    int32_t replace_phi, pad;
+    double params[10];
+};
+constexpr uint64_t kMagic = 0x4d424c4650ULL;  // "PFLBM"
+}  // namespace
+
+int pflbm_save(pflbm_t* h, void* buf, size_t* len)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!len) return fail(PFLBM_EINVAL, "NULL len");
+    Sizes s = sizes_of(h->nx, h->ny, h->precision);
+    size_t need = sizeof(Blob) + s.pop + s.sprev;
+    if (!buf) { *len = need; return PFLBM_OK; }
+    if (*len < need) { *len = need; return fail(PFLBM_EINVAL, "buffer too small"); }
+    DeviceGuard g(h->device);
+    Blob b{};
+    b.magic = kMagic;
+    b.version = 1;
+    b.nx = h->nx;
+    b.ny = h->ny;
+    b.precision = h->precision;
+    b.steps = h->steps;
+    b.replace_phi = h->replace_phi;
+    const Params& q = h->prm;
+    double pv[10] = {q.beta, q.kappa, q.alpha, q.tau_f, q.tau_g, q.rho_l, q.rho_g, q.W, q.sigma, q.M};
+    std::memcpy(b.params, pv, sizeof(pv));
+    std::memcpy(buf, &b, sizeof(b));
+    char* dst = (char*)buf + sizeof(Blob);
+    CK(cudaMemcpyAsync(dst, h->pop[h->cur], s.pop, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(dst + s.pop, h->sprev, s.sprev, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *len = need;
+    return PFLBM_OK;
+}
+
+int pflbm_load(pflbm_t* h, const void* buf, size_t len)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!buf || len < sizeof(Blob)) return fail(PFLBM_EINVAL, "blob too small");
+    Blob b;
+    std::memcpy(&b, buf, sizeof(b));
+    Sizes s = sizes_of(h->nx, h->ny, h->precision);
+    if (b.magic != kMagic || b.version != 1) return fail(PFLBM_EINVAL, "not a pflbm checkpoint");
+    if (b.nx != h->nx || b.ny != h->ny || b.precision != h->precision)
+        return fail(PFLBM_EINVAL, "checkpoint size or precision differs from the handle");
+    if (len < sizeof(Blob) + s.pop + s.sprev) return fail(PFLBM_EINVAL, "blob truncated");
+    DeviceGuard g(h->device);
+    const char* src = (const char*)buf + sizeof(Blob);
+    CK(cudaMemcpyAsync(h->pop[h->cur], src, s.pop, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->sprev, src + s.pop, s.sprev, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->hstatus) h->hstatus[0] = 0;
+    h->steps = b.steps;
+    h->replace_phi = b.replace_phi != 0;
+    return PFLBM_OK;
+}
+
+}  // extern "C"

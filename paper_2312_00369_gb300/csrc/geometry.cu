@@ -1,0 +1,161 @@
+// geometry.cu -- node classification and the effective surface area a_v
+// (Sec. 2.2.2 and Sec. 2.2.3), once per handle. Integer work; a_v is exact:
+// with epsilon in {0, 1}, grad(epsilon) = n / 12 with the integer vector
+// n = sum_i w36_i c_i epsilon(x + c_i), w36 = 36 w_i = (4 axes, 1 diagonals),
+// so a_v = sqrt(n.n) / 12 is one correctly rounded sqrt and one division.
+#include "pflbm_internal.cuh"
+
+namespace pfk {
+namespace {
+
+__device__ inline int wrapx(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
+// Pass 1: fluid / boundary / (tentatively) interior from the solid mask.
+__global__ void k_classify_1(const uint8_t* __restrict__ solid, uint8_t* __restrict__ cls,
+                             int nx, int ny, int pitch)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    uint8_t c;
+    if (!solid[k]) {
+        c = CLS_FLUID;
+    } else {
+        bool touches = false;
+        for (int i = 1; i < 9; ++i) {
+            int yy = y + cy(i);
+            if (yy < 0 || yy >= ny) continue;
+            if (!solid[(size_t)yy * pitch + wrapx(x + cx(i), nx)]) touches = true;
+        }
+        c = touches ? CLS_BOUNDARY : CLS_INTERIOR;
+    }
+    cls[k] = c;
+}
+
+// Pass 2: interior nodes next to a zeta = 1 node become ghosts.
+__global__ void k_classify_2(uint8_t* __restrict__ cls, int nx, int ny, int pitch)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    if (cls[k] != CLS_INTERIOR) return;
+    for (int i = 1; i < 9; ++i) {
+        int yy = y + cy(i);
+        if (yy < 0 || yy >= ny) continue;
+        uint8_t c = cls[(size_t)yy * pitch + wrapx(x + cx(i), nx)];
+        // pass 1 wrote only FLUID / BOUNDARY / INTERIOR; a concurrent
+        // INTERIOR -> GHOST update of a neighbour does not change zeta.
+        if ((c & CLS_MASK) <= CLS_BOUNDARY) {
+            cls[k] = CLS_GHOST;
+            return;
+        }
+    }
+}
+
+// Pass 3: a_v, the flag bits, and zero a_v elsewhere.
+__global__ void k_classify_3(uint8_t* __restrict__ cls, double* __restrict__ av, int nx,
+                             int ny, int pitch)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    uint8_t c = cls[k] & CLS_MASK;
+    double a = 0.0;
+    uint8_t flags = 0;
+    if (c <= CLS_BOUNDARY) {
+        int n_x = 0, n_y = 0;
+        for (int i = 1; i < 9; ++i) {
+            int yy = y + cy(i);  // in range: rows 0 and ny-1 are never zeta = 1
+            uint8_t cn = cls[(size_t)yy * pitch + wrapx(x + cx(i), nx)] & CLS_MASK;
+            int w36 = (i <= 4) ? 4 : 1;
+            int eps = (cn == CLS_FLUID) ? 1 : 0;
+            n_x += w36 * cx(i) * eps;
+            n_y += w36 * cy(i) * eps;
+            if (cn > CLS_BOUNDARY) flags |= F_LINK;
+            if (cn == CLS_GHOST) flags |= F_NEARGHOST;
+        }
+        if (n_x != 0 || n_y != 0) {
+            a = sqrt((double)(n_x * n_x + n_y * n_y)) / 12.0;
+            flags |= F_WET;
+        }
+    }
+    av[k] = a;
+    // pass 3 reads only the class bits of neighbours, so writing the flag
+    // bits of this node concurrently is safe
+    cls[k] = c | flags;
+}
+
+template <typename C>
+__global__ void k_wet(const uint8_t* __restrict__ cls, const double* __restrict__ av,
+                      const float* __restrict__ theta, C* __restrict__ wet, double root,
+                      double theta_uniform, int nx, int ny, int pitch)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    double th = theta ? (double)theta[k] : theta_uniform;
+    // Eq. chemical_potencial2: the wall term is a_v sqrt(2 kappa beta) cos(theta) (phi - phi^2)
+    wet[k] = (C)(av[k] * root * cos(th * 3.14159265358979323846 / 180.0));
+}
+
+__global__ void k_links(const uint8_t* __restrict__ cls, uint16_t* __restrict__ unknown,
+                        uint16_t* __restrict__ doubly, int nx, int ny, int pitch)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    uint16_t un = 0, db = 0;
+    if (zeta_of(cls[k])) {
+        for (int i = 1; i < 9; ++i) {
+            uint8_t src = cls[(size_t)(y - cy(i)) * pitch + wrapx(x - cx(i), nx)];
+            uint8_t dst = cls[(size_t)(y + cy(i)) * pitch + wrapx(x + cx(i), nx)];
+            if (!zeta_of(src)) {
+                un |= (uint16_t)(1u << i);
+                if (!zeta_of(dst)) db |= (uint16_t)(1u << i);
+            }
+        }
+    }
+    size_t o = (size_t)y * nx + x;  // dense output
+    if (unknown) unknown[o] = un;
+    if (doubly) doubly[o] = db;
+}
+
+dim3 grid2d(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+}  // namespace
+
+cudaError_t launch_classify(pflbm_t* h)
+{
+    dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
+    k_classify_1<<<g, b, 0, h->stream>>>(h->solid, h->cls, h->nx, h->ny, h->pitch);
+    k_classify_2<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->pitch);
+    k_classify_3<<<g, b, 0, h->stream>>>(h->cls, h->av, h->nx, h->ny, h->pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wet(pflbm_t* h)
+{
+    dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
+    double root = sqrt(2.0 * h->prm.kappa * h->prm.beta);
+    if (h->precision == PFLBM_FP64)
+        k_wet<double><<<g, b, 0, h->stream>>>(h->cls, h->av, h->theta, (double*)h->wet, root,
+                                              h->theta_uniform, h->nx, h->ny, h->pitch);
+    else
+        k_wet<float><<<g, b, 0, h->stream>>>(h->cls, h->av, h->theta, (float*)h->wet, root,
+                                             h->theta_uniform, h->nx, h->ny, h->pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links(pflbm_t* h, uint16_t* unknown, uint16_t* doubly)
+{
+    dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
+    k_links<<<g, b, 0, h->stream>>>(h->cls, unknown, doubly, h->nx, h->ny, h->pitch);
+    return cudaGetLastError();
+}
+
+}  // namespace pfk

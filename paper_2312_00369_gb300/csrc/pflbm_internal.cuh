@@ -1,0 +1,104 @@
+// pflbm_internal.cuh -- shared definitions of the CUDA library (not part of
+// the ABI): lattice constants, the handle layout, kernel entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/pflbm.h"
+
+namespace pfk {
+
+// ---------------------------------------------------------------------------
+// D2Q9 in the library's order: rest, the four axes counter-clockwise from +x,
+// then the four diagonals counter-clockwise from (+1,+1). Weights 4/9, 1/9,
+// 1/36 and c_s^2 = 1/3 (Sec. 2.1.2).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int cy(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5); }
+
+template <typename C> __host__ __device__ constexpr C wgt(int i) {
+    return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// Node byte: bits 0-1 class, bit 2 "a_v != 0" (read the wetting coefficient),
+// bit 3 "zeta = 1 with a zeta = 0 neighbour" (bounce-back links present),
+// bit 4 "ghost node in the 8-neighbourhood" (stencil reaches a ghost value).
+enum : uint8_t {
+    CLS_FLUID = 0, CLS_BOUNDARY = 1, CLS_GHOST = 2, CLS_INTERIOR = 3,
+    CLS_MASK = 3, F_WET = 4, F_LINK = 8, F_NEARGHOST = 16,
+    CLS_OUT = 0xFF  // outside the lattice in y (tile halos only)
+};
+__host__ __device__ inline bool zeta_of(uint8_t c) { return c != CLS_OUT && (c & CLS_MASK) <= CLS_BOUNDARY; }
+
+// Tile of the fused step: TX x TY nodes per CTA, one node per thread.
+constexpr int TX = 32;
+constexpr int TY = 8;
+
+struct Params {           // derived parameters (Sec. 2.1-2.2), in FP64
+    double beta, kappa, alpha, tau_f, tau_g, rho_l, rho_g, W, sigma, M;
+};
+
+}  // namespace pfk
+
+// The handle.
+struct pflbm {
+    int nx = 0, ny = 0, pitch = 0;
+    int precision = PFLBM_FP32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    pfk::Params prm{};
+    double theta_uniform = 90.0;
+    // allocator
+    void* (*alloc_fn)(size_t, void*) = nullptr;
+    void (*free_fn)(void*, size_t, void*) = nullptr;
+    void* alloc_ctx = nullptr;
+    // device buffers (sizes: N = ny*pitch nodes)
+    uint8_t* cls = nullptr;       // node byte [N]
+    uint8_t* solid = nullptr;     // user mask [N]
+    float* theta = nullptr;       // angle field [N] (degrees)
+    void* wet = nullptr;          // a_v sqrt(2 kappa beta) cos(theta) [N] (FP64 or FP32)
+    double* av = nullptr;         // a_v [N]
+    void* pop[2] = {nullptr, nullptr};  // f then g, each [9][ny][pitch], ping-pong
+    void* sprev = nullptr;        // u.grad(phi) history [N]
+    double* phi0 = nullptr;       // initial-field staging / ghost-filled phi [N]
+    double* mu0 = nullptr;        // initial chemical potential [N]
+    double* red = nullptr;        // reduction scratch
+    double* pts = nullptr;        // contact-angle points (2 * pts_cap)
+    int pts_cap = 0;
+    double* out = nullptr;        // read-back scratch (4 dense [ny][nx] doubles)
+    size_t out_bytes = 0;
+    int* dstatus = nullptr;       // device status word
+    int* hstatus = nullptr;       // pinned host mirror
+    int cur = 0;                  // which pop buffer holds the current state
+    bool replace_phi = true;
+    int64_t steps = 0;
+    size_t bytes_allocated = 0;
+    cudaEvent_t status_ev = nullptr;
+};
+
+namespace pfk {
+
+size_t elem_size(int precision);
+size_t pop_bytes(int ny, int pitch, int precision);   // one of f or g, one copy
+
+// geometry.cu
+cudaError_t launch_classify(pflbm_t* h);
+cudaError_t launch_wet(pflbm_t* h);
+cudaError_t launch_links(pflbm_t* h, uint16_t* unknown, uint16_t* doubly);
+
+// step.cu
+cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, int replace);
+cudaError_t launch_init_populations(pflbm_t* h);
+cudaError_t launch_step(pflbm_t* h);
+cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p);
+
+// diag.cu
+cudaError_t launch_mass(pflbm_t* h, double* d_out);
+cudaError_t launch_contact_angle(pflbm_t* h, const pflbm_wall_t* wall, const double* d_phi,
+                                 double* d_result /* theta, a, b, R, n */);
+
+}  // namespace pfk

@@ -1,0 +1,448 @@
+// step.cu -- initial state, the fused time step and the macroscopic read-back.
+//
+// State layout (HBM): one buffer per copy holds 18 planes [ny][pitch]: f_0..f_8
+// then g_0..g_8, in the library's velocity order; two copies ping-pong. The
+// stored values are POST-COLLISION populations f*_i(x), g*_i(x) at the node
+// that produced them (pull scheme). A step at node x first pulls its
+// post-streaming populations,
+//     f_i(x) = f*_i(x - c_i)          if zeta(x - c_i) = 1   (streaming)
+//            = f*_{i'}(x + c_i)       else if zeta(x + c_i) = 1
+//            = f*_{i'}(x)             otherwise,
+// which is the modified bounce-back of Sec. 2.2.2 (unknown f_i(x_b) takes the
+// post-streaming f_{i'}(x_b); if that is unknown too, the node's own
+// post-collision f*_{i'}). Then it computes phi = sum g_i (Eq.
+// order-parameter) on a shared-memory tile with a two-node halo, fills ghost
+// nodes with the zeta-weighted neighbour mean (Sec. 2.2.2), takes the
+// isotropic gradient and Laplacian (Eqs. gradient, Laplace), the chemical
+// potential with the wetting term (Eq. chemical_potencial2), rho, the force
+// F = mu grad(phi), u and p (Sec. 2.1.2), collides f (Eqs. BGK-NS, feq_i, Siu,
+// GGi) and g (Eqs. BGK, H_i, F_i with (1/2) dG/dt as a backward difference)
+// and stores f*, g* and the new u.grad(phi) history.
+#include "pflbm_internal.cuh"
+
+namespace pfk {
+namespace {
+
+__device__ __forceinline__ int wrap1(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+__device__ __forceinline__ int wrapn(int x, int nx) { int r = x % nx; return r < 0 ? r + nx : r; }
+
+template <typename S, typename C>
+struct StepArgs {
+    const uint8_t* cls;
+    const C* wet;
+    const S* fin;   // 18 planes
+    S* fout;        // 18 planes
+    S* sprev;
+    int nx, ny, pitch;
+    size_t plane;
+    C beta4, kappa, rho_g, drho, omega_f, omega_g, force_pre, alpha;
+    int* status;
+    // macroscopic output (read-back kernel only), dense [ny][nx]
+    double* o_phi;
+    double* o_u;
+    double* o_p;
+};
+
+// Pull of direction i at node (gx, gy), whose class byte sits at s_cls[sy][sx].
+template <int I, typename S, typename C, bool CHECK>
+__device__ __forceinline__ C pull(const S* __restrict__ base, const uint8_t (*s_cls)[TX + 6], int sy,
+                                  int sx, int gx, int gy, int nx, int pitch, size_t plane)
+{
+    constexpr int X = cx(I), Y = cy(I), O = opp(I);
+    if (!CHECK || zeta_of(s_cls[sy - Y][sx - X])) {
+        return (C)base[I * plane + (size_t)(gy - Y) * pitch + wrap1(gx - X, nx)];
+    }
+    if (zeta_of(s_cls[sy + Y][sx + X])) {
+        return (C)base[O * plane + (size_t)(gy + Y) * pitch + wrap1(gx + X, nx)];
+    }
+    return (C)base[O * plane + (size_t)gy * pitch + gx];
+}
+
+template <typename S, typename C, bool CHECK>
+__device__ __forceinline__ void pull_all(C v[9], const S* __restrict__ base, const uint8_t (*s_cls)[TX + 6],
+                                         int sy, int sx, int gx, int gy, int nx, int pitch, size_t plane)
+{
+    v[0] = (C)base[(size_t)gy * pitch + gx];
+    v[1] = pull<1, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[2] = pull<2, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[3] = pull<3, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[4] = pull<4, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[5] = pull<5, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[6] = pull<6, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[7] = pull<7, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[8] = pull<8, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ C pulled_phi(const S* __restrict__ gbase, const uint8_t (*s_cls)[TX + 6], int sy,
+                                        int sx, int gx, int gy, int nx, int pitch, size_t plane)
+{
+    C v[9];
+    if (s_cls[sy][sx] & F_LINK)
+        pull_all<S, C, true>(v, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    else
+        pull_all<S, C, false>(v, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// Common prologue: class tile (halo 3), phi tile (halo 2) with ghost values.
+// Returns the own node's pulled g in gown[] when it is a zeta = 1 node.
+template <typename S, typename C>
+__device__ __forceinline__ void tile_prologue(const StepArgs<S, C>& a, uint8_t (*s_cls)[TX + 6],
+                                              C (*s_phi)[TX + 4], int x0, int y0, C gown[9])
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const S* gbase = a.fin + 9 * a.plane;
+
+    for (int p = tid; p < (TY + 6) * (TX + 6); p += TX * TY) {
+        int py = p / (TX + 6), px = p - py * (TX + 6);
+        int gy = y0 - 3 + py, gx = wrapn(x0 - 3 + px, nx);
+        s_cls[py][px] = (gy < 0 || gy >= ny) ? (uint8_t)CLS_OUT : a.cls[(size_t)gy * pitch + gx];
+    }
+    __syncthreads();
+
+    // own node (a tile that runs past x = nx - 1 holds wrapped nodes there:
+    // they are computed like halo nodes but not collided)
+    {
+        int gx = wrapn(x0 + tx, nx), gy = y0 + ty;
+        C ph = C(0);
+        if (gy < ny && zeta_of(s_cls[ty + 3][tx + 3])) {
+            if (s_cls[ty + 3][tx + 3] & F_LINK)
+                pull_all<S, C, true>(gown, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+            else
+                pull_all<S, C, false>(gown, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+            ph = ((gown[0] + gown[1]) + (gown[2] + gown[3])) + ((gown[4] + gown[5]) + (gown[6] + gown[7])) + gown[8];
+        }
+        s_phi[ty + 2][tx + 2] = ph;
+    }
+    // halo ring of width 2
+    for (int p = tid; p < (TY + 4) * (TX + 4); p += TX * TY) {
+        int py = p / (TX + 4), px = p - py * (TX + 4);
+        if (py >= 2 && py < TY + 2 && px >= 2 && px < TX + 2) continue;
+        int sy = py + 1, sx = px + 1;
+        C ph = C(0);
+        if (zeta_of(s_cls[sy][sx])) {
+            int gy = y0 - 2 + py, gx = wrapn(x0 - 2 + px, nx);
+            ph = pulled_phi<S, C>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, a.plane);
+        }
+        s_phi[py][px] = ph;
+    }
+    __syncthreads();
+
+    // ghost nodes within one node of the tile: zeta-weighted 3x3 mean
+    for (int p = tid; p < (TY + 2) * (TX + 2); p += TX * TY) {
+        int py = p / (TX + 2) + 1, px = p % (TX + 2) + 1;   // phi-tile coords 1..T+2
+        uint8_t c = s_cls[py + 1][px + 1];
+        if (c == CLS_OUT || (c & CLS_MASK) != CLS_GHOST) continue;
+        C num = C(0), den = C(0);
+#pragma unroll
+        for (int j = 1; j < 9; ++j) {
+            if (zeta_of(s_cls[py + 1 + cy(j)][px + 1 + cx(j)])) {
+                num += s_phi[py + cy(j)][px + cx(j)];
+                den += C(1);
+            }
+        }
+        s_phi[py][px] = num / den;
+    }
+    __syncthreads();
+}
+
+// Stencils of Eqs. gradient and Laplace at phi-tile position (py, px).
+template <typename C>
+__device__ __forceinline__ void stencils(C (*s_phi)[TX + 4], int py, int px, C& gx, C& gy, C& lap)
+{
+    C c = s_phi[py][px];
+    C E = s_phi[py][px + 1], W = s_phi[py][px - 1], N = s_phi[py + 1][px], Sx = s_phi[py - 1][px];
+    C NE = s_phi[py + 1][px + 1], NW = s_phi[py + 1][px - 1], SW = s_phi[py - 1][px - 1], SE = s_phi[py - 1][px + 1];
+    gx = (E - W) * (C(1) / C(3)) + ((NE + SE) - (NW + SW)) * (C(1) / C(12));
+    gy = (N - Sx) * (C(1) / C(3)) + ((NE + NW) - (SE + SW)) * (C(1) / C(12));
+    lap = ((E + W) + (N + Sx)) * (C(2) / C(3)) + ((NE + NW) + (SE + SW)) * (C(1) / C(6)) - c * (C(10) / C(3));
+}
+
+template <typename S, typename C, bool COLLIDE>
+__global__ void __launch_bounds__(TX * TY) k_step(StepArgs<S, C> a)
+{
+    __shared__ uint8_t s_cls[TY + 6][TX + 6];
+    __shared__ C s_phi[TY + 4][TX + 4];
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    C g[9];
+    tile_prologue<S, C>(a, s_cls, s_phi, x0, y0, g);
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx >= a.nx || gy >= a.ny) return;
+    const uint8_t code = s_cls[ty + 3][tx + 3];
+    const size_t k = (size_t)gy * a.pitch + gx;
+    if (!zeta_of(code)) {
+        if (!COLLIDE) {
+            size_t o = (size_t)gy * a.nx + gx;
+            if (a.o_phi) a.o_phi[o] = (double)s_phi[ty + 2][tx + 2];
+            if (a.o_u) { a.o_u[2 * o] = 0.0; a.o_u[2 * o + 1] = 0.0; }
+            if (a.o_p) a.o_p[o] = 0.0;
+        }
+        return;
+    }
+
+    // ---- chemical potential (Eq. chemical_potencial2) ----
+    C gpx, gpy, lap;
+    stencils<C>(s_phi, ty + 2, tx + 2, gpx, gpy, lap);
+    const C ph = s_phi[ty + 2][tx + 2];
+    const C wet = (code & F_WET) ? a.wet[k] : C(0);
+    const C mu = a.beta4 * ph * (ph - C(1)) * (ph - C(0.5)) - a.kappa * lap - wet * (ph - ph * ph);
+
+    // ---- coupling fields (Sec. 2.1.1) ----
+    const C rho = a.rho_g + a.drho * ph;
+    const C drx = a.drho * gpx, dry = a.drho * gpy;
+    const C Fx = mu * gpx, Fy = mu * gpy;
+
+    // ---- hydrodynamic moments (Sec. 2.1.2) ----
+    C f[9];
+    if (code & F_LINK)
+        pull_all<S, C, true>(f, a.fin, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
+    else
+        pull_all<S, C, false>(f, a.fin, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
+    const C mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const C my = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const C inv_rho = C(1) / rho;
+    const C ux = (mx + C(0.5) * Fx) * inv_rho;
+    const C uy = (my + C(0.5) * Fy) * inv_rho;
+    const C uu = ux * ux + uy * uy;
+    const C sum_moving = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+    // p = c_s^2/(1 - w_0) [sum_{i!=0} f_i + u.grad(rho)/2 + rho s_0(u)], s_0 = -w_0 (3/2) u^2
+    const C p = C(0.6) * (sum_moving + C(0.5) * (ux * drx + uy * dry) - rho * (C(2) / C(3)) * uu);
+
+    if (!COLLIDE) {
+        size_t o = (size_t)gy * a.nx + gx;
+        if (a.o_phi) a.o_phi[o] = (double)ph;
+        if (a.o_u) { a.o_u[2 * o] = (double)ux; a.o_u[2 * o + 1] = (double)uy; }
+        if (a.o_p) a.o_p[o] = (double)p;
+        return;
+    }
+    if (!(uu < C(0.09))) atomicOr(a.status, 1);
+
+    // ---- f collision: f* = f + (f^eq - f)/tau_f + F_i ----
+    S* fo = a.fout;
+    const C of = a.omega_f;
+    {
+        const C feq0 = C(-5) / C(3) * p - rho * (wgt<C>(0) * C(1.5)) * uu;
+        fo[k] = (S)(f[0] + of * (feq0 - f[0]));
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const C w = wgt<C>(i);
+        const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
+        const C cF = C(cx(i)) * Fx + C(cy(i)) * Fy;
+        const C cdr = C(cx(i)) * drx + C(cy(i)) * dry;
+        const C feq = w * (C(3) * p + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
+        const C Fi = a.force_pre * w * C(3) * (cF + cu * cdr);
+        fo[i * a.plane + k] = (S)(f[i] + of * (feq - f[i]) + Fi);
+    }
+
+    // ---- g collision: g* = g + (g^eq - g)/tau_g + (3/2) G_i(t) - (1/2) G_i(t-1) ----
+    const C s_now = ux * gpx + uy * gpy;
+    const C s_old = (C)a.sprev[k];
+    const C src = C(1.5) * s_now - C(0.5) * s_old;
+    const C am = a.alpha * mu;
+    const C og = a.omega_g;
+    S* go = a.fout + 9 * a.plane;
+    {
+        const C geq0 = ph - (C(1) - wgt<C>(0)) * am;
+        go[k] = (S)(g[0] + og * (geq0 - g[0]) + wgt<C>(0) * C(-2) * src);
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const C w = wgt<C>(i);
+        const C h = (i <= 4) ? C(-0.5) : C(1);
+        go[i * a.plane + k] = (S)(g[i] + og * (w * am - g[i]) + w * h * src);
+    }
+    a.sprev[k] = (S)s_now;
+}
+
+template <typename S, typename C>
+StepArgs<S, C> make_args(pflbm_t* h)
+{
+    StepArgs<S, C> a{};
+    a.cls = h->cls;
+    a.wet = (const C*)h->wet;
+    a.fin = (const S*)h->pop[h->cur];
+    a.fout = (S*)h->pop[h->cur ^ 1];
+    a.sprev = (S*)h->sprev;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = (size_t)h->ny * h->pitch;
+    const Params& q = h->prm;
+    a.beta4 = (C)(4.0 * q.beta);
+    a.kappa = (C)q.kappa;
+    a.rho_g = (C)q.rho_g;
+    a.drho = (C)(q.rho_l - q.rho_g);
+    a.omega_f = (C)(1.0 / q.tau_f);
+    a.omega_g = (C)(1.0 / q.tau_g);
+    a.force_pre = (C)(1.0 - 1.0 / (2.0 * q.tau_f));
+    a.alpha = (C)q.alpha;
+    a.status = h->dstatus;
+    return a;
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (FP64 arithmetic for every storage precision)
+// ---------------------------------------------------------------------------
+__global__ void k_init_droplet(const uint8_t* __restrict__ cls, double* __restrict__ phi, int nx, int ny,
+                               int pitch, double x0, double y0, double R, double W, int replace)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    if (!zeta_of(cls[k])) {
+        if (replace) phi[k] = 0.0;
+        return;
+    }
+    double dx = fabs((double)x - x0);
+    dx = fmod(dx, (double)nx);
+    if (dx > 0.5 * nx) dx = nx - dx;       // x-periodic distance
+    double dy = (double)y - y0;
+    double r = sqrt(dx * dx + dy * dy);
+    // Eq. initialphi
+    double v = 0.5 + 0.5 * tanh(2.0 * (R - r) / W);
+    if (replace || v > phi[k]) phi[k] = v;
+}
+
+__global__ void k_ghost_fill(const uint8_t* __restrict__ cls, double* __restrict__ phi, int nx, int ny, int pitch)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    uint8_t c = cls[k] & CLS_MASK;
+    if (c == CLS_INTERIOR) { phi[k] = 0.0; return; }
+    if (c != CLS_GHOST) return;
+    double num = 0.0, den = 0.0;
+    for (int j = 1; j < 9; ++j) {
+        int yy = y + cy(j);
+        if (yy < 0 || yy >= ny) continue;
+        size_t m = (size_t)yy * pitch + wrap1(x + cx(j), nx);
+        if (zeta_of(cls[m])) { num += phi[m]; den += 1.0; }
+    }
+    phi[k] = num / den;
+}
+
+template <typename C>
+__global__ void k_init_mu(const uint8_t* __restrict__ cls, const C* __restrict__ wet, const double* __restrict__ phi,
+                          double* __restrict__ mu, void* __restrict__ sprev_v, int nx, int ny, int pitch,
+                          Params q)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    C* sprev = (C*)sprev_v;
+    uint8_t code = cls[k];
+    if (!zeta_of(code)) { mu[k] = 0.0; sprev[k] = (C)0; return; }
+    auto at = [&](int dx, int dy) { return phi[(size_t)(y + dy) * pitch + wrap1(x + dx, nx)]; };
+    double c = phi[k];
+    double E = at(1, 0), Wv = at(-1, 0), N = at(0, 1), S = at(0, -1);
+    double NE = at(1, 1), NW = at(-1, 1), SW = at(-1, -1), SE = at(1, -1);
+    double gpx = (E - Wv) / 3.0 + ((NE + SE) - (NW + SW)) / 12.0;
+    double gpy = (N - S) / 3.0 + ((NE + NW) - (SE + SW)) / 12.0;
+    double lap = ((E + Wv) + (N + S)) * (2.0 / 3.0) + ((NE + NW) + (SE + SW)) / 6.0 - c * (10.0 / 3.0);
+    double wv = (code & F_WET) ? (double)wet[k] : 0.0;
+    double m = 4.0 * q.beta * c * (c - 1.0) * (c - 0.5) - q.kappa * lap - wv * (c - c * c);
+    mu[k] = m;
+    // u at t = 0 from f = 0: u = F / (2 rho); the history of the first step is u.grad(phi)
+    double rho = q.rho_g + (q.rho_l - q.rho_g) * c;
+    double ux = 0.5 * m * gpx / rho, uy = 0.5 * m * gpy / rho;
+    sprev[k] = (C)(ux * gpx + uy * gpy);
+}
+
+// Post-collision arrays that the first pull turns into f = 0, g = g^eq(phi0, mu0).
+template <typename S>
+__global__ void k_init_pop(const uint8_t* __restrict__ cls, const double* __restrict__ phi,
+                           const double* __restrict__ mu, S* __restrict__ pop, int nx, int ny, int pitch,
+                           size_t plane, double alpha)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t k = (size_t)y * pitch + x;
+    for (int i = 0; i < 18; ++i) pop[i * plane + k] = (S)0;
+    if (!zeta_of(cls[k])) return;
+    S* g = pop + 9 * plane;
+    for (int j = 0; j < 9; ++j) {
+        // the pull at x + c_j reads this value as its g_j when x + c_j is a
+        // zeta = 1 node; when it is not, only the doubly-unknown rule of this
+        // node reads it, as the node's own value
+        size_t m = k;
+        if (j != 0) {
+            size_t mm = (size_t)(y + cy(j)) * pitch + wrap1(x + cx(j), nx);
+            if (zeta_of(cls[mm])) m = mm;
+        }
+        double w = j == 0 ? 4.0 / 9.0 : (j <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        double geq = (j == 0) ? phi[m] - (1.0 - w) * alpha * mu[m] : w * alpha * mu[m];
+        g[j * plane + k] = (S)geq;
+    }
+}
+
+dim3 grid2d(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+template <typename S, typename C, bool COLLIDE>
+cudaError_t run_step_kernel(pflbm_t* h, double* o_phi, double* o_u, double* o_p)
+{
+    StepArgs<S, C> a = make_args<S, C>(h);
+    a.o_phi = o_phi;
+    a.o_u = o_u;
+    a.o_p = o_p;
+    dim3 b(TX, TY), g((h->nx + TX - 1) / TX, (h->ny + TY - 1) / TY);
+    k_step<S, C, COLLIDE><<<g, b, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, int replace)
+{
+    dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
+    k_init_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, x0, y0, R, h->prm.W, replace);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_populations(pflbm_t* h)
+{
+    dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
+    k_ghost_fill<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch);
+    size_t plane = (size_t)h->ny * h->pitch;
+    if (h->precision == PFLBM_FP64) {
+        k_init_mu<double><<<g, b, 0, h->stream>>>(h->cls, (const double*)h->wet, h->phi0, h->mu0, h->sprev,
+                                                  h->nx, h->ny, h->pitch, h->prm);
+        k_init_pop<double><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->mu0, (double*)h->pop[h->cur], h->nx,
+                                                   h->ny, h->pitch, plane, h->prm.alpha);
+    } else {
+        k_init_mu<float><<<g, b, 0, h->stream>>>(h->cls, (const float*)h->wet, h->phi0, h->mu0, h->sprev,
+                                                 h->nx, h->ny, h->pitch, h->prm);
+        k_init_pop<float><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->mu0, (float*)h->pop[h->cur], h->nx,
+                                                  h->ny, h->pitch, plane, h->prm.alpha);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(pflbm_t* h)
+{
+    cudaError_t e;
+    if (h->precision == PFLBM_FP64)
+        e = run_step_kernel<double, double, true>(h, nullptr, nullptr, nullptr);
+    else
+        e = run_step_kernel<float, float, true>(h, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) h->cur ^= 1;
+    return e;
+}
+
+cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p)
+{
+    if (h->precision == PFLBM_FP64)
+        return run_step_kernel<double, double, false>(h, phi, u, p);
+    return run_step_kernel<float, float, false>(h, phi, u, p);
+}
+
+}  // namespace pfk

@@ -1,0 +1,286 @@
+"""ctypes binding of libpflbm.so (include/pflbm.h) with the same names.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. PyTorch supplies device memory (its caching allocator, through the
+library's allocator callbacks) and streams. If the library is missing or
+cannot be loaded, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpflbm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pflbm.h")
+
+OK, EINVAL, ENOMEM, EBADMASK, ENUMERIC, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
+FLUID, BOUNDARY, GHOST, INTERIOR = 0, 1, 2, 3
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class PflbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pflbm error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("solid_mask", ctypes.POINTER(ctypes.c_uint8)),
+                ("theta_deg", ctypes.c_double),
+                ("theta_field_deg", ctypes.POINTER(ctypes.c_float)),
+                ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
+                ("tau_f", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
+                ("tau_g", ctypes.c_double), ("precision", ctypes.c_int), ("device", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+class Wall(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("px", ctypes.c_double), ("py", ctypes.c_double),
+                ("nx", ctypes.c_double), ("ny", ctypes.c_double), ("r", ctypes.c_double),
+                ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
+                ("exclude", ctypes.c_double)]
+
+
+_lib = None
+_H = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_u16p = ctypes.POINTER(ctypes.c_uint16)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "pflbm_params_default": (None, [ctypes.POINTER(Params)]),
+    "pflbm_create": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.c_int, ctypes.c_int, _u8p]
+                     + [ctypes.c_double] * 7),
+    "pflbm_create_ex": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(Params)]),
+    "pflbm_destroy": (None, [_H]),
+    "pflbm_set_theta_field": (ctypes.c_int, [_H, _fp]),
+    "pflbm_init_droplet": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "pflbm_init_phi": (ctypes.c_int, [_H, _dp]),
+    "pflbm_step": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "pflbm_get": (ctypes.c_int, [_H, _dp, _dp, _dp]),
+    "pflbm_get_device": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pflbm_mass": (ctypes.c_int, [_H, _dp]),
+    "pflbm_contact_angle": (ctypes.c_int, [_H, ctypes.POINTER(Wall), _dp, _dp, _ip]),
+    "pflbm_geometry": (ctypes.c_int, [_H, _u8p, _u16p, _u16p, _dp]),
+    "pflbm_lattice": (None, [_ip, _ip]),
+    "pflbm_check": (ctypes.c_int, [_H]),
+    "pflbm_steps": (ctypes.c_int64, [_H]),
+    "pflbm_footprint_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pflbm_save": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "pflbm_load": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
+    "pflbm_last_error": (ctypes.c_char_p, []),
+}
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions include/pflbm.h declares."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pflbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load libpflbm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2312_00369_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise PflbmError(rc, lib().pflbm_last_error().decode())
+    return rc
+
+
+def _p(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def pflbm_lattice():
+    cx = (ctypes.c_int * 9)()
+    cy = (ctypes.c_int * 9)()
+    lib().pflbm_lattice(cx, cy)
+    return np.array(cx[:]), np.array(cy[:])
+
+
+def pflbm_footprint_bytes(nx, ny, precision="fp32"):
+    return int(lib().pflbm_footprint_bytes(nx, ny, PRECISIONS.get(precision, precision)))
+
+
+class TorchAllocator:
+    """Device memory from PyTorch's caching allocator for one handle."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+        self._alloc = _ALLOC(self.alloc)
+        self._free = _FREE(self.free)
+
+    def alloc(self, nbytes, ctx):
+        try:
+            return int(self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+        except Exception:
+            return None
+
+    def free(self, ptr, nbytes, ctx):
+        if ptr:
+            self.torch.cuda.caching_allocator_delete(ptr)
+
+
+class Solver:
+    """One lattice (``pflbm_t``) owned from Python.
+
+    ``solid``: uint8 [ny, nx] mask (1 = solid). ``precision``: "fp64",
+    "fp32", "bf16" or "fp16". ``stream``: a ``torch.cuda.Stream`` (default:
+    the current stream of ``device``). Memory comes from PyTorch's caching
+    allocator unless ``torch_memory=False``.
+    """
+
+    def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
+                 rho_l=1.0, rho_g=0.1, tau_g=0.0, theta_field=None, precision="fp32",
+                 device=None, stream=None, torch_memory=True):
+        import torch
+        L = lib()
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        self.ny, self.nx = solid.shape
+        self.precision = precision
+        dev = torch.cuda.current_device() if device is None else int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        self.device = dev
+        p = Params()
+        L.pflbm_params_default(ctypes.byref(p))
+        p.nx, p.ny = self.nx, self.ny
+        p.solid_mask = _p(solid, _u8p)
+        p.theta_deg = float(theta_deg)
+        self._theta_field = None
+        if theta_field is not None:
+            self._theta_field = np.ascontiguousarray(theta_field, dtype=np.float32)
+            p.theta_field_deg = _p(self._theta_field, _fp)
+        p.sigma, p.W, p.M, p.tau_f = sigma, W, M, tau_f
+        p.rho_l, p.rho_g, p.tau_g = rho_l, rho_g, tau_g
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.device = dev
+        p.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._allocator = None
+        if torch_memory:
+            self._allocator = TorchAllocator(dev, stream.cuda_stream)
+            p.alloc = self._allocator._alloc
+            p.free = self._allocator._free
+        h = _H()
+        _check(L.pflbm_create_ex(ctypes.byref(h), ctypes.byref(p)))
+        self._h = h
+        self.W = W
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().pflbm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- the API ---------------------------------------------------------------
+    def init_droplet(self, x0, y0, R):
+        _check(lib().pflbm_init_droplet(self._h, float(x0), float(y0), float(R)))
+
+    def init_phi(self, phi):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        assert phi.shape == (self.ny, self.nx)
+        _check(lib().pflbm_init_phi(self._h, _p(phi)))
+
+    def set_theta_field(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().pflbm_set_theta_field(self._h, _p(theta, _fp)))
+
+    def step(self, n=1):
+        _check(lib().pflbm_step(self._h, int(n)))
+
+    def get(self):
+        phi = np.empty((self.ny, self.nx))
+        u = np.empty((self.ny, self.nx, 2))
+        p = np.empty((self.ny, self.nx))
+        _check(lib().pflbm_get(self._h, _p(phi), _p(u), _p(p)))
+        return phi, u, p
+
+    def get_device(self, phi=None, u=None, p=None):
+        """Fill caller-owned torch float64 CUDA tensors (any may be None)."""
+        ptr = (lambda t: None if t is None else ctypes.c_void_p(t.data_ptr()))
+        _check(lib().pflbm_get_device(self._h, ptr(phi), ptr(u), ptr(p)))
+
+    def mass(self):
+        out = ctypes.c_double()
+        _check(lib().pflbm_mass(self._h, ctypes.byref(out)))
+        return out.value
+
+    def contact_angle(self, wall: dict, exclude=None):
+        w = Wall(type=int(wall.get("type", 0)), px=wall.get("px", 0.0), py=wall.get("py", 0.0),
+                 nx=wall.get("nx", 0.0), ny=wall.get("ny", 1.0), r=wall.get("r", 0.0),
+                 x_lo=wall.get("x_lo", -1e300), x_hi=wall.get("x_hi", 1e300),
+                 exclude=wall.get("exclude", 1.5 * self.W if exclude is None else exclude))
+        th = ctypes.c_double()
+        circ = (ctypes.c_double * 3)()
+        n = ctypes.c_int()
+        _check(lib().pflbm_contact_angle(self._h, ctypes.byref(w), ctypes.byref(th), circ,
+                                         ctypes.byref(n)))
+        return th.value, np.array(circ[:]), n.value
+
+    def geometry(self):
+        shp = (self.ny, self.nx)
+        cls = np.empty(shp, np.uint8)
+        un = np.empty(shp, np.uint16)
+        db = np.empty(shp, np.uint16)
+        av = np.empty(shp)
+        _check(lib().pflbm_geometry(self._h, _p(cls, _u8p), _p(un, _u16p), _p(db, _u16p), _p(av)))
+        return dict(cls=cls, unknown=un, doubly=db, av=av)
+
+    def check(self):
+        _check(lib().pflbm_check(self._h))
+
+    @property
+    def steps(self):
+        return int(lib().pflbm_steps(self._h))
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(lib().pflbm_save(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().pflbm_save(self._h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().pflbm_load(self._h, buf, len(blob)))

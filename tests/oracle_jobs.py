@@ -1,0 +1,87 @@
+"""Oracle reference runs used by the GPU parity tests.
+
+Each job builds a case from the seeded input generators, runs the FP64 oracle
+and returns plain numpy arrays. The jobs run in a ``spawn`` process pool so
+that the slow CPU oracle overlaps with the GPU tests (the pool is started
+with ``spawn``, never forked from a process that already touched CUDA).
+"""
+import math
+
+import numpy as np
+
+import oracle
+from paper_2312_00369_gb300 import workloads as wl
+
+
+def case_by_name(name):
+    if name == "flat60":
+        return wl.droplet_on_flat_wall(theta=60.0)
+    if name == "flat60_short":
+        return wl.droplet_on_flat_wall(theta=60.0, steps=600)
+    if name == "incline30":
+        return wl.droplet_on_incline(theta=60.0, steps=800)
+    if name == "incline45_ragged":
+        return wl.droplet_on_incline(nx=130, ny=91, gamma=45.0, R=18.0, theta=120.0, steps=400)
+    if name == "cylinder":
+        return wl.droplet_on_cylinder(theta=120.0, steps=200)
+    if name == "crop":
+        return wl.many_droplets_flat(nx=512, ny=256, n_drops=8, seed=2312, steps=400)
+    if name == "tiny":
+        s = np.ones((6, 3), np.uint8)
+        s[2:4] = 0
+        return wl.Case("tiny", s, [(1.0, 2.0, 1.5)], dict(type=0, px=0, py=0.5, nx=0, ny=1),
+                       theta_deg=70.0, steps=50)
+    if name == "block":
+        from tests.oracle_fixtures import read_geometry
+        mask, _, _ = read_geometry("geometry_block.txt")
+        big = np.tile(mask, (1, 3))           # 36 x 10, x-periodic copies
+        return wl.Case("block", big, [(17.0, 6.0, 4.0)], dict(type=0, px=0, py=0.5, nx=0, ny=1),
+                       theta_deg=45.0, steps=120)
+    raise KeyError(name)
+
+
+def run_case(name, steps=None, with_angle=False):
+    case = case_by_name(name)
+    steps = case.steps if steps is None else steps
+    o = oracle.Oracle(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
+                      **case.physical())
+    for d in case.droplets:
+        o.init_droplet(*d)
+    o.step(steps)
+    phi, u, p = o.get()
+    out = dict(phi=phi, u=u, p=p, mass=o.mass(), steps=steps)
+    if with_angle:
+        w = dict(case.wall, exclude=1.5 * case.W)
+        th, circ, n = oracle.contact_angle(phi, o.geometry()["cls"], w)
+        out.update(theta=th, circle=circ, npts=n)
+    return out
+
+
+def geometry_of(name_or_mask):
+    solid = case_by_name(name_or_mask).solid if isinstance(name_or_mask, str) else name_or_mask
+    o = oracle.Oracle(solid)
+    return o.geometry()
+
+
+def window_run(case_name_kwargs, x_centre, half, steps):
+    """Run the oracle on a full-height window [x_centre - half, x_centre + half]
+    of a large case, built from the same generator, for `steps` steps. Nodes
+    farther than 2 * steps + 1 from the window edges do not feel the wrong
+    periodic wrap of the window, so the centre column equals the full run."""
+    case = wl.many_droplets_flat(**case_name_kwargs)
+    nx_full = case.nx
+    xs = (np.arange(x_centre - half, x_centre + half + 1)) % nx_full
+    solid = case.solid[:, xs]
+    tf = case.theta_field[:, xs] if case.theta_field is not None else None
+    o = oracle.Oracle(solid, theta_deg=case.theta_deg, theta_field=tf, **case.physical())
+    ny = case.ny
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, len(xs)))
+    x = np.broadcast_to(xs[None, :].astype(float), y.shape)
+    phi0 = None
+    for (x0, y0, R) in case.droplets:
+        # Eq. initialphi with the period of the full lattice, max over droplets
+        phi0 = oracle.droplet_phi(x, y, x0, y0, R, case.W, nx_full, out=phi0)
+    o.init_phi(phi0)
+    o.step(steps)
+    phi, u, p = o.get()
+    return dict(phi=phi[:, half], u=u[:, half], p=p[:, half])

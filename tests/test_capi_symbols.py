@@ -1,0 +1,37 @@
+"""The C-ABI library builds for sm_103a and exports every declared symbol
+(no GPU needed: nothing is called that touches the device)."""
+import ctypes
+
+from paper_2312_00369_gb300 import build as libbuild
+from paper_2312_00369_gb300 import pflbm
+
+
+def test_library_builds_and_exports_header():
+    path = libbuild.build()
+    L = ctypes.CDLL(path)
+    names = pflbm.declared_functions()
+    assert "pflbm_create" in names and "pflbm_step" in names and "pflbm_get" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding declares a signature for every header function
+    assert set(names) <= set(pflbm._SIGS)
+
+
+def test_host_only_entry_points():
+    L = pflbm.lib()
+    cx, cy = pflbm.pflbm_lattice()
+    assert cx[0] == 0 and cy[0] == 0
+    vecs = set(zip(cx.tolist(), cy.tolist()))
+    assert vecs == {(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)}
+    # footprint grows with the lattice and the storage precision
+    f64 = pflbm.pflbm_footprint_bytes(128, 64, "fp64")
+    f32 = pflbm.pflbm_footprint_bytes(128, 64, "fp32")
+    assert f64 > f32 > 0
+    assert pflbm.pflbm_footprint_bytes(256, 64, "fp32") > f32
+    # argument checks that fail before any CUDA call
+    h = pflbm._H()
+    P = pflbm.Params()
+    L.pflbm_params_default(ctypes.byref(P))
+    assert L.pflbm_create_ex(ctypes.byref(h), ctypes.byref(P)) == pflbm.EINVAL
+    assert L.pflbm_step(None, 1) == pflbm.EINVAL
+    assert b"NULL handle" in L.pflbm_last_error()

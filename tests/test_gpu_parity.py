@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: node classes and link masks bit-exact; phi within 1e-10 in FP64 mode
+and 1e-5 in FP32 mode after the stated steps (the tolerances the method's
+target states); u and p within bounds derived from the same arithmetic.
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from tests import oracle_jobs as oj
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": dict(phi=1e-10, u=1e-12, p=1e-12), "fp32": dict(phi=1e-5, u=1e-6, p=1e-6)}
+
+# oracle jobs started before the first GPU call, in spawned workers
+_JOBS = {
+    "flat60": (oj.run_case, ("flat60", None, True)),
+    "flat60_short": (oj.run_case, ("flat60_short",)),
+    "incline30": (oj.run_case, ("incline30",)),
+    "incline45_ragged": (oj.run_case, ("incline45_ragged",)),
+    "cylinder": (oj.run_case, ("cylinder",)),
+    "crop": (oj.run_case, ("crop",)),
+    "tiny": (oj.run_case, ("tiny",)),
+    "block": (oj.run_case, ("block",)),
+}
+FULL = dict(nx=4096, ny=2048, n_drops=64, seed=2312)
+WIN_STEPS, WIN_HALF = 12, 40
+WIN_X = [0, 1000, 2047, 3333, 4095]
+for _x in WIN_X:
+    _JOBS[f"win{_x}"] = (oj.window_run, (FULL, _x, WIN_HALF, WIN_STEPS))
+
+_pool = None
+_futures = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def oracle_pool():
+    """Start the oracle jobs in spawned workers; they overlap the GPU tests."""
+    global _pool
+    _pool = mp.get_context("spawn").Pool(processes=min(len(_JOBS), 12))
+    for k, (fn, args) in _JOBS.items():
+        _futures[k] = _pool.apply_async(fn, args)
+    yield
+    _pool.terminate()
+
+
+def ref(name):
+    return _futures[name].get(timeout=1800)
+
+
+def solver(case, precision, init=True):
+    from paper_2312_00369_gb300.pflbm import Solver
+    s = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
+               precision=precision, **case.physical())
+    if init:
+        for d in case.droplets:
+            s.init_droplet(*d)
+    return s
+
+
+def compare(name, precision, steps=None):
+    case = oj.case_by_name(name)
+    r = ref(name)
+    s = solver(case, precision)
+    s.step(r["steps"] if steps is None else steps)
+    phi, u, p = s.get()
+    t = TOL[precision]
+    dphi = np.max(np.abs(phi - r["phi"]))
+    du = np.max(np.abs(u - r["u"]))
+    dp = np.max(np.abs(p - r["p"]))
+    assert dphi <= t["phi"], (name, precision, dphi)
+    assert du <= t["u"], (name, precision, du)
+    assert dp <= t["p"], (name, precision, dp)
+    return s, phi
+
+
+# ---------------------------------------------------------------- geometry --
+def _links_by_vector(mask_bits, cx, cy):
+    out = {}
+    for i in range(1, 9):
+        out[(int(cx[i]), int(cy[i]))] = (mask_bits >> i) & 1
+    return out
+
+
+@pytest.mark.parametrize("name", ["flat60", "incline30", "incline45_ragged", "cylinder", "block",
+                                  "tiny", "crop"])
+def test_geometry_bit_exact(name):
+    import oracle
+    from paper_2312_00369_gb300.pflbm import Solver, pflbm_lattice
+    case = oj.case_by_name(name)
+    g_or = oj.geometry_of(name)
+    s = Solver(case.solid, precision="fp64")
+    g = s.geometry()
+    assert np.array_equal(g["cls"], g_or["cls"])
+    ocx, ocy, _, _ = oracle.lattice()
+    gcx, gcy = pflbm_lattice()
+    a = _links_by_vector(g["unknown"], gcx, gcy)
+    b = _links_by_vector(g_or["unknown"], ocx, ocy)
+    for v in a:
+        assert np.array_equal(a[v], b[v]), v
+    a = _links_by_vector(g["doubly"], gcx, gcy)
+    b = _links_by_vector(g_or["doubly"], ocx, ocy)
+    for v in a:
+        assert np.array_equal(a[v], b[v]), v
+    assert np.allclose(g["av"], g_or["av"], rtol=2e-16, atol=0)
+
+
+def test_random_masks_bit_exact():
+    from paper_2312_00369_gb300.pflbm import Solver
+    rng = np.random.default_rng(11)
+    for trial in range(4):
+        nx, ny = int(rng.integers(20, 90)), int(rng.integers(12, 60))
+        solid = (rng.random((ny, nx)) < 0.35).astype(np.uint8)
+        solid[:2] = 1
+        solid[-2:] = 1
+        g = Solver(solid, precision="fp32").geometry()
+        assert np.array_equal(g["cls"], oj.geometry_of(solid)["cls"])
+
+
+# ------------------------------------------------------------------ parity --
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_flat_wall_full_steps(precision):
+    # 100 x 50, R = 20, theta = 60 deg, 5000 steps
+    compare("flat60", precision)
+
+
+@pytest.mark.parametrize("name", ["incline30", "incline45_ragged", "cylinder", "tiny", "block",
+                                  "crop"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_parity_cases(name, precision):
+    compare(name, precision)
+
+
+def test_full_size_many_droplets_sampled_columns():
+    # 4096 x 2048, 64 droplets, per-node theta, FP32, the benchmark's launch
+    # configuration: columns compared with oracle windows of the same input
+    from paper_2312_00369_gb300 import workloads as wl
+    case = wl.many_droplets_flat(**FULL)
+    s = solver(case, "fp32")
+    s.step(WIN_STEPS)
+    phi, u, p = s.get()
+    for x in WIN_X:
+        r = ref(f"win{x}")
+        assert np.max(np.abs(phi[:, x] - r["phi"])) <= 1e-5
+        assert np.max(np.abs(u[:, x] - r["u"])) <= 1e-6
+        assert np.max(np.abs(p[:, x] - r["p"])) <= 1e-6
+
+
+# ---------------------------------------------------------- diagnostics --
+def test_mass_and_contact_angle_fp64():
+    case = oj.case_by_name("flat60")
+    r = ref("flat60")
+    s = solver(case, "fp64")
+    s.step(r["steps"])
+    assert abs(s.mass() - r["mass"]) <= 1e-12 * abs(r["mass"])
+    th, circ, n = s.contact_angle(case.wall)
+    assert n == r["npts"]
+    assert abs(th - r["theta"]) < 1e-6
+    assert np.allclose(circ, r["circle"], atol=1e-6)
+
+
+def test_contact_angle_fp32_within_half_degree():
+    case = oj.case_by_name("flat60")
+    r = ref("flat60")
+    s = solver(case, "fp32")
+    s.step(r["steps"])
+    th, _, _ = s.contact_angle(case.wall)
+    assert abs(th - r["theta"]) < 0.5
+    assert abs(s.mass() - r["mass"]) <= 1e-5 * abs(r["mass"])
+
+
+# ------------------------------------------------------------ host paths --
+def test_save_load_continues_bit_exact():
+    case = oj.case_by_name("flat60_short")
+    a = solver(case, "fp32")
+    a.step(100)
+    blob = a.save()
+    a.step(50)
+    pa, ua, qa = a.get()
+    b = solver(case, "fp32")
+    b.load(blob)
+    assert b.steps == 100
+    b.step(50)
+    pb, ub, qb = b.get()
+    assert np.array_equal(pa, pb) and np.array_equal(ua, ub) and np.array_equal(qa, qb)
+
+
+def test_nan_is_reported():
+    from paper_2312_00369_gb300.pflbm import PflbmError, ENUMERIC
+    case = oj.case_by_name("flat60_short")
+    s = solver(case, "fp32")
+    phi = np.zeros((case.ny, case.nx))
+    phi[25, 50] = np.nan                  # poisoned on the host
+    s.init_phi(phi)
+    s.step(3)
+    with pytest.raises(PflbmError) as e:
+        s.check()
+    assert e.value.code == ENUMERIC
+
+
+def test_bad_mask_and_arguments():
+    from paper_2312_00369_gb300.pflbm import PflbmError, Solver, EBADMASK, EINVAL
+    solid = np.zeros((20, 30), np.uint8)
+    with pytest.raises(PflbmError) as e:
+        Solver(solid)
+    assert e.value.code == EBADMASK
+    solid[:2] = 1
+    solid[-2:] = 1
+    with pytest.raises(PflbmError) as e:
+        Solver(solid, tau_f=0.4)
+    assert e.value.code == EINVAL
+
+
+def test_repeated_init_and_steps_match_oracle():
+    import oracle
+    case = oj.case_by_name("flat60_short")
+    s = solver(case, "fp64", init=False)
+    o = oracle.Oracle(case.solid, theta_deg=case.theta_deg, **case.physical())
+    for obj in (s, o):
+        obj.init_droplet(30, 0.5, 10)
+        obj.init_droplet(70, 0.5, 12)      # pointwise max
+        obj.step(20)
+        obj.init_droplet(50, 0.5, 15)      # replaces after a step
+        obj.step(30)
+    ps, us, qs = s.get()
+    po, uo, qo = o.get()
+    assert np.max(np.abs(ps - po)) <= 1e-12 and np.max(np.abs(us - uo)) <= 1e-13
