@@ -84,7 +84,7 @@ void dfree(pflbm_t* h, void* p, size_t bytes)
 int pitch_of(int nx) { return (nx + 63) / 64 * 64; }
 
 struct Sizes {
-    size_t N, pop, sprev, wet, red, pts;
+    size_t N, pop, sprev, wet, red, pts, tiles;
     int pts_cap;
 };
 
@@ -102,13 +102,17 @@ Sizes sizes_of(int nx, int ny, int precision)
     if (cap > (1 << 22)) cap = 1 << 22;
     s.pts_cap = (int)cap;
     s.pts = (size_t)s.pts_cap * 2 * sizeof(double);
+    s.tiles = (size_t)tiles_x(nx) * tiles_y(ny);
     return s;
 }
 
 bool valid_params(const pflbm_params_t* p, std::string& why)
 {
     if (p->nx < 3 || p->ny < 5) { why = "nx must be >= 3 and ny >= 5"; return false; }
-    if ((long long)p->nx * p->ny > (1LL << 31)) { why = "lattice too large"; return false; }
+    if (18LL * p->ny * ((p->nx + 63) / 64 * 64) >= (1LL << 31)) {
+        why = "lattice too large (18 * ny * padded nx must stay below 2^31)";
+        return false;
+    }
     if (!p->solid_mask) { why = "solid_mask is NULL"; return false; }
     if (!(p->W > 0) || !(p->M > 0) || !(p->tau_f > 0.5) || !(p->rho_l > 0) || !(p->rho_g > 0) ||
         !(p->sigma >= 0) || !std::isfinite(p->theta_deg)) {
@@ -131,6 +135,7 @@ void release(pflbm_t* h)
     DeviceGuard g(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     dfree(h, h->cls, s.N);
+    dfree(h, h->tiles, s.tiles);
     dfree(h, h->solid, s.N);
     dfree(h, h->theta, s.N * sizeof(float));
     dfree(h, h->wet, s.wet);
@@ -166,6 +171,17 @@ int read_status(pflbm_t* h)
 int post_status_copy(pflbm_t* h)
 {
     CK(cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    return PFLBM_OK;
+}
+
+// Build the populations from phi0 once after one or more initialisations.
+int materialize(pflbm_t* h)
+{
+    if (!h->init_pending) return PFLBM_OK;
+    CK(launch_init_populations(h));
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    if (h->hstatus) h->hstatus[0] = 0;
+    h->init_pending = false;
     return PFLBM_OK;
 }
 
@@ -227,7 +243,7 @@ size_t pflbm_footprint_bytes(int nx, int ny, int precision)
 {
     if (nx < 1 || ny < 1) return 0;
     Sizes s = sizes_of(nx, ny, precision);
-    return 2 * s.pop + s.sprev + s.wet + s.N * (1 + 1 + 8 + 8 + 8) + s.red + s.pts + 16 +
+    return 2 * s.pop + s.sprev + s.wet + s.N * (1 + 1 + 8 + 8 + 8) + s.red + s.pts + s.tiles + 16 +
            (size_t)nx * ny * 4 * sizeof(double);
 }
 
@@ -294,6 +310,7 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
         h->field = (decltype(h->field))p;                     \
     } while (0)
     ALLOC(cls, s.N);
+    ALLOC(tiles, s.tiles);
     ALLOC(solid, s.N);
     ALLOC(wet, s.wet);
     ALLOC(av, s.N * sizeof(double));
@@ -331,6 +348,7 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
         CKR(cudaMemcpy2DAsync(h->theta, h->pitch * sizeof(float), prm->theta_field_deg, nx * sizeof(float),
                               nx * sizeof(float), ny, cudaMemcpyHostToDevice, h->stream));
     CKR(launch_classify(h));
+    CKR(launch_tile_flags(h));
     CKR(launch_wet(h));
     CKR(cudaStreamSynchronize(h->stream));
 #undef CKR
@@ -384,9 +402,7 @@ int pflbm_init_droplet(pflbm_t* h, double x0, double y0, double R)
     DeviceGuard g(h->device);
     CK(launch_init_phi_droplet(h, x0, y0, R, h->replace_phi ? 1 : 0));
     h->replace_phi = false;
-    CK(launch_init_populations(h));
-    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
-    if (h->hstatus) h->hstatus[0] = 0;
+    h->init_pending = true;   // populations are built by the next call that needs them
     h->steps = 0;
     return PFLBM_OK;
 }
@@ -399,10 +415,8 @@ int pflbm_init_phi(pflbm_t* h, const double* phi)
     CK(cudaMemcpy2DAsync(h->phi0, h->pitch * sizeof(double), phi, h->nx * sizeof(double), h->nx * sizeof(double),
                          h->ny, cudaMemcpyHostToDevice, h->stream));
     h->replace_phi = false;
-    CK(launch_init_populations(h));
-    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    h->init_pending = true;
     CK(cudaStreamSynchronize(h->stream));   // phi is a caller buffer: done with it on return
-    if (h->hstatus) h->hstatus[0] = 0;
     h->steps = 0;
     return PFLBM_OK;
 }
@@ -413,6 +427,7 @@ int pflbm_step(pflbm_t* h, int64_t n)
     if (n < 0) return fail(PFLBM_EINVAL, "negative step count");
     if (int rc = read_status(h)) return rc;
     DeviceGuard g(h->device);
+    if (int rc = materialize(h)) return rc;
     for (int64_t t = 0; t < n; ++t) {
         CK(launch_step(h));
         h->steps += 1;
@@ -428,6 +443,7 @@ int pflbm_get_device(pflbm_t* h, double* phi, double* u, double* p)
 {
     if (int rc = check_handle(h)) return rc;
     DeviceGuard g(h->device);
+    if (int rc = materialize(h)) return rc;
     CK(launch_macro(h, phi, u, p));
     return PFLBM_OK;
 }
@@ -436,6 +452,7 @@ int pflbm_get(pflbm_t* h, double* phi, double* u, double* p)
 {
     if (int rc = check_handle(h)) return rc;
     DeviceGuard g(h->device);
+    if (int rc = materialize(h)) return rc;
     if (int rc = ensure_out(h)) return rc;
     size_t N = (size_t)h->nx * h->ny;
     double* dphi = h->out;
@@ -454,6 +471,7 @@ int pflbm_mass(pflbm_t* h, double* out)
     if (int rc = check_handle(h)) return rc;
     if (!out) return fail(PFLBM_EINVAL, "NULL out");
     DeviceGuard g(h->device);
+    if (int rc = materialize(h)) return rc;
     double* d = h->red + mass_scratch_doubles() - 8;
     CK(launch_mass(h, d));
     CK(cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -468,6 +486,7 @@ int pflbm_contact_angle(pflbm_t* h, const pflbm_wall_t* wall, double* theta_deg,
     if (wall->type != 0 && wall->type != 1) return fail(PFLBM_EINVAL, "wall type must be 0 or 1");
     if (wall->type == 1 && !(wall->r > 0)) return fail(PFLBM_EINVAL, "circular wall needs r > 0");
     DeviceGuard g(h->device);
+    if (int rc = materialize(h)) return rc;
     if (int rc = ensure_out(h)) return rc;
     double* dphi = h->out;
     double* dres = h->out + 3 * (size_t)h->nx * h->ny;   // the p slot, unused here
@@ -545,6 +564,7 @@ int pflbm_save(pflbm_t* h, void* buf, size_t* len)
     if (!buf) { *len = need; return PFLBM_OK; }
     if (*len < need) { *len = need; return fail(PFLBM_EINVAL, "buffer too small"); }
     DeviceGuard g(h->device);
+    if (int rc = materialize(h)) return rc;
     Blob b{};
     b.magic = kMagic;
     b.version = 1;
@@ -583,6 +603,7 @@ int pflbm_load(pflbm_t* h, const void* buf, size_t len)
     CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (h->hstatus) h->hstatus[0] = 0;
+    h->init_pending = false;
     h->steps = b.steps;
     h->replace_phi = b.replace_phi != 0;
     return PFLBM_OK;

@@ -40,7 +40,11 @@ template <typename S>
 __device__ double pulled(const S* __restrict__ base, const uint8_t* __restrict__ cls, int i, int x, int y,
                          int nx, int pitch, size_t plane)
 {
-    if (i == 0) return (double)base[(size_t)y * pitch + x];
+    if (i == 0) {
+        if (sizeof(S) == 4)  // FP32 mode: g_0 is fixed point, 2^-30
+            return (double)reinterpret_cast<const int32_t*>(base)[(size_t)y * pitch + x] * (1.0 / 1073741824.0);
+        return (double)base[(size_t)y * pitch + x];
+    }
     const int X = cx(i), Y = cy(i), O = opp(i);
     size_t src = (size_t)(y - Y) * pitch + wrap1(x - X, nx);
     if (zeta_of(cls[src])) return (double)base[i * plane + src];

@@ -125,9 +125,38 @@ __global__ void k_links(const uint8_t* __restrict__ cls, uint16_t* __restrict__ 
     if (doubly) doubly[o] = db;
 }
 
+// Per step tile: 1 when every node within two nodes of the tile (x periodic)
+// exists and is a fluid node, so the step can skip the class tile, the
+// bounce-back checks, the ghost fill and the wetting term there. Needs
+// nx >= 2 TX so that one wrap covers the tile's halo.
+__global__ void k_tile_flags(const uint8_t* __restrict__ cls, uint8_t* __restrict__ tiles, int nx, int ny,
+                             int pitch, int ntx, int nty)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntx * nty) return;
+    int bx = t % ntx, by = t / ntx;
+    int x0 = bx * TX, y0 = by * TY;
+    uint8_t ok = (nx >= 2 * TX) ? 1 : 0;
+    for (int y = y0 - 2; ok && y < y0 + TY + 2; ++y) {
+        if (y < 0 || y >= ny) { ok = 0; break; }
+        for (int x = x0 - 2; x < x0 + TX + 2; ++x) {
+            int xx = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+            if ((cls[(size_t)y * pitch + xx] & CLS_MASK) != CLS_FLUID) { ok = 0; break; }
+        }
+    }
+    tiles[t] = ok;
+}
+
 dim3 grid2d(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
 }  // namespace
+
+cudaError_t launch_tile_flags(pflbm_t* h)
+{
+    int ntx = tiles_x(h->nx), nty = tiles_y(h->ny), n = ntx * nty;
+    k_tile_flags<<<(n + 127) / 128, 128, 0, h->stream>>>(h->cls, h->tiles, h->nx, h->ny, h->pitch, ntx, nty);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_classify(pflbm_t* h)
 {

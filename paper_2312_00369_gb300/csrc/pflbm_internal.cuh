@@ -58,6 +58,7 @@ struct pflbm {
     void* alloc_ctx = nullptr;
     // device buffers (sizes: N = ny*pitch nodes)
     uint8_t* cls = nullptr;       // node byte [N]
+    uint8_t* tiles = nullptr;     // per step tile: 1 = all nodes within 2 are fluid
     uint8_t* solid = nullptr;     // user mask [N]
     float* theta = nullptr;       // angle field [N] (degrees)
     void* wet = nullptr;          // a_v sqrt(2 kappa beta) cos(theta) [N] (FP64 or FP32)
@@ -75,6 +76,7 @@ struct pflbm {
     int* hstatus = nullptr;       // pinned host mirror
     int cur = 0;                  // which pop buffer holds the current state
     bool replace_phi = true;
+    bool init_pending = false;    // phi0 set, populations not yet built
     int64_t steps = 0;
     size_t bytes_allocated = 0;
     cudaEvent_t status_ev = nullptr;
@@ -89,6 +91,9 @@ size_t pop_bytes(int ny, int pitch, int precision);   // one of f or g, one copy
 cudaError_t launch_classify(pflbm_t* h);
 cudaError_t launch_wet(pflbm_t* h);
 cudaError_t launch_links(pflbm_t* h, uint16_t* unknown, uint16_t* doubly);
+cudaError_t launch_tile_flags(pflbm_t* h);
+inline int tiles_x(int nx) { return (nx + TX - 1) / TX; }
+inline int tiles_y(int ny) { return (ny + TY - 1) / TY; }
 
 // step.cu
 cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, int replace);

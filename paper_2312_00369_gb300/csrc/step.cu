@@ -18,6 +18,15 @@
 // F = mu grad(phi), u and p (Sec. 2.1.2), collides f (Eqs. BGK-NS, feq_i, Siu,
 // GGi) and g (Eqs. BGK, H_i, F_i with (1/2) dG/dt as a backward difference)
 // and stores f*, g* and the new u.grad(phi) history.
+//
+// g_0 carries phi (it is O(1) while every other population is O(alpha mu)),
+// so rounding it on every store is what limits a 32-bit state: in the FP32
+// mode it is kept as a 32-bit fixed-point number q = g_0 2^30 (|g_0| < 2,
+// resolution 9.3e-10) and advanced by integer addition of the collision
+// increment g*_0 - g_0 = (g_0^eq - g_0)/tau_g + (3/2 G_0(t) - 1/2 G_0(t-1)),
+// where g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu holds no O(1) term.
+#include <climits>
+
 #include "pflbm_internal.cuh"
 
 namespace pfk {
@@ -26,15 +35,38 @@ namespace {
 __device__ __forceinline__ int wrap1(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
 __device__ __forceinline__ int wrapn(int x, int nx) { int r = x % nx; return r < 0 ? r + nx : r; }
 
+// Storage of g_0 (see the note at the top of the file).
+template <typename S> struct G0;
+template <> struct G0<double> {
+    using T = double;
+    __device__ static double value(T raw) { return raw; }
+    __device__ static T add(T raw, double d, int*) { return raw + d; }
+    static T from_double(double v) { return v; }
+};
+template <> struct G0<float> {
+    using T = int32_t;
+    __device__ static float value(T raw) { return (float)raw * (1.0f / 1073741824.0f); }
+    __device__ static T add(T raw, float d, int* status)
+    {
+        long long q = (long long)raw + __float2ll_rn(d * 1073741824.0f);
+        if (q > INT_MAX || q < -INT_MAX) {
+            atomicOr(status, 2);
+            q = q > 0 ? INT_MAX : -INT_MAX;
+        }
+        return (T)q;
+    }
+};
+
 template <typename S, typename C>
 struct StepArgs {
     const uint8_t* cls;
+    const uint8_t* tiles;  // per tile: 1 when every node within 2 of it is fluid
     const C* wet;
     const S* fin;   // 18 planes
     S* fout;        // 18 planes
     S* sprev;
     int nx, ny, pitch;
-    size_t plane;
+    int plane;      // 18 * plane < 2^31 (checked at create)
     C beta4, kappa, rho_g, drho, omega_f, omega_g, force_pre, alpha;
     int* status;
     // macroscopic output (read-back kernel only), dense [ny][nx]
@@ -44,25 +76,26 @@ struct StepArgs {
 };
 
 // Pull of direction i at node (gx, gy), whose class byte sits at s_cls[sy][sx].
+// CHECK = false: every neighbour is a zeta = 1 node (s_cls is not read).
 template <int I, typename S, typename C, bool CHECK>
 __device__ __forceinline__ C pull(const S* __restrict__ base, const uint8_t (*s_cls)[TX + 6], int sy,
-                                  int sx, int gx, int gy, int nx, int pitch, size_t plane)
+                                  int sx, int gx, int gy, int nx, int pitch, int plane)
 {
     constexpr int X = cx(I), Y = cy(I), O = opp(I);
     if (!CHECK || zeta_of(s_cls[sy - Y][sx - X])) {
-        return (C)base[I * plane + (size_t)(gy - Y) * pitch + wrap1(gx - X, nx)];
+        return (C)base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)];
     }
     if (zeta_of(s_cls[sy + Y][sx + X])) {
-        return (C)base[O * plane + (size_t)(gy + Y) * pitch + wrap1(gx + X, nx)];
+        return (C)base[O * plane + (gy + Y) * pitch + wrap1(gx + X, nx)];
     }
-    return (C)base[O * plane + (size_t)gy * pitch + gx];
+    return (C)base[O * plane + gy * pitch + gx];
 }
 
 template <typename S, typename C, bool CHECK>
 __device__ __forceinline__ void pull_all(C v[9], const S* __restrict__ base, const uint8_t (*s_cls)[TX + 6],
-                                         int sy, int sx, int gx, int gy, int nx, int pitch, size_t plane)
+                                         int sy, int sx, int gx, int gy, int nx, int pitch, int plane)
 {
-    v[0] = (C)base[(size_t)gy * pitch + gx];
+    v[0] = (C)base[gy * pitch + gx];
     v[1] = pull<1, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     v[2] = pull<2, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     v[3] = pull<3, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
@@ -73,23 +106,87 @@ __device__ __forceinline__ void pull_all(C v[9], const S* __restrict__ base, con
     v[8] = pull<8, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
 }
 
-template <typename S, typename C>
-__device__ __forceinline__ C pulled_phi(const S* __restrict__ gbase, const uint8_t (*s_cls)[TX + 6], int sy,
-                                        int sx, int gx, int gy, int nx, int pitch, size_t plane)
+// Pulled g at a node: g_0 raw (storage form) and its value, g_1..g_8.
+template <typename S, typename C, bool CHECK>
+__device__ __forceinline__ void pull_g(C v[9], typename G0<S>::T& raw0, const S* __restrict__ gbase,
+                                       const uint8_t (*s_cls)[TX + 6], int sy, int sx, int gx, int gy, int nx,
+                                       int pitch, int plane)
 {
-    C v[9];
-    if (s_cls[sy][sx] & F_LINK)
-        pull_all<S, C, true>(v, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    else
-        pull_all<S, C, false>(v, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+    raw0 = reinterpret_cast<const typename G0<S>::T*>(gbase)[gy * pitch + gx];
+    v[0] = (C)G0<S>::value(raw0);
+    v[1] = pull<1, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[2] = pull<2, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[3] = pull<3, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[4] = pull<4, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[5] = pull<5, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[6] = pull<6, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[7] = pull<7, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[8] = pull<8, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
 }
 
-// Common prologue: class tile (halo 3), phi tile (halo 2) with ghost values.
-// Returns the own node's pulled g in gown[] when it is a zeta = 1 node.
+template <typename C>
+__device__ __forceinline__ C sum_moving(const C v[9])
+{
+    return ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
+}
+
+// phi = sum_i g_i (Eq. order-parameter), in one fixed order everywhere.
+template <typename C>
+__device__ __forceinline__ C phi_of(const C v[9]) { return v[0] + sum_moving(v); }
+
+template <typename S, typename C>
+__device__ __forceinline__ C pulled_phi(const S* __restrict__ gbase, const uint8_t (*s_cls)[TX + 6], int sy,
+                                        int sx, int gx, int gy, int nx, int pitch, int plane)
+{
+    C v[9];
+    typename G0<S>::T raw0;
+    if (s_cls[sy][sx] & F_LINK)
+        pull_g<S, C, true>(v, raw0, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    else
+        pull_g<S, C, false>(v, raw0, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    return phi_of(v);
+}
+
+// Prologue of a tile whose nodes within two of it are all fluid: no class
+// tile, no bounce-back checks, no ghosts, phi on a one-node ring.
+template <typename S, typename C>
+__device__ __forceinline__ void tile_prologue_fluid(const StepArgs<S, C>& a, C (*s_phi)[TX + 4], int x0, int y0,
+                                                    C gown[9], typename G0<S>::T& raw0)
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
+    const int nx = a.nx, pitch = a.pitch, plane = a.plane;
+    const S* gbase = a.fin + 9 * plane;
+    {
+        const int gx = wrap1(x0 + tx, nx), gy = y0 + ty;
+        pull_g<S, C, false>(gown, raw0, gbase, nullptr, 0, 0, gx, gy, nx, pitch, plane);
+        s_phi[ty + 2][tx + 2] = phi_of(gown);
+    }
+    // ring: top row, bottom row (TX + 2 each), left and right columns (TY each)
+    constexpr int RT = TX + 2, NR = 2 * (TX + 2) + 2 * TY;
+    if (tid < NR) {
+        int py, px;
+        if (tid < RT) { py = 1; px = 1 + tid; }
+        else if (tid < 2 * RT) { py = TY + 2; px = 1 + tid - RT; }
+        else if (tid < 2 * RT + TY) { py = 2 + tid - 2 * RT; px = 1; }
+        else { py = 2 + tid - 2 * RT - TY; px = TX + 2; }
+        const int gy = y0 - 2 + py, gx = wrap1(x0 - 2 + px, nx);
+        C v[9];
+        typename G0<S>::T r;
+        pull_g<S, C, false>(v, r, gbase, nullptr, 0, 0, gx, gy, nx, pitch, plane);
+        s_phi[py][px] = phi_of(v);
+    }
+    __syncthreads();
+}
+
+// Common prologue: class tile (halo 3) and phi tile with ghost values. A
+// tile needs phi two nodes out only when a ghost node lies next to one of its
+// nodes (the ghost average reaches one node further); otherwise one ring.
+// Returns the own node's pulled g (and raw g_0) when it is a zeta = 1 node.
 template <typename S, typename C>
 __device__ __forceinline__ void tile_prologue(const StepArgs<S, C>& a, uint8_t (*s_cls)[TX + 6],
-                                              C (*s_phi)[TX + 4], int x0, int y0, C gown[9])
+                                              C (*s_phi)[TX + 4], int x0, int y0, C gown[9],
+                                              typename G0<S>::T& raw0)
 {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
@@ -99,27 +196,34 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<S, C>& a, uint8_t (
     for (int p = tid; p < (TY + 6) * (TX + 6); p += TX * TY) {
         int py = p / (TX + 6), px = p - py * (TX + 6);
         int gy = y0 - 3 + py, gx = wrapn(x0 - 3 + px, nx);
-        s_cls[py][px] = (gy < 0 || gy >= ny) ? (uint8_t)CLS_OUT : a.cls[(size_t)gy * pitch + gx];
+        s_cls[py][px] = (gy < 0 || gy >= ny) ? (uint8_t)CLS_OUT : a.cls[gy * pitch + gx];
     }
     __syncthreads();
+    const uint8_t own = s_cls[ty + 3][tx + 3];
+    // halo 2 when a node of the tile reads a ghost value: a zeta = 1 node next
+    // to a ghost, or a ghost node itself (its value is part of the read-back)
+    const bool near_ghost = (y0 + ty < ny) && own != CLS_OUT &&
+                            ((zeta_of(own) && (own & F_NEARGHOST)) || (own & CLS_MASK) == CLS_GHOST);
+    const int halo = __syncthreads_or(near_ghost) ? 2 : 1;
 
     // own node (a tile that runs past x = nx - 1 holds wrapped nodes there:
     // they are computed like halo nodes but not collided)
     {
         int gx = wrapn(x0 + tx, nx), gy = y0 + ty;
         C ph = C(0);
-        if (gy < ny && zeta_of(s_cls[ty + 3][tx + 3])) {
-            if (s_cls[ty + 3][tx + 3] & F_LINK)
-                pull_all<S, C, true>(gown, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+        if (gy < ny && zeta_of(own)) {
+            if (own & F_LINK)
+                pull_g<S, C, true>(gown, raw0, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
             else
-                pull_all<S, C, false>(gown, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
-            ph = ((gown[0] + gown[1]) + (gown[2] + gown[3])) + ((gown[4] + gown[5]) + (gown[6] + gown[7])) + gown[8];
+                pull_g<S, C, false>(gown, raw0, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+            ph = phi_of(gown);
         }
         s_phi[ty + 2][tx + 2] = ph;
     }
-    // halo ring of width 2
-    for (int p = tid; p < (TY + 4) * (TX + 4); p += TX * TY) {
-        int py = p / (TX + 4), px = p - py * (TX + 4);
+    // halo ring
+    const int lo = 2 - halo, wy = TY + 2 * halo, wx = TX + 2 * halo;
+    for (int p = tid; p < wy * wx; p += TX * TY) {
+        int py = p / wx + lo, px = p % wx + lo;
         if (py >= 2 && py < TY + 2 && px >= 2 && px < TX + 2) continue;
         int sy = py + 1, sx = px + 1;
         C ph = C(0);
@@ -130,6 +234,7 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<S, C>& a, uint8_t (
         s_phi[py][px] = ph;
     }
     __syncthreads();
+    if (halo == 1) return;
 
     // ghost nodes within one node of the tile: zeta-weighted 3x3 mean
     for (int p = tid; p < (TY + 2) * (TX + 2); p += TX * TY) {
@@ -168,16 +273,21 @@ __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<S, C> a)
     __shared__ C s_phi[TY + 4][TX + 4];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     C g[9];
-    tile_prologue<S, C>(a, s_cls, s_phi, x0, y0, g);
+    typename G0<S>::T g0raw;
+    const bool fluid_tile = a.tiles[blockIdx.y * gridDim.x + blockIdx.x] != 0;
+    if (fluid_tile)
+        tile_prologue_fluid<S, C>(a, s_phi, x0, y0, g, g0raw);
+    else
+        tile_prologue<S, C>(a, s_cls, s_phi, x0, y0, g, g0raw);
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx >= a.nx || gy >= a.ny) return;
-    const uint8_t code = s_cls[ty + 3][tx + 3];
-    const size_t k = (size_t)gy * a.pitch + gx;
+    const uint8_t code = fluid_tile ? (uint8_t)CLS_FLUID : s_cls[ty + 3][tx + 3];
+    const int k = gy * a.pitch + gx;
     if (!zeta_of(code)) {
         if (!COLLIDE) {
-            size_t o = (size_t)gy * a.nx + gx;
+            const size_t o = (size_t)gy * a.nx + gx;
             if (a.o_phi) a.o_phi[o] = (double)s_phi[ty + 2][tx + 2];
             if (a.o_u) { a.o_u[2 * o] = 0.0; a.o_u[2 * o + 1] = 0.0; }
             if (a.o_p) a.o_p[o] = 0.0;
@@ -209,9 +319,9 @@ __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<S, C> a)
     const C ux = (mx + C(0.5) * Fx) * inv_rho;
     const C uy = (my + C(0.5) * Fy) * inv_rho;
     const C uu = ux * ux + uy * uy;
-    const C sum_moving = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+    const C fsum = sum_moving(f);
     // p = c_s^2/(1 - w_0) [sum_{i!=0} f_i + u.grad(rho)/2 + rho s_0(u)], s_0 = -w_0 (3/2) u^2
-    const C p = C(0.6) * (sum_moving + C(0.5) * (ux * drx + uy * dry) - rho * (C(2) / C(3)) * uu);
+    const C p = C(0.6) * (fsum + C(0.5) * (ux * drx + uy * dry) - rho * (C(2) / C(3)) * uu);
 
     if (!COLLIDE) {
         size_t o = (size_t)gy * a.nx + gx;
@@ -248,8 +358,9 @@ __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<S, C> a)
     const C og = a.omega_g;
     S* go = a.fout + 9 * a.plane;
     {
-        const C geq0 = ph - (C(1) - wgt<C>(0)) * am;
-        go[k] = (S)(g[0] + og * (geq0 - g[0]) + wgt<C>(0) * C(-2) * src);
+        // g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu (Eq. H_i)
+        const C d0 = og * (sum_moving(g) - (C(1) - wgt<C>(0)) * am) + wgt<C>(0) * C(-2) * src;
+        reinterpret_cast<typename G0<S>::T*>(go)[k] = G0<S>::add(g0raw, d0, a.status);
     }
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -265,6 +376,7 @@ StepArgs<S, C> make_args(pflbm_t* h)
 {
     StepArgs<S, C> a{};
     a.cls = h->cls;
+    a.tiles = h->tiles;
     a.wet = (const C*)h->wet;
     a.fin = (const S*)h->pop[h->cur];
     a.fout = (S*)h->pop[h->cur ^ 1];
@@ -272,7 +384,7 @@ StepArgs<S, C> make_args(pflbm_t* h)
     a.nx = h->nx;
     a.ny = h->ny;
     a.pitch = h->pitch;
-    a.plane = (size_t)h->ny * h->pitch;
+    a.plane = h->ny * h->pitch;
     const Params& q = h->prm;
     a.beta4 = (C)(4.0 * q.beta);
     a.kappa = (C)q.kappa;
@@ -357,6 +469,14 @@ __global__ void k_init_mu(const uint8_t* __restrict__ cls, const C* __restrict__
     sprev[k] = (C)(ux * gpx + uy * gpy);
 }
 
+template <typename S> __device__ typename G0<S>::T g0_store(double v);
+template <> __device__ double g0_store<double>(double v) { return v; }
+template <> __device__ int32_t g0_store<float>(double v)
+{
+    double q = rint(v * 1073741824.0);
+    return (int32_t)fmax(-(double)INT_MAX, fmin((double)INT_MAX, q));
+}
+
 // Post-collision arrays that the first pull turns into f = 0, g = g^eq(phi0, mu0).
 template <typename S>
 __global__ void k_init_pop(const uint8_t* __restrict__ cls, const double* __restrict__ phi,
@@ -381,7 +501,10 @@ __global__ void k_init_pop(const uint8_t* __restrict__ cls, const double* __rest
         }
         double w = j == 0 ? 4.0 / 9.0 : (j <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
         double geq = (j == 0) ? phi[m] - (1.0 - w) * alpha * mu[m] : w * alpha * mu[m];
-        g[j * plane + k] = (S)geq;
+        if (j == 0)
+            reinterpret_cast<typename G0<S>::T*>(g)[k] = g0_store<S>(geq);
+        else
+            g[j * plane + k] = (S)geq;
     }
 }
 
