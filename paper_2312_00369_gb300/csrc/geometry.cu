@@ -97,9 +97,11 @@ __global__ void k_wet(const uint8_t* __restrict__ cls, const double* __restrict_
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= nx || y >= ny) return;
     size_t k = (size_t)y * pitch + x;
+    const double a = av[k];
+    if (a == 0.0) { wet[k] = (C)0; return; }
     double th = theta ? (double)theta[k] : theta_uniform;
     // Eq. chemical_potencial2: the wall term is a_v sqrt(2 kappa beta) cos(theta) (phi - phi^2)
-    wet[k] = (C)(av[k] * root * cos(th * 3.14159265358979323846 / 180.0));
+    wet[k] = (C)(a * root * cos(th * 3.14159265358979323846 / 180.0));
 }
 
 __global__ void k_links(const uint8_t* __restrict__ cls, uint16_t* __restrict__ unknown,

@@ -401,25 +401,26 @@ StepArgs<S, C> make_args(pflbm_t* h)
 // ---------------------------------------------------------------------------
 // Initial state (FP64 arithmetic for every storage precision)
 // ---------------------------------------------------------------------------
+// Eq. initialphi over the box x in [xlo, xlo + xw) (x periodic), y in
+// [ylo, yhi), combined with the field by maximum (a replacing call cleared it).
 __global__ void k_init_droplet(const uint8_t* __restrict__ cls, double* __restrict__ phi, int nx, int ny,
-                               int pitch, double x0, double y0, double R, double W, int replace)
+                               int pitch, int xlo, int xw, int ylo, int yhi, double x0, double y0, double R,
+                               double W)
 {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= nx || y >= ny) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = ylo + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= xw || y >= yhi) return;
+    int x = (xlo + i) % nx;
+    if (x < 0) x += nx;
     size_t k = (size_t)y * pitch + x;
-    if (!zeta_of(cls[k])) {
-        if (replace) phi[k] = 0.0;
-        return;
-    }
+    if (!zeta_of(cls[k])) return;
     double dx = fabs((double)x - x0);
     dx = fmod(dx, (double)nx);
     if (dx > 0.5 * nx) dx = nx - dx;       // x-periodic distance
     double dy = (double)y - y0;
     double r = sqrt(dx * dx + dy * dy);
-    // Eq. initialphi
     double v = 0.5 + 0.5 * tanh(2.0 * (R - r) / W);
-    if (replace || v > phi[k]) phi[k] = v;
+    if (v > phi[k]) phi[k] = v;
 }
 
 __global__ void k_ghost_fill(const uint8_t* __restrict__ cls, double* __restrict__ phi, int nx, int ny, int pitch)
@@ -526,8 +527,24 @@ cudaError_t run_step_kernel(pflbm_t* h, double* o_phi, double* o_u, double* o_p)
 
 cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, int replace)
 {
-    dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
-    k_init_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, x0, y0, R, h->prm.W, replace);
+    // Outside r = R + 10 W the profile is exactly 0 in FP64 (tanh(-20) rounds
+    // to -1), so only the droplet's bounding box is evaluated; a replacing
+    // call clears the field first.
+    if (replace) {
+        cudaError_t e = cudaMemsetAsync(h->phi0, 0, (size_t)h->ny * h->pitch * sizeof(double), h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    double reach = fabs(R) + 10.0 * h->prm.W;
+    int ylo = (int)fmax(0.0, floor(y0 - reach)), yhi = (int)fmin((double)h->ny - 1, ceil(y0 + reach));
+    if (ylo > yhi) return cudaSuccess;
+    int xlo = 0, xw = h->nx;
+    if (2.0 * reach + 2.0 < h->nx) {
+        xlo = (int)floor(x0 - reach);
+        xw = (int)(ceil(x0 + reach) - floor(x0 - reach)) + 1;
+    }
+    dim3 b(32, 8), g = grid2d(xw, yhi - ylo + 1, b);
+    k_init_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yhi + 1, x0, y0,
+                                           R, h->prm.W);
     return cudaGetLastError();
 }
 
