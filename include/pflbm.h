@@ -136,6 +136,24 @@ int pflbm_get_device(pflbm_t* h, double* phi, double* u, double* p);
 /* FP64 sum of phi = sum_i g_i over zeta = 1 nodes (synchronous). */
 int pflbm_mass(pflbm_t* h, double* out);
 
+/* FP64 sum of a phi field held in caller-owned DEVICE memory, over the nodes
+ * with d_zeta[k] != 0 (every node when d_zeta is NULL): the mass reduction of
+ * pflbm_mass applied to, e.g., the phi written by pflbm_get_device. The paper
+ * has no counterpart; this entry point exists for callers that cannot
+ * allocate device memory (a component inside a framework whose pool owns the
+ * device, or a loop where cudaMalloc's possible device synchronisation is not
+ * allowed) and so cannot create a handle. It allocates nothing: its block
+ * partials live in a static 32 KB device array that the library holds on
+ * every GPU it is loaded on until exit. d_phi: [ny][nx] doubles; d_zeta:
+ * [ny][nx] bytes or NULL; d_out: one double, written asynchronously on
+ * `stream` (cudaStream_t, NULL = default stream) of the current device.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture. Calls whose kernels overlap on the
+ * GPU share the array and race. Errors: EINVAL for NULL phi/out, nx or
+ * ny < 1, or nx * ny > 33,554,432 (the static limit); ECUDA. */
+int pflbm_phi_mass_noalloc(const double* d_phi, const uint8_t* d_zeta, int nx, int ny, double* d_out,
+                           void* stream);
+
 /* Contact angle (degrees) from a circle fitted to the phi = 1/2 crossings,
  * measured through the liquid against the given wall (synchronous; FP64 on
  * the device). circle (may be NULL) receives {centre x, centre y, R};

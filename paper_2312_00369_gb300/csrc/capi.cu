@@ -200,6 +200,8 @@ int ensure_out(pflbm_t* h)
 }  // namespace
 
 namespace pfk {
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
 size_t elem_size(int precision)
 {
     switch (precision) {

@@ -72,6 +72,8 @@ _SIGS = {
     "pflbm_get": (ctypes.c_int, [_H, _dp, _dp, _dp]),
     "pflbm_get_device": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pflbm_mass": (ctypes.c_int, [_H, _dp]),
+    "pflbm_phi_mass_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "pflbm_contact_angle": (ctypes.c_int, [_H, ctypes.POINTER(Wall), _dp, _dp, _ip]),
     "pflbm_geometry": (ctypes.c_int, [_H, _u8p, _u16p, _u16p, _dp]),
     "pflbm_lattice": (None, [_ip, _ip]),
@@ -126,6 +128,16 @@ def pflbm_lattice():
 
 def pflbm_footprint_bytes(nx, ny, precision="fp32"):
     return int(lib().pflbm_footprint_bytes(nx, ny, PRECISIONS.get(precision, precision)))
+
+
+def pflbm_phi_mass_noalloc(d_phi, d_zeta, nx, ny, d_out, stream=None):
+    """Allocation-free FP64 sum of a device phi field (raw device pointers as
+    ints; d_zeta may be None). Asynchronous on ``stream`` (a cudaStream_t
+    handle as int, or None for the default stream)."""
+    _check(lib().pflbm_phi_mass_noalloc(ctypes.c_void_p(d_phi),
+                                        None if d_zeta is None else ctypes.c_void_p(d_zeta),
+                                        int(nx), int(ny), ctypes.c_void_p(d_out),
+                                        None if stream is None else ctypes.c_void_p(stream)))
 
 
 class TorchAllocator:
