@@ -31,7 +31,18 @@ import numpy as np  # noqa: E402
 # algorithmic bytes per lattice update of the fused step: every f_i and g_i
 # read once and written once, the u.grad(phi) history read and written once,
 # one node byte (the wetting coefficient is read on wall layers only)
-BYTES_PER_LU = {"fp64": 2 * 9 * 2 * 8 + 2 * 8 + 1, "fp32": 2 * 9 * 2 * 4 + 2 * 4 + 1}
+BYTES_PER_LU = {"fp64": 2 * 9 * 2 * 8 + 2 * 8 + 1, "fp32": 2 * 9 * 2 * 4 + 2 * 4 + 1,
+                # 17 populations in 16 bits, g_0 in 32 bits, FP32 history
+                "bf16": 2 * (17 * 2 + 4) + 2 * 4 + 1, "fp16": 2 * (17 * 2 + 4) + 2 * 4 + 1}
+
+
+def step_source_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("step.cu", "storage.cuh", "pflbm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2312_00369_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def load_peaks():
@@ -157,7 +168,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"])
     ap.add_argument("--workload", default="many_flat")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
@@ -219,10 +230,12 @@ def main():
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
+        # DRAM bytes per launch from one ncu capture; null once the step
+        # kernel's source differs from the one that was captured
         try:
-            t = json.load(open(tfile))
-            key = f"{args.workload}:{args.precision}"
-            traffic = t.get(key)
+            t = json.load(open(tfile)).get(f"{args.workload}:{args.precision}")
+            if t and t.get("step_source_sha256") == step_source_sha256():
+                traffic = t["bytes_per_launch"]
         except Exception:
             traffic = None
     s.close()
@@ -260,7 +273,8 @@ def main():
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16 storage, f32 arithmetic",
+                      "fp16": "f16 storage, f32 arithmetic"}[args.precision], "data": "synthetic",
             "config": {"workload": case.name, "nx": case.nx, "ny": case.ny,
                        "droplets": len(case.droplets), "precision": args.precision,
                        "parallelism": "replicas" if world > 1 else "single",

@@ -9,7 +9,7 @@
 #include <new>
 #include <string>
 
-#include "pflbm_internal.cuh"
+#include "storage.cuh"
 
 namespace pfk {
 size_t mass_scratch_doubles();
@@ -120,8 +120,8 @@ bool valid_params(const pflbm_params_t* p, std::string& why)
         return false;
     }
     if (p->tau_g > 0 && !(p->tau_g > 0.5)) { why = "tau_g must be > 1/2"; return false; }
-    if (p->precision < PFLBM_FP64 || p->precision > PFLBM_FP32) {
-        why = "precision not supported by this build";
+    if (p->precision < PFLBM_FP64 || p->precision > PFLBM_FP16) {
+        why = "precision must be PFLBM_FP64, PFLBM_FP32, PFLBM_BF16 or PFLBM_FP16";
         return false;
     }
     if ((p->alloc == nullptr) != (p->free == nullptr)) { why = "alloc and free must be given together"; return false; }
@@ -210,7 +210,7 @@ size_t elem_size(int precision)
         default: return 2;
     }
 }
-size_t pop_bytes(int ny, int pitch, int precision) { return (size_t)18 * ny * pitch * elem_size(precision); }
+size_t pop_bytes(int ny, int pitch, int precision) { return state_copy_bytes(precision, (size_t)ny * pitch); }
 }  // namespace pfk
 
 extern "C" {

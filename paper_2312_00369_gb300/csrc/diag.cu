@@ -1,7 +1,7 @@
 // diag.cu -- FP64 diagnostics: the phi mass and the contact-angle fit.
 // Both are reductions in FP64 with warp shuffles and a fixed block order
 // (the mass is bit-reproducible run to run).
-#include "pflbm_internal.cuh"
+#include "storage.cuh"
 
 namespace pfk {
 namespace {
@@ -35,28 +35,23 @@ __device__ double block_sum(double v, double* sh)
     return r;
 }
 
-// Pulled value of population plane i at node (x, y) (same rule as the step).
-template <typename S>
-__device__ double pulled(const S* __restrict__ base, const uint8_t* __restrict__ cls, int i, int x, int y,
-                         int nx, int pitch, size_t plane)
+// Pulled g_I at node (x, y), same rule as the step, as a double.
+template <int PREC, int I>
+__device__ __forceinline__ double pulled_g(const Planes<PREC>& P, const uint8_t* __restrict__ cls, int x, int y,
+                                           int nx, int pitch, size_t plane)
 {
-    if (i == 0) {
-        if (sizeof(S) == 4)  // FP32 mode: g_0 is fixed point, 2^-30
-            return (double)reinterpret_cast<const int32_t*>(base)[(size_t)y * pitch + x] * (1.0 / 1073741824.0);
-        return (double)base[(size_t)y * pitch + x];
-    }
-    const int X = cx(i), Y = cy(i), O = opp(i);
+    using T = Store<PREC>;
+    constexpr int X = cx(I), Y = cy(I), O = opp(I);
     size_t src = (size_t)(y - Y) * pitch + wrap1(x - X, nx);
-    if (zeta_of(cls[src])) return (double)base[i * plane + src];
+    if (zeta_of(cls[src])) return (double)T::template ld<I>(P.g[I * plane + src]);
     size_t dst = (size_t)(y + Y) * pitch + wrap1(x + X, nx);
-    if (zeta_of(cls[dst])) return (double)base[O * plane + dst];
-    return (double)base[O * plane + (size_t)y * pitch + x];
+    if (zeta_of(cls[dst])) return (double)T::template ld<O>(P.g[O * plane + dst]);
+    return (double)T::template ld<O>(P.g[O * plane + (size_t)y * pitch + x]);
 }
 
-template <typename S>
-__global__ void __launch_bounds__(RB) k_mass_partial(const uint8_t* __restrict__ cls, const S* __restrict__ gbase,
-                                                     int nx, int ny, int pitch, size_t plane,
-                                                     double* __restrict__ partial)
+template <int PREC>
+__global__ void __launch_bounds__(RB) k_mass_partial(const uint8_t* __restrict__ cls, Planes<PREC> P, int nx, int ny,
+                                                     int pitch, size_t plane, double* __restrict__ partial)
 {
     __shared__ double sh[RB / 32];
     double acc = 0.0;
@@ -64,10 +59,16 @@ __global__ void __launch_bounds__(RB) k_mass_partial(const uint8_t* __restrict__
     for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < N; t += (long long)gridDim.x * RB) {
         int y = (int)(t / nx), x = (int)(t - (long long)y * nx);
         if (!zeta_of(cls[(size_t)y * pitch + x])) continue;
-        double v[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) v[i] = pulled<S>(gbase, cls, i, x, y, nx, pitch, plane);
-        acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+        double v0 = Store<PREC>::g0_double(P.g0[(size_t)y * pitch + x]);
+        double v1 = pulled_g<PREC, 1>(P, cls, x, y, nx, pitch, plane);
+        double v2 = pulled_g<PREC, 2>(P, cls, x, y, nx, pitch, plane);
+        double v3 = pulled_g<PREC, 3>(P, cls, x, y, nx, pitch, plane);
+        double v4 = pulled_g<PREC, 4>(P, cls, x, y, nx, pitch, plane);
+        double v5 = pulled_g<PREC, 5>(P, cls, x, y, nx, pitch, plane);
+        double v6 = pulled_g<PREC, 6>(P, cls, x, y, nx, pitch, plane);
+        double v7 = pulled_g<PREC, 7>(P, cls, x, y, nx, pitch, plane);
+        double v8 = pulled_g<PREC, 8>(P, cls, x, y, nx, pitch, plane);
+        acc += ((v0 + v1) + (v2 + v3)) + ((v4 + v5) + (v6 + v7)) + v8;
     }
     double r = block_sum<RB>(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -237,15 +238,22 @@ __global__ void __launch_bounds__(FB) k_fit(const double* __restrict__ pts, cons
 
 }  // namespace
 
+template <int PREC>
+void mass_prec(pflbm_t* h, size_t plane)
+{
+    k_mass_partial<PREC><<<MASS_BLOCKS, RB, 0, h->stream>>>(h->cls, Planes<PREC>::make(h->pop[h->cur], plane), h->nx,
+                                                            h->ny, h->pitch, plane, h->red);
+}
+
 cudaError_t launch_mass(pflbm_t* h, double* d_out)
 {
     size_t plane = (size_t)h->ny * h->pitch;
-    if (h->precision == PFLBM_FP64)
-        k_mass_partial<double><<<MASS_BLOCKS, RB, 0, h->stream>>>(h->cls, (const double*)h->pop[h->cur] + 9 * plane,
-                                                                  h->nx, h->ny, h->pitch, plane, h->red);
-    else
-        k_mass_partial<float><<<MASS_BLOCKS, RB, 0, h->stream>>>(h->cls, (const float*)h->pop[h->cur] + 9 * plane,
-                                                                 h->nx, h->ny, h->pitch, plane, h->red);
+    switch (h->precision) {
+        case PFLBM_FP64: mass_prec<PFLBM_FP64>(h, plane); break;
+        case PFLBM_FP32: mass_prec<PFLBM_FP32>(h, plane); break;
+        case PFLBM_BF16: mass_prec<PFLBM_BF16>(h, plane); break;
+        default: mass_prec<PFLBM_FP16>(h, plane); break;
+    }
     k_sum_partials<<<1, RB, 0, h->stream>>>(h->red, MASS_BLOCKS, d_out);
     return cudaGetLastError();
 }

@@ -1,33 +1,29 @@
 // step.cu -- initial state, the fused time step and the macroscopic read-back.
 //
-// State layout (HBM): one buffer per copy holds 18 planes [ny][pitch]: f_0..f_8
-// then g_0..g_8, in the library's velocity order; two copies ping-pong. The
-// stored values are POST-COLLISION populations f*_i(x), g*_i(x) at the node
-// that produced them (pull scheme). A step at node x first pulls its
-// post-streaming populations,
+// The stored values are POST-COLLISION populations f*_i(x), g*_i(x) at the
+// node that produced them (pull scheme; storage formats in storage.cuh). A
+// step at node x first pulls its post-streaming populations,
 //     f_i(x) = f*_i(x - c_i)          if zeta(x - c_i) = 1   (streaming)
 //            = f*_{i'}(x + c_i)       else if zeta(x + c_i) = 1
 //            = f*_{i'}(x)             otherwise,
 // which is the modified bounce-back of Sec. 2.2.2 (unknown f_i(x_b) takes the
 // post-streaming f_{i'}(x_b); if that is unknown too, the node's own
 // post-collision f*_{i'}). Then it computes phi = sum g_i (Eq.
-// order-parameter) on a shared-memory tile with a two-node halo, fills ghost
-// nodes with the zeta-weighted neighbour mean (Sec. 2.2.2), takes the
-// isotropic gradient and Laplacian (Eqs. gradient, Laplace), the chemical
+// order-parameter) on a shared-memory tile with a one- or two-node halo,
+// fills ghost nodes with the zeta-weighted neighbour mean (Sec. 2.2.2), takes
+// the isotropic gradient and Laplacian (Eqs. gradient, Laplace), the chemical
 // potential with the wetting term (Eq. chemical_potencial2), rho, the force
 // F = mu grad(phi), u and p (Sec. 2.1.2), collides f (Eqs. BGK-NS, feq_i, Siu,
 // GGi) and g (Eqs. BGK, H_i, F_i with (1/2) dG/dt as a backward difference)
 // and stores f*, g* and the new u.grad(phi) history.
 //
 // g_0 carries phi (it is O(1) while every other population is O(alpha mu)),
-// so rounding it on every store is what limits a 32-bit state: in the FP32
-// mode it is kept as a 32-bit fixed-point number q = g_0 2^30 (|g_0| < 2,
-// resolution 9.3e-10) and advanced by integer addition of the collision
-// increment g*_0 - g_0 = (g_0^eq - g_0)/tau_g + (3/2 G_0(t) - 1/2 G_0(t-1)),
-// where g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu holds no O(1) term.
-#include <climits>
-
-#include "pflbm_internal.cuh"
+// so rounding it on every store is what limits a 32-bit state: outside FP64
+// it is a 32-bit fixed-point number advanced by integer addition of the
+// collision increment g*_0 - g_0 = (g_0^eq - g_0)/tau_g + (3/2 G_0(t) -
+// 1/2 G_0(t-1)), where g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu holds
+// no O(1) term.
+#include "storage.cuh"
 
 namespace pfk {
 namespace {
@@ -35,36 +31,16 @@ namespace {
 __device__ __forceinline__ int wrap1(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
 __device__ __forceinline__ int wrapn(int x, int nx) { int r = x % nx; return r < 0 ? r + nx : r; }
 
-// Storage of g_0 (see the note at the top of the file).
-template <typename S> struct G0;
-template <> struct G0<double> {
-    using T = double;
-    __device__ static double value(T raw) { return raw; }
-    __device__ static T add(T raw, double d, int*) { return raw + d; }
-    static T from_double(double v) { return v; }
-};
-template <> struct G0<float> {
-    using T = int32_t;
-    __device__ static float value(T raw) { return (float)raw * (1.0f / 1073741824.0f); }
-    __device__ static T add(T raw, float d, int* status)
-    {
-        long long q = (long long)raw + __float2ll_rn(d * 1073741824.0f);
-        if (q > INT_MAX || q < -INT_MAX) {
-            atomicOr(status, 2);
-            q = q > 0 ? INT_MAX : -INT_MAX;
-        }
-        return (T)q;
-    }
-};
-
-template <typename S, typename C>
+template <int PREC>
 struct StepArgs {
+    using T = Store<PREC>;
+    using S = typename T::S;
+    using C = typename T::C;
     const uint8_t* cls;
     const uint8_t* tiles;  // per tile: 1 when every node within 2 of it is fluid
     const C* wet;
-    const S* fin;   // 18 planes
-    S* fout;        // 18 planes
-    S* sprev;
+    Planes<PREC> in, out;
+    C* sprev;
     int nx, ny, pitch;
     int plane;      // 18 * plane < 2^31 (checked at create)
     C beta4, kappa, rho_g, drho, omega_f, omega_g, force_pre, alpha;
@@ -75,53 +51,58 @@ struct StepArgs {
     double* o_p;
 };
 
-// Pull of direction i at node (gx, gy), whose class byte sits at s_cls[sy][sx].
+// Pull of direction I at node (gx, gy), whose class byte sits at s_cls[sy][sx].
 // CHECK = false: every neighbour is a zeta = 1 node (s_cls is not read).
-template <int I, typename S, typename C, bool CHECK>
-__device__ __forceinline__ C pull(const S* __restrict__ base, const uint8_t (*s_cls)[TX + 6], int sy,
-                                  int sx, int gx, int gy, int nx, int pitch, int plane)
+template <int I, int PREC, bool CHECK>
+__device__ __forceinline__ typename Store<PREC>::C pull(const typename Store<PREC>::S* __restrict__ base,
+                                                        const uint8_t (*s_cls)[TX + 6], int sy, int sx, int gx,
+                                                        int gy, int nx, int pitch, int plane)
 {
+    using T = Store<PREC>;
     constexpr int X = cx(I), Y = cy(I), O = opp(I);
     if (!CHECK || zeta_of(s_cls[sy - Y][sx - X])) {
-        return (C)base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)];
+        return T::template ld<I>(base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)]);
     }
     if (zeta_of(s_cls[sy + Y][sx + X])) {
-        return (C)base[O * plane + (gy + Y) * pitch + wrap1(gx + X, nx)];
+        return T::template ld<O>(base[O * plane + (gy + Y) * pitch + wrap1(gx + X, nx)]);
     }
-    return (C)base[O * plane + gy * pitch + gx];
+    return T::template ld<O>(base[O * plane + gy * pitch + gx]);
 }
 
-template <typename S, typename C, bool CHECK>
-__device__ __forceinline__ void pull_all(C v[9], const S* __restrict__ base, const uint8_t (*s_cls)[TX + 6],
-                                         int sy, int sx, int gx, int gy, int nx, int pitch, int plane)
-{
-    v[0] = (C)base[gy * pitch + gx];
-    v[1] = pull<1, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[2] = pull<2, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[3] = pull<3, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[4] = pull<4, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[5] = pull<5, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[6] = pull<6, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[7] = pull<7, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[8] = pull<8, S, C, CHECK>(base, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-}
-
-// Pulled g at a node: g_0 raw (storage form) and its value, g_1..g_8.
-template <typename S, typename C, bool CHECK>
-__device__ __forceinline__ void pull_g(C v[9], typename G0<S>::T& raw0, const S* __restrict__ gbase,
+template <int PREC, bool CHECK>
+__device__ __forceinline__ void pull_f(typename Store<PREC>::C v[9], const typename Store<PREC>::S* __restrict__ f,
                                        const uint8_t (*s_cls)[TX + 6], int sy, int sx, int gx, int gy, int nx,
                                        int pitch, int plane)
 {
-    raw0 = reinterpret_cast<const typename G0<S>::T*>(gbase)[gy * pitch + gx];
-    v[0] = (C)G0<S>::value(raw0);
-    v[1] = pull<1, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[2] = pull<2, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[3] = pull<3, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[4] = pull<4, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[5] = pull<5, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[6] = pull<6, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[7] = pull<7, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[8] = pull<8, S, C, CHECK>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    using T = Store<PREC>;
+    v[0] = T::template ld<0>(f[gy * pitch + gx]);
+    v[1] = pull<1, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[2] = pull<2, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[3] = pull<3, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[4] = pull<4, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[5] = pull<5, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[6] = pull<6, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[7] = pull<7, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[8] = pull<8, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+}
+
+// Pulled g at a node: g_0 raw (storage form) and its value, g_1..g_8.
+template <int PREC, bool CHECK>
+__device__ __forceinline__ void pull_g(typename Store<PREC>::C v[9], typename Store<PREC>::G0T& raw0,
+                                       const Planes<PREC>& P, const uint8_t (*s_cls)[TX + 6], int sy, int sx,
+                                       int gx, int gy, int nx, int pitch, int plane)
+{
+    using T = Store<PREC>;
+    raw0 = P.g0[gy * pitch + gx];
+    v[0] = T::g0(raw0);
+    v[1] = pull<1, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[2] = pull<2, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[3] = pull<3, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[4] = pull<4, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[5] = pull<5, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[6] = pull<6, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[7] = pull<7, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[8] = pull<8, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
 }
 
 template <typename C>
@@ -134,32 +115,31 @@ __device__ __forceinline__ C sum_moving(const C v[9])
 template <typename C>
 __device__ __forceinline__ C phi_of(const C v[9]) { return v[0] + sum_moving(v); }
 
-template <typename S, typename C>
-__device__ __forceinline__ C pulled_phi(const S* __restrict__ gbase, const uint8_t (*s_cls)[TX + 6], int sy,
-                                        int sx, int gx, int gy, int nx, int pitch, int plane)
+template <int PREC, bool CHECK>
+__device__ __forceinline__ typename Store<PREC>::C pulled_phi(const Planes<PREC>& P, const uint8_t (*s_cls)[TX + 6],
+                                                              int sy, int sx, int gx, int gy, int nx, int pitch,
+                                                              int plane)
 {
-    C v[9];
-    typename G0<S>::T raw0;
-    if (s_cls[sy][sx] & F_LINK)
-        pull_g<S, C, true>(v, raw0, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    else
-        pull_g<S, C, false>(v, raw0, gbase, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    typename Store<PREC>::C v[9];
+    typename Store<PREC>::G0T raw0;
+    pull_g<PREC, CHECK>(v, raw0, P, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     return phi_of(v);
 }
 
 // Prologue of a tile whose nodes within two of it are all fluid: no class
 // tile, no bounce-back checks, no ghosts, phi on a one-node ring.
-template <typename S, typename C>
-__device__ __forceinline__ void tile_prologue_fluid(const StepArgs<S, C>& a, C (*s_phi)[TX + 4], int x0, int y0,
-                                                    C gown[9], typename G0<S>::T& raw0)
+template <int PREC>
+__device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
+                                                    typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0,
+                                                    typename Store<PREC>::C gown[9],
+                                                    typename Store<PREC>::G0T& raw0)
 {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int nx = a.nx, pitch = a.pitch, plane = a.plane;
-    const S* gbase = a.fin + 9 * plane;
     {
         const int gx = wrap1(x0 + tx, nx), gy = y0 + ty;
-        pull_g<S, C, false>(gown, raw0, gbase, nullptr, 0, 0, gx, gy, nx, pitch, plane);
+        pull_g<PREC, false>(gown, raw0, a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
         s_phi[ty + 2][tx + 2] = phi_of(gown);
     }
     // ring: top row, bottom row (TX + 2 each), left and right columns (TY each)
@@ -171,27 +151,24 @@ __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<S, C>& a, C (
         else if (tid < 2 * RT + TY) { py = 2 + tid - 2 * RT; px = 1; }
         else { py = 2 + tid - 2 * RT - TY; px = TX + 2; }
         const int gy = y0 - 2 + py, gx = wrap1(x0 - 2 + px, nx);
-        C v[9];
-        typename G0<S>::T r;
-        pull_g<S, C, false>(v, r, gbase, nullptr, 0, 0, gx, gy, nx, pitch, plane);
-        s_phi[py][px] = phi_of(v);
+        s_phi[py][px] = pulled_phi<PREC, false>(a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
     }
     __syncthreads();
 }
 
-// Common prologue: class tile (halo 3) and phi tile with ghost values. A
+// General prologue: class tile (halo 3) and phi tile with ghost values. A
 // tile needs phi two nodes out only when a ghost node lies next to one of its
 // nodes (the ghost average reaches one node further); otherwise one ring.
 // Returns the own node's pulled g (and raw g_0) when it is a zeta = 1 node.
-template <typename S, typename C>
-__device__ __forceinline__ void tile_prologue(const StepArgs<S, C>& a, uint8_t (*s_cls)[TX + 6],
-                                              C (*s_phi)[TX + 4], int x0, int y0, C gown[9],
-                                              typename G0<S>::T& raw0)
+template <int PREC>
+__device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (*s_cls)[TX + 6],
+                                              typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0,
+                                              typename Store<PREC>::C gown[9], typename Store<PREC>::G0T& raw0)
 {
+    using C = typename Store<PREC>::C;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
-    const S* gbase = a.fin + 9 * a.plane;
 
     for (int p = tid; p < (TY + 6) * (TX + 6); p += TX * TY) {
         int py = p / (TX + 6), px = p - py * (TX + 6);
@@ -213,9 +190,9 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<S, C>& a, uint8_t (
         C ph = C(0);
         if (gy < ny && zeta_of(own)) {
             if (own & F_LINK)
-                pull_g<S, C, true>(gown, raw0, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+                pull_g<PREC, true>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
             else
-                pull_g<S, C, false>(gown, raw0, gbase, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+                pull_g<PREC, false>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
             ph = phi_of(gown);
         }
         s_phi[ty + 2][tx + 2] = ph;
@@ -227,9 +204,13 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<S, C>& a, uint8_t (
         if (py >= 2 && py < TY + 2 && px >= 2 && px < TX + 2) continue;
         int sy = py + 1, sx = px + 1;
         C ph = C(0);
-        if (zeta_of(s_cls[sy][sx])) {
+        const uint8_t c = s_cls[sy][sx];
+        if (zeta_of(c)) {
             int gy = y0 - 2 + py, gx = wrapn(x0 - 2 + px, nx);
-            ph = pulled_phi<S, C>(gbase, s_cls, sy, sx, gx, gy, nx, pitch, a.plane);
+            if (c & F_LINK)
+                ph = pulled_phi<PREC, true>(a.in, s_cls, sy, sx, gx, gy, nx, pitch, a.plane);
+            else
+                ph = pulled_phi<PREC, false>(a.in, s_cls, sy, sx, gx, gy, nx, pitch, a.plane);
         }
         s_phi[py][px] = ph;
     }
@@ -266,19 +247,59 @@ __device__ __forceinline__ void stencils(C (*s_phi)[TX + 4], int py, int px, C& 
     lap = ((E + W) + (N + Sx)) * (C(2) / C(3)) + ((NE + NW) + (SE + SW)) * (C(1) / C(6)) - c * (C(10) / C(3));
 }
 
-template <typename S, typename C, bool COLLIDE>
-__global__ void __launch_bounds__(TX * TY) k_step(StepArgs<S, C> a)
+template <int PREC, int I>
+__device__ __forceinline__ void collide_f_dir(const StepArgs<PREC>& a, typename Store<PREC>::C f_i,
+                                              typename Store<PREC>::C p, typename Store<PREC>::C rho,
+                                              typename Store<PREC>::C ux, typename Store<PREC>::C uy,
+                                              typename Store<PREC>::C uu, typename Store<PREC>::C Fx,
+                                              typename Store<PREC>::C Fy, typename Store<PREC>::C drx,
+                                              typename Store<PREC>::C dry, int k)
 {
+    using T = Store<PREC>;
+    using C = typename T::C;
+    const C w = wgt<C>(I);
+    const C cu = C(cx(I)) * ux + C(cy(I)) * uy;
+    const C cF = C(cx(I)) * Fx + C(cy(I)) * Fy;
+    const C cdr = C(cx(I)) * drx + C(cy(I)) * dry;
+    const C feq = w * (C(3) * p + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
+    const C Fi = a.force_pre * w * C(3) * (cF + cu * cdr);
+    a.out.f[I * a.plane + k] = T::template st<I>(f_i + a.omega_f * (feq - f_i) + Fi);
+}
+
+// g_i (i != 0) collision and store; returns the storage rounding residual
+// (population computed minus population stored) for the 16-bit formats.
+template <int PREC, int I>
+__device__ __forceinline__ typename Store<PREC>::C collide_g_dir(const StepArgs<PREC>& a,
+                                                                 typename Store<PREC>::C g_i,
+                                                                 typename Store<PREC>::C am,
+                                                                 typename Store<PREC>::C src, int k)
+{
+    using T = Store<PREC>;
+    using C = typename T::C;
+    const C w = wgt<C>(I);
+    const C h = (I <= 4) ? C(-0.5) : C(1);
+    const C v = g_i + a.omega_g * (w * am - g_i) + w * h * src;
+    const typename T::S s = T::template st<I>(v);
+    a.out.g[I * a.plane + k] = s;
+    if (T::kAbsorb) return v - T::template ld<I>(s);
+    return C(0);
+}
+
+template <int PREC, bool COLLIDE>
+__global__ void __launch_bounds__(TX * TY) k_step(StepArgs<PREC> a)
+{
+    using T = Store<PREC>;
+    using C = typename T::C;
     __shared__ uint8_t s_cls[TY + 6][TX + 6];
     __shared__ C s_phi[TY + 4][TX + 4];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     C g[9];
-    typename G0<S>::T g0raw;
+    typename T::G0T g0raw;
     const bool fluid_tile = a.tiles[blockIdx.y * gridDim.x + blockIdx.x] != 0;
     if (fluid_tile)
-        tile_prologue_fluid<S, C>(a, s_phi, x0, y0, g, g0raw);
+        tile_prologue_fluid<PREC>(a, s_phi, x0, y0, g, g0raw);
     else
-        tile_prologue<S, C>(a, s_cls, s_phi, x0, y0, g, g0raw);
+        tile_prologue<PREC>(a, s_cls, s_phi, x0, y0, g, g0raw);
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int gx = x0 + tx, gy = y0 + ty;
@@ -310,9 +331,9 @@ __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<S, C> a)
     // ---- hydrodynamic moments (Sec. 2.1.2) ----
     C f[9];
     if (code & F_LINK)
-        pull_all<S, C, true>(f, a.fin, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
+        pull_f<PREC, true>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
     else
-        pull_all<S, C, false>(f, a.fin, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
+        pull_f<PREC, false>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
     const C mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const C my = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
     const C inv_rho = C(1) / rho;
@@ -333,58 +354,57 @@ __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<S, C> a)
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
 
     // ---- f collision: f* = f + (f^eq - f)/tau_f + F_i ----
-    S* fo = a.fout;
-    const C of = a.omega_f;
     {
         const C feq0 = C(-5) / C(3) * p - rho * (wgt<C>(0) * C(1.5)) * uu;
-        fo[k] = (S)(f[0] + of * (feq0 - f[0]));
+        a.out.f[k] = T::template st<0>(f[0] + a.omega_f * (feq0 - f[0]));
     }
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const C w = wgt<C>(i);
-        const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
-        const C cF = C(cx(i)) * Fx + C(cy(i)) * Fy;
-        const C cdr = C(cx(i)) * drx + C(cy(i)) * dry;
-        const C feq = w * (C(3) * p + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
-        const C Fi = a.force_pre * w * C(3) * (cF + cu * cdr);
-        fo[i * a.plane + k] = (S)(f[i] + of * (feq - f[i]) + Fi);
-    }
+    collide_f_dir<PREC, 1>(a, f[1], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 2>(a, f[2], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 3>(a, f[3], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 4>(a, f[4], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 5>(a, f[5], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 6>(a, f[6], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 7>(a, f[7], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 8>(a, f[8], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
 
     // ---- g collision: g* = g + (g^eq - g)/tau_g + (3/2) G_i(t) - (1/2) G_i(t-1) ----
     const C s_now = ux * gpx + uy * gpy;
-    const C s_old = (C)a.sprev[k];
+    const C s_old = a.sprev[k];
     const C src = C(1.5) * s_now - C(0.5) * s_old;
     const C am = a.alpha * mu;
-    const C og = a.omega_g;
-    S* go = a.fout + 9 * a.plane;
+    C resid = collide_g_dir<PREC, 1>(a, g[1], am, src, k);
+    resid += collide_g_dir<PREC, 2>(a, g[2], am, src, k);
+    resid += collide_g_dir<PREC, 3>(a, g[3], am, src, k);
+    resid += collide_g_dir<PREC, 4>(a, g[4], am, src, k);
+    resid += collide_g_dir<PREC, 5>(a, g[5], am, src, k);
+    resid += collide_g_dir<PREC, 6>(a, g[6], am, src, k);
+    resid += collide_g_dir<PREC, 7>(a, g[7], am, src, k);
+    resid += collide_g_dir<PREC, 8>(a, g[8], am, src, k);
     {
-        // g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu (Eq. H_i)
-        const C d0 = og * (sum_moving(g) - (C(1) - wgt<C>(0)) * am) + wgt<C>(0) * C(-2) * src;
-        reinterpret_cast<typename G0<S>::T*>(go)[k] = G0<S>::add(g0raw, d0, a.status);
+        // g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu (Eq. H_i); in the
+        // 16-bit formats g_0 also takes back what rounding removed from g_1..g_8
+        const C d0 = a.omega_g * (sum_moving(g) - (C(1) - wgt<C>(0)) * am) + wgt<C>(0) * C(-2) * src;
+        a.out.g0[k] = T::g0_add(g0raw, T::kAbsorb ? d0 + resid : d0, a.status);
     }
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const C w = wgt<C>(i);
-        const C h = (i <= 4) ? C(-0.5) : C(1);
-        go[i * a.plane + k] = (S)(g[i] + og * (w * am - g[i]) + w * h * src);
-    }
-    a.sprev[k] = (S)s_now;
+    a.sprev[k] = s_now;
 }
 
-template <typename S, typename C>
-StepArgs<S, C> make_args(pflbm_t* h)
+template <int PREC>
+StepArgs<PREC> make_args(pflbm_t* h)
 {
-    StepArgs<S, C> a{};
+    using C = typename Store<PREC>::C;
+    StepArgs<PREC> a{};
+    const size_t plane = (size_t)h->ny * h->pitch;
     a.cls = h->cls;
     a.tiles = h->tiles;
     a.wet = (const C*)h->wet;
-    a.fin = (const S*)h->pop[h->cur];
-    a.fout = (S*)h->pop[h->cur ^ 1];
-    a.sprev = (S*)h->sprev;
+    a.in = Planes<PREC>::make(h->pop[h->cur], plane);
+    a.out = Planes<PREC>::make(h->pop[h->cur ^ 1], plane);
+    a.sprev = (C*)h->sprev;
     a.nx = h->nx;
     a.ny = h->ny;
     a.pitch = h->pitch;
-    a.plane = h->ny * h->pitch;
+    a.plane = (int)plane;
     const Params& q = h->prm;
     a.beta4 = (C)(4.0 * q.beta);
     a.kappa = (C)q.kappa;
@@ -444,14 +464,12 @@ __global__ void k_ghost_fill(const uint8_t* __restrict__ cls, double* __restrict
 
 template <typename C>
 __global__ void k_init_mu(const uint8_t* __restrict__ cls, const C* __restrict__ wet, const double* __restrict__ phi,
-                          double* __restrict__ mu, void* __restrict__ sprev_v, int nx, int ny, int pitch,
-                          Params q)
+                          double* __restrict__ mu, C* __restrict__ sprev, int nx, int ny, int pitch, Params q)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= nx || y >= ny) return;
     size_t k = (size_t)y * pitch + x;
-    C* sprev = (C*)sprev_v;
     uint8_t code = cls[k];
     if (!zeta_of(code)) { mu[k] = 0.0; sprev[k] = (C)0; return; }
     auto at = [&](int dx, int dy) { return phi[(size_t)(y + dy) * pitch + wrap1(x + dx, nx)]; };
@@ -470,56 +488,81 @@ __global__ void k_init_mu(const uint8_t* __restrict__ cls, const C* __restrict__
     sprev[k] = (C)(ux * gpx + uy * gpy);
 }
 
-template <typename S> __device__ typename G0<S>::T g0_store(double v);
-template <> __device__ double g0_store<double>(double v) { return v; }
-template <> __device__ int32_t g0_store<float>(double v)
+// g_J^eq (J != 0) in storage form; returns the rounding residual.
+template <int PREC, int J>
+__device__ __forceinline__ double init_g_dir(const uint8_t* cls, const double* mu, const Planes<PREC>& P, int x,
+                                             int y, int nx, int pitch, size_t k, size_t plane, double alpha)
 {
-    double q = rint(v * 1073741824.0);
-    return (int32_t)fmax(-(double)INT_MAX, fmin((double)INT_MAX, q));
+    using T = Store<PREC>;
+    // the pull at x + c_j reads this value as its g_j when x + c_j is a
+    // zeta = 1 node; when it is not, only the doubly-unknown rule of this
+    // node reads it, as the node's own value
+    size_t m = (size_t)(y + cy(J)) * pitch + wrap1(x + cx(J), nx);
+    if (!zeta_of(cls[m])) m = k;
+    const double w = J <= 4 ? 1.0 / 9.0 : 1.0 / 36.0;
+    const double v = w * alpha * mu[m];
+    const typename T::S s = T::template st<J>((typename T::C)v);
+    P.g[J * plane + k] = s;
+    return v - (double)T::template ld<J>(s);
 }
 
 // Post-collision arrays that the first pull turns into f = 0, g = g^eq(phi0, mu0).
-template <typename S>
+template <int PREC>
 __global__ void k_init_pop(const uint8_t* __restrict__ cls, const double* __restrict__ phi,
-                           const double* __restrict__ mu, S* __restrict__ pop, int nx, int ny, int pitch,
-                           size_t plane, double alpha)
+                           const double* __restrict__ mu, Planes<PREC> P, int nx, int ny, int pitch, size_t plane,
+                           double alpha)
 {
+    using T = Store<PREC>;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= nx || y >= ny) return;
     size_t k = (size_t)y * pitch + x;
-    for (int i = 0; i < 18; ++i) pop[i * plane + k] = (S)0;
-    if (!zeta_of(cls[k])) return;
-    S* g = pop + 9 * plane;
-    for (int j = 0; j < 9; ++j) {
-        // the pull at x + c_j reads this value as its g_j when x + c_j is a
-        // zeta = 1 node; when it is not, only the doubly-unknown rule of this
-        // node reads it, as the node's own value
-        size_t m = k;
-        if (j != 0) {
-            size_t mm = (size_t)(y + cy(j)) * pitch + wrap1(x + cx(j), nx);
-            if (zeta_of(cls[mm])) m = mm;
-        }
-        double w = j == 0 ? 4.0 / 9.0 : (j <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-        double geq = (j == 0) ? phi[m] - (1.0 - w) * alpha * mu[m] : w * alpha * mu[m];
-        if (j == 0)
-            reinterpret_cast<typename G0<S>::T*>(g)[k] = g0_store<S>(geq);
-        else
-            g[j * plane + k] = (S)geq;
+    const typename T::S zero = T::template st<0>((typename T::C)0);
+    for (int i = 0; i < 9; ++i) {
+        P.f[i * plane + k] = zero;
+        P.g[i * plane + k] = zero;
     }
+    P.g0[k] = T::g0_from_double(0.0);
+    if (!zeta_of(cls[k])) return;
+    double r = 0.0;
+    r += init_g_dir<PREC, 1>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    r += init_g_dir<PREC, 2>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    r += init_g_dir<PREC, 3>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    r += init_g_dir<PREC, 4>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    r += init_g_dir<PREC, 5>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    r += init_g_dir<PREC, 6>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    r += init_g_dir<PREC, 7>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    r += init_g_dir<PREC, 8>(cls, mu, P, x, y, nx, pitch, k, plane, alpha);
+    // g_0^eq (Eq. H_i); with 16-bit g_i it also holds their rounding residual
+    double g0 = phi[k] - (5.0 / 9.0) * alpha * mu[k];
+    if (T::kAbsorb) g0 += r;
+    P.g0[k] = T::g0_from_double(g0);
 }
 
 dim3 grid2d(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
-template <typename S, typename C, bool COLLIDE>
+template <int PREC, bool COLLIDE>
 cudaError_t run_step_kernel(pflbm_t* h, double* o_phi, double* o_u, double* o_p)
 {
-    StepArgs<S, C> a = make_args<S, C>(h);
+    StepArgs<PREC> a = make_args<PREC>(h);
     a.o_phi = o_phi;
     a.o_u = o_u;
     a.o_p = o_p;
-    dim3 b(TX, TY), g((h->nx + TX - 1) / TX, (h->ny + TY - 1) / TY);
-    k_step<S, C, COLLIDE><<<g, b, 0, h->stream>>>(a);
+    dim3 b(TX, TY), g(tiles_x(h->nx), tiles_y(h->ny));
+    k_step<PREC, COLLIDE><<<g, b, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t init_pop_prec(pflbm_t* h)
+{
+    using C = typename Store<PREC>::C;
+    dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
+    size_t plane = (size_t)h->ny * h->pitch;
+    k_init_mu<C><<<g, b, 0, h->stream>>>(h->cls, (const C*)h->wet, h->phi0, h->mu0, (C*)h->sprev, h->nx, h->ny,
+                                         h->pitch, h->prm);
+    k_init_pop<PREC><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->mu0, Planes<PREC>::make(h->pop[h->cur], plane),
+                                             h->nx, h->ny, h->pitch, plane, h->prm.alpha);
     return cudaGetLastError();
 }
 
@@ -552,37 +595,35 @@ cudaError_t launch_init_populations(pflbm_t* h)
 {
     dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
     k_ghost_fill<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch);
-    size_t plane = (size_t)h->ny * h->pitch;
-    if (h->precision == PFLBM_FP64) {
-        k_init_mu<double><<<g, b, 0, h->stream>>>(h->cls, (const double*)h->wet, h->phi0, h->mu0, h->sprev,
-                                                  h->nx, h->ny, h->pitch, h->prm);
-        k_init_pop<double><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->mu0, (double*)h->pop[h->cur], h->nx,
-                                                   h->ny, h->pitch, plane, h->prm.alpha);
-    } else {
-        k_init_mu<float><<<g, b, 0, h->stream>>>(h->cls, (const float*)h->wet, h->phi0, h->mu0, h->sprev,
-                                                 h->nx, h->ny, h->pitch, h->prm);
-        k_init_pop<float><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->mu0, (float*)h->pop[h->cur], h->nx,
-                                                  h->ny, h->pitch, plane, h->prm.alpha);
+    switch (h->precision) {
+        case PFLBM_FP64: return init_pop_prec<PFLBM_FP64>(h);
+        case PFLBM_FP32: return init_pop_prec<PFLBM_FP32>(h);
+        case PFLBM_BF16: return init_pop_prec<PFLBM_BF16>(h);
+        default: return init_pop_prec<PFLBM_FP16>(h);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_step(pflbm_t* h)
 {
     cudaError_t e;
-    if (h->precision == PFLBM_FP64)
-        e = run_step_kernel<double, double, true>(h, nullptr, nullptr, nullptr);
-    else
-        e = run_step_kernel<float, float, true>(h, nullptr, nullptr, nullptr);
+    switch (h->precision) {
+        case PFLBM_FP64: e = run_step_kernel<PFLBM_FP64, true>(h, nullptr, nullptr, nullptr); break;
+        case PFLBM_FP32: e = run_step_kernel<PFLBM_FP32, true>(h, nullptr, nullptr, nullptr); break;
+        case PFLBM_BF16: e = run_step_kernel<PFLBM_BF16, true>(h, nullptr, nullptr, nullptr); break;
+        default: e = run_step_kernel<PFLBM_FP16, true>(h, nullptr, nullptr, nullptr); break;
+    }
     if (e == cudaSuccess) h->cur ^= 1;
     return e;
 }
 
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p)
 {
-    if (h->precision == PFLBM_FP64)
-        return run_step_kernel<double, double, false>(h, phi, u, p);
-    return run_step_kernel<float, float, false>(h, phi, u, p);
+    switch (h->precision) {
+        case PFLBM_FP64: return run_step_kernel<PFLBM_FP64, false>(h, phi, u, p);
+        case PFLBM_FP32: return run_step_kernel<PFLBM_FP32, false>(h, phi, u, p);
+        case PFLBM_BF16: return run_step_kernel<PFLBM_BF16, false>(h, phi, u, p);
+        default: return run_step_kernel<PFLBM_FP16, false>(h, phi, u, p);
+    }
 }
 
 }  // namespace pfk

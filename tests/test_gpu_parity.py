@@ -173,6 +173,27 @@ def test_contact_angle_fp32_within_half_degree():
     assert abs(s.mass() - r["mass"]) <= 1e-5 * abs(r["mass"])
 
 
+# ------------------------------------------------------- 16-bit storage --
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_16bit_storage_error_and_contact_angle(precision):
+    # f_i and g_i (i != 0) in 16 bits, g_0 32-bit fixed point, FP32 arithmetic:
+    # the error against the FP64 oracle is reported; the bar is the contact
+    # angle within 0.5 deg of the oracle's (mass within 1e-4, phi within 5e-2).
+    case = oj.case_by_name("flat60")
+    r = ref("flat60")
+    s = solver(case, precision)
+    s.step(r["steps"])
+    phi, u, p = s.get()
+    dphi = float(np.max(np.abs(phi - r["phi"])))
+    du = float(np.max(np.abs(u - r["u"])))
+    th, _, _ = s.contact_angle(case.wall)
+    print(f"{precision}: max|dphi|={dphi:.3e} max|du|={du:.3e} theta={th:.4f} "
+          f"oracle={r['theta']:.4f} mass_rel={(s.mass() - r['mass']) / r['mass']:.3e}")
+    assert abs(th - r["theta"]) < 0.5
+    assert abs(s.mass() - r["mass"]) <= 1e-4 * abs(r["mass"])
+    assert dphi < 5e-2
+
+
 # ------------------------------------------------------------ host paths --
 def test_save_load_continues_bit_exact():
     case = oj.case_by_name("flat60_short")
