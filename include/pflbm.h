@@ -185,6 +185,39 @@ size_t pflbm_footprint_bytes(int nx, int ny, int precision);
 int pflbm_save(pflbm_t* h, void* buf, size_t* len);
 int pflbm_load(pflbm_t* h, const void* buf, size_t len);
 
+/* ---- many lattices per launch ------------------------------------------
+ * A batch advances several handles (of any sizes) together: each time step
+ * is one persistent launch over a work list of (lattice, tile) items, and
+ * pairs of steps can be replayed from a captured CUDA graph. The per-node
+ * update is exactly that of pflbm_step; the paper has no batching. All
+ * handles of a batch must share precision, device and stream; the batch runs
+ * on that stream and keeps no copy of the handles' state. */
+typedef struct pflbm_batch pflbm_batch_t;
+typedef struct {
+    int ctas_per_sm;     /* persistent CTAs per SM; <= 0: as many as fit      */
+    int tiles_per_item;  /* 32 x 8 tiles of one tile column per work item     */
+    int order;           /* 0: lattice by lattice; 1: largest lattices first,
+                            items interleaved across lattices                 */
+    int use_graph;       /* replay step pairs from a captured CUDA graph      */
+} pflbm_schedule_t;
+
+/* Defaults: as many CTAs as fit, 1 tile per item, order 0, graphs on. */
+void pflbm_schedule_default(pflbm_schedule_t* s);
+/* Build a batch over hs[0..count-1] (schedule NULL: defaults). Allocates the
+ * device work list and descriptors (through hs[0]'s allocator). EINVAL if the
+ * handles differ in precision, device or stream, or repeat. */
+int pflbm_batch_create(pflbm_batch_t** out, pflbm_t* const* hs, int count, const pflbm_schedule_t* sched);
+/* Replace the members (same rules); reuses the device buffers when they are
+ * large enough. */
+int pflbm_batch_set(pflbm_batch_t* b, pflbm_t* const* hs, int count);
+/* n time steps of every member (asynchronous). Members stepped on their own
+ * in between are picked up (descriptors are rewritten). ENUMERIC if a member
+ * reported a NaN or |u| >= 0.3 earlier. */
+int pflbm_batch_step(pflbm_batch_t* b, int64_t n);
+/* Work items, persistent grid size and total nodes of the batch. */
+int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes);
+void pflbm_batch_destroy(pflbm_batch_t* b);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* pflbm_last_error(void);
 

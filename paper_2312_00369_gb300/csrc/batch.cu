@@ -1,0 +1,334 @@
+// batch.cu -- many independent lattices advanced by one persistent launch
+// per time step (the extern "C" pflbm_batch_* entry points of pflbm.h).
+//
+// A batch holds, in device memory, one step descriptor per lattice for each
+// parity of the ping-pong state (set 0: in = current copy, out = the other;
+// set 1: swapped) and a work list of (lattice, first tile) items. Each step
+// is one launch of k_step_batch over the work list; with use_graph the pair
+// of launches (set p, set 1 - p) is captured once in a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pflbm_internal.cuh"
+
+namespace pfk {
+int set_error(int code, const char* msg);
+int materialize_handle(pflbm_t* h);
+int post_status(pflbm_t* h);
+}  // namespace pfk
+
+using namespace pfk;
+
+struct pflbm_batch {
+    int precision = PFLBM_FP32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    pflbm_schedule_t sched{};
+    std::vector<pflbm_t*> hs;
+    std::vector<int> cur0;        // each lattice's state copy when descriptors were written
+    int phase = 0;                // steps taken since then, mod 2
+    size_t args_bytes = 0;
+    int cap_lattices = 0, cap_work = 0;
+    void* d_args[2] = {nullptr, nullptr};
+    int2* d_work = nullptr;
+    int n_work = 0;
+    int grid = 0;
+    long long nodes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_n_work = -1;
+    void* (*alloc_fn)(size_t, void*) = nullptr;
+    void (*free_fn)(void*, size_t, void*) = nullptr;
+    void* alloc_ctx = nullptr;
+};
+
+namespace {
+
+struct Guard {
+    int prev = -1;
+    explicit Guard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~Guard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int balloc(pflbm_batch_t* b, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (b->alloc_fn) {
+        *p = b->alloc_fn(bytes, b->alloc_ctx);
+        return *p ? PFLBM_OK : set_error(PFLBM_ENOMEM, "batch: allocator callback returned NULL");
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(PFLBM_ENOMEM, "batch: cudaMalloc failed");
+    }
+    return PFLBM_OK;
+}
+
+void bfree(pflbm_batch_t* b, void* p, size_t bytes)
+{
+    if (!p) return;
+    if (b->free_fn)
+        b->free_fn(p, bytes, b->alloc_ctx);
+    else
+        cudaFree(p);
+}
+
+void drop_graph(pflbm_batch_t* b)
+{
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+    b->graph_n_work = -1;
+}
+
+std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s)
+{
+    const int G = std::max(1, s.tiles_per_item);
+    std::vector<std::vector<int2>> per(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) {
+        int ntx = tiles_x(hs[i]->nx), nty = tiles_y(hs[i]->ny);
+        for (int by = 0; by < nty; by += G)
+            for (int bx = 0; bx < ntx; ++bx) per[i].push_back(make_int2((int)i, by * ntx + bx));
+    }
+    std::vector<int2> w;
+    if (s.order == 1) {
+        // largest lattices first, items interleaved across lattices
+        std::vector<size_t> idx(hs.size());
+        for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return per[a].size() > per[b].size(); });
+        size_t longest = idx.empty() ? 0 : per[idx[0]].size();
+        for (size_t j = 0; j < longest; ++j)
+            for (size_t i : idx)
+                if (j < per[i].size()) w.push_back(per[i][j]);
+    } else {
+        for (auto& v : per) w.insert(w.end(), v.begin(), v.end());
+    }
+    return w;
+}
+
+int upload(pflbm_batch_t* b)
+{
+    const int n = (int)b->hs.size();
+    std::vector<unsigned char> a0(b->args_bytes * n), a1(b->args_bytes * n);
+    b->cur0.resize(n);
+    b->nodes = 0;
+    for (int i = 0; i < n; ++i) {
+        pflbm_t* h = b->hs[i];
+        write_step_args(h, 0, a0.data() + b->args_bytes * i);
+        write_step_args(h, 1, a1.data() + b->args_bytes * i);
+        b->cur0[i] = h->cur;
+        b->nodes += (long long)h->nx * h->ny;
+    }
+    std::vector<int2> w = build_work(b->hs, b->sched);
+    if (n > b->cap_lattices) {
+        int cap = std::max(n, 2 * b->cap_lattices);
+        for (int k = 0; k < 2; ++k) {
+            bfree(b, b->d_args[k], b->args_bytes * b->cap_lattices);
+            b->d_args[k] = nullptr;
+        }
+        for (int k = 0; k < 2; ++k)
+            if (int rc = balloc(b, &b->d_args[k], b->args_bytes * cap)) return rc;
+        b->cap_lattices = cap;
+        drop_graph(b);
+    }
+    if ((int)w.size() > b->cap_work) {
+        int cap = std::max((int)w.size(), 2 * b->cap_work);
+        bfree(b, b->d_work, sizeof(int2) * b->cap_work);
+        b->d_work = nullptr;
+        void* p;
+        if (int rc = balloc(b, &p, sizeof(int2) * cap)) return rc;
+        b->d_work = (int2*)p;
+        b->cap_work = cap;
+        drop_graph(b);
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_args[0], a0.data(), a0.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_args[1], a1.data(), a1.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !w.empty())
+        e = cudaMemcpyAsync(b->d_work, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice, b->stream);
+    // the host vectors go out of scope on return: finish the copies first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
+    b->n_work = (int)w.size();
+    b->phase = 0;
+    int per_sm = batch_max_ctas_per_sm(b->precision);
+    if (b->sched.ctas_per_sm > 0) per_sm = std::min(per_sm, b->sched.ctas_per_sm);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->grid = std::max(1, std::min(b->n_work, std::max(1, per_sm) * std::max(1, sms)));
+    return PFLBM_OK;
+}
+
+int check_members(pflbm_t* const* hs, int count, int precision, int device, cudaStream_t stream)
+{
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i]) return set_error(PFLBM_EINVAL, "batch: NULL handle");
+        if (hs[i]->precision != precision || hs[i]->device != device || hs[i]->stream != stream)
+            return set_error(PFLBM_EINVAL, "batch: all handles need the same precision, device and stream");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return set_error(PFLBM_EINVAL, "batch: a handle appears twice");
+    }
+    return PFLBM_OK;
+}
+
+cudaError_t launch_set(pflbm_batch_t* b, int set)
+{
+    return launch_step_batch(b->precision, b->d_args[set], b->d_work, b->n_work, std::max(1, b->sched.tiles_per_item),
+                             b->grid, b->stream);
+}
+
+int ensure_graph(pflbm_batch_t* b)
+{
+    if (b->graph_exec && b->graph_n_work == b->n_work) return PFLBM_OK;
+    drop_graph(b);
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
+    cudaError_t e1 = launch_set(b, 0);
+    cudaError_t e2 = launch_set(b, 1);
+    e = cudaStreamEndCapture(b->stream, &b->graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
+        drop_graph(b);
+        return set_error(PFLBM_ECUDA, "batch: graph capture failed");
+    }
+    e = cudaGraphInstantiate(&b->graph_exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        drop_graph(b);
+        return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
+    }
+    b->graph_n_work = b->n_work;
+    return PFLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pflbm_schedule_default(pflbm_schedule_t* s)
+{
+    if (!s) return;
+    s->ctas_per_sm = 0;
+    s->tiles_per_item = 1;
+    s->order = 0;
+    s->use_graph = 1;
+}
+
+int pflbm_batch_create(pflbm_batch_t** out, pflbm_t* const* hs, int count, const pflbm_schedule_t* sched)
+{
+    if (!out) return set_error(PFLBM_EINVAL, "batch: NULL out");
+    *out = nullptr;
+    if (!hs || count < 1) return set_error(PFLBM_EINVAL, "batch: need at least one handle");
+    if (!hs[0]) return set_error(PFLBM_EINVAL, "batch: NULL handle");
+    if (int rc = check_members(hs, count, hs[0]->precision, hs[0]->device, hs[0]->stream)) return rc;
+    pflbm_batch_t* b = new pflbm_batch();
+    b->precision = hs[0]->precision;
+    b->device = hs[0]->device;
+    b->stream = hs[0]->stream;
+    b->alloc_fn = hs[0]->alloc_fn;
+    b->free_fn = hs[0]->free_fn;
+    b->alloc_ctx = hs[0]->alloc_ctx;
+    pflbm_schedule_default(&b->sched);
+    if (sched) b->sched = *sched;
+    if (b->sched.tiles_per_item < 1) b->sched.tiles_per_item = 1;
+    b->args_bytes = step_args_bytes(b->precision);
+    b->hs.assign(hs, hs + count);
+    Guard g(b->device);
+    if (int rc = upload(b)) {
+        pflbm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return PFLBM_OK;
+}
+
+int pflbm_batch_set(pflbm_batch_t* b, pflbm_t* const* hs, int count)
+{
+    if (!b || !hs || count < 1) return set_error(PFLBM_EINVAL, "batch: invalid arguments");
+    if (int rc = check_members(hs, count, b->precision, b->device, b->stream)) return rc;
+    Guard g(b->device);
+    b->hs.assign(hs, hs + count);
+    return upload(b);
+}
+
+int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
+{
+    if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
+    if (n < 0) return set_error(PFLBM_EINVAL, "batch: negative step count");
+    if (n == 0) return PFLBM_OK;
+    Guard g(b->device);
+    bool stale = false;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        pflbm_t* h = b->hs[i];
+        if (h->hstatus && h->hstatus[0] != 0)
+            return set_error(PFLBM_ENUMERIC, "batch: NaN or |u| >= 0.3 detected on the device");
+        if (h->init_pending) {
+            if (int rc = materialize_handle(h)) return rc;
+        }
+        if (h->cur != (b->cur0[i] ^ b->phase)) stale = true;
+    }
+    if (stale) {  // a member was stepped on its own: rewrite the descriptors
+        if (int rc = upload(b)) return rc;
+    }
+    int64_t left = n;
+    if (b->phase == 1) {
+        cudaError_t e = launch_set(b, 1);
+        if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
+        b->phase = 0;
+        --left;
+    }
+    if (b->sched.use_graph && left >= 2) {
+        if (int rc = ensure_graph(b)) return rc;
+        for (; left >= 2; left -= 2) {
+            cudaError_t e = cudaGraphLaunch(b->graph_exec, b->stream);
+            if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
+        }
+    }
+    while (left > 0) {
+        cudaError_t e = launch_set(b, b->phase);
+        if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
+        b->phase ^= 1;
+        --left;
+    }
+    for (pflbm_t* h : b->hs) {
+        if (n & 1) h->cur ^= 1;
+        h->steps += n;
+        h->replace_phi = true;
+        if (int rc = post_status(h)) return rc;
+    }
+    // invariant: every member's current copy is cur0[i] ^ phase
+    return PFLBM_OK;
+}
+
+int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes)
+{
+    if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
+    if (n_work) *n_work = b->n_work;
+    if (grid) *grid = b->grid;
+    if (nodes) *nodes = b->nodes;
+    return PFLBM_OK;
+}
+
+void pflbm_batch_destroy(pflbm_batch_t* b)
+{
+    if (!b) return;
+    Guard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (int k = 0; k < 2; ++k) bfree(b, b->d_args[k], b->args_bytes * b->cap_lattices);
+    bfree(b, b->d_work, sizeof(int2) * b->cap_work);
+    delete b;
+}
+
+}  // extern "C"

@@ -201,6 +201,8 @@ int ensure_out(pflbm_t* h)
 
 namespace pfk {
 int set_error(int code, const char* msg) { return fail(code, msg); }
+int materialize_handle(pflbm_t* h) { return materialize(h); }
+int post_status(pflbm_t* h) { return post_status_copy(h); }
 
 size_t elem_size(int precision)
 {

@@ -92,14 +92,19 @@ cudaError_t launch_classify(pflbm_t* h);
 cudaError_t launch_wet(pflbm_t* h);
 cudaError_t launch_links(pflbm_t* h, uint16_t* unknown, uint16_t* doubly);
 cudaError_t launch_tile_flags(pflbm_t* h);
-inline int tiles_x(int nx) { return (nx + TX - 1) / TX; }
-inline int tiles_y(int ny) { return (ny + TY - 1) / TY; }
+__host__ __device__ inline int tiles_x(int nx) { return (nx + TX - 1) / TX; }
+__host__ __device__ inline int tiles_y(int ny) { return (ny + TY - 1) / TY; }
 
 // step.cu
 cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, int replace);
 cudaError_t launch_init_populations(pflbm_t* h);
 cudaError_t launch_step(pflbm_t* h);
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p);
+size_t step_args_bytes(int precision);
+void write_step_args(pflbm_t* h, int flip, void* dst);   // flip: in/out swapped
+cudaError_t launch_step_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,
+                              int grid, cudaStream_t stream);
+int batch_max_ctas_per_sm(int precision);
 
 // diag.cu
 cudaError_t launch_mass(pflbm_t* h, double* d_out);

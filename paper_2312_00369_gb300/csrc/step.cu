@@ -285,17 +285,18 @@ __device__ __forceinline__ typename Store<PREC>::C collide_g_dir(const StepArgs<
     return C(0);
 }
 
+// One tile (bx, by) of one lattice: the whole time step for its nodes.
+// Called by every thread of the CTA; the shared tiles are the caller's.
 template <int PREC, bool COLLIDE>
-__global__ void __launch_bounds__(TX * TY) k_step(StepArgs<PREC> a)
+__device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int by, int ntx,
+                                          uint8_t (*s_cls)[TX + 6], typename Store<PREC>::C (*s_phi)[TX + 4])
 {
     using T = Store<PREC>;
     using C = typename T::C;
-    __shared__ uint8_t s_cls[TY + 6][TX + 6];
-    __shared__ C s_phi[TY + 4][TX + 4];
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     C g[9];
     typename T::G0T g0raw;
-    const bool fluid_tile = a.tiles[blockIdx.y * gridDim.x + blockIdx.x] != 0;
+    const bool fluid_tile = a.tiles[by * ntx + bx] != 0;
     if (fluid_tile)
         tile_prologue_fluid<PREC>(a, s_phi, x0, y0, g, g0raw);
     else
@@ -387,6 +388,45 @@ __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<PREC> a)
         a.out.g0[k] = T::g0_add(g0raw, T::kAbsorb ? d0 + resid : d0, a.status);
     }
     a.sprev[k] = s_now;
+}
+
+template <int PREC, bool COLLIDE>
+__global__ void __launch_bounds__(TX * TY) k_step(StepArgs<PREC> a)
+{
+    __shared__ uint8_t s_cls[TY + 6][TX + 6];
+    __shared__ typename Store<PREC>::C s_phi[TY + 4][TX + 4];
+    step_tile<PREC, COLLIDE>(a, blockIdx.x, blockIdx.y, gridDim.x, s_cls, s_phi);
+}
+
+// Persistent step over many lattices: work item w = (instance, first tile);
+// an item covers `group` tiles of one tile column, top to bottom. CTAs take
+// items w = blockIdx.x, blockIdx.x + gridDim.x, ...
+template <int PREC>
+__global__ void __launch_bounds__(TX * TY) k_step_batch(const StepArgs<PREC>* __restrict__ args,
+                                                        const int2* __restrict__ work, int n_work, int group)
+{
+    __shared__ uint8_t s_cls[TY + 6][TX + 6];
+    __shared__ typename Store<PREC>::C s_phi[TY + 4][TX + 4];
+    // the item's lattice descriptor lives in shared memory (read field by
+    // field where used) rather than in registers
+    __shared__ __align__(16) unsigned char s_args_raw[sizeof(StepArgs<PREC>)];
+    const StepArgs<PREC>& a = *reinterpret_cast<const StepArgs<PREC>*>(s_args_raw);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const int2 it = work[w];
+        {
+            const int* src = reinterpret_cast<const int*>(args + it.x);
+            int* dst = reinterpret_cast<int*>(s_args_raw);
+            for (int i = tid; i < (int)(sizeof(StepArgs<PREC>) / sizeof(int)); i += TX * TY) dst[i] = src[i];
+        }
+        __syncthreads();
+        const int ntx = tiles_x(a.nx), nty = tiles_y(a.ny);
+        const int bx = it.y % ntx, by0 = it.y / ntx;
+        for (int gi = 0; gi < group && by0 + gi < nty; ++gi) {
+            step_tile<PREC, true>(a, bx, by0 + gi, ntx, s_cls, s_phi);
+            __syncthreads();   // the next tile reuses the shared tiles and descriptor
+        }
+    }
 }
 
 template <int PREC>
@@ -614,6 +654,74 @@ cudaError_t launch_step(pflbm_t* h)
     }
     if (e == cudaSuccess) h->cur ^= 1;
     return e;
+}
+
+size_t step_args_bytes(int precision)
+{
+    switch (precision) {
+        case PFLBM_FP64: return sizeof(StepArgs<PFLBM_FP64>);
+        case PFLBM_FP32: return sizeof(StepArgs<PFLBM_FP32>);
+        case PFLBM_BF16: return sizeof(StepArgs<PFLBM_BF16>);
+        default: return sizeof(StepArgs<PFLBM_FP16>);
+    }
+}
+
+namespace {
+template <int PREC>
+void write_args_prec(pflbm_t* h, int flip, void* dst)
+{
+    StepArgs<PREC> a = make_args<PREC>(h);
+    if (flip) {
+        Planes<PREC> t = a.in;
+        a.in = a.out;
+        a.out = t;
+    }
+    *(StepArgs<PREC>*)dst = a;
+}
+}  // namespace
+
+void write_step_args(pflbm_t* h, int flip, void* dst)
+{
+    switch (h->precision) {
+        case PFLBM_FP64: write_args_prec<PFLBM_FP64>(h, flip, dst); break;
+        case PFLBM_FP32: write_args_prec<PFLBM_FP32>(h, flip, dst); break;
+        case PFLBM_BF16: write_args_prec<PFLBM_BF16>(h, flip, dst); break;
+        default: write_args_prec<PFLBM_FP16>(h, flip, dst); break;
+    }
+}
+
+cudaError_t launch_step_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,
+                              int grid, cudaStream_t stream)
+{
+    dim3 b(TX, TY);
+    switch (precision) {
+        case PFLBM_FP64:
+            k_step_batch<PFLBM_FP64><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_FP64>*)d_args, d_work, n_work, group);
+            break;
+        case PFLBM_FP32:
+            k_step_batch<PFLBM_FP32><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_FP32>*)d_args, d_work, n_work, group);
+            break;
+        case PFLBM_BF16:
+            k_step_batch<PFLBM_BF16><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_BF16>*)d_args, d_work, n_work, group);
+            break;
+        default:
+            k_step_batch<PFLBM_FP16><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_FP16>*)d_args, d_work, n_work, group);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+int batch_max_ctas_per_sm(int precision)
+{
+    int n = 0;
+    cudaError_t e;
+    switch (precision) {
+        case PFLBM_FP64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<PFLBM_FP64>, TX * TY, 0); break;
+        case PFLBM_FP32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<PFLBM_FP32>, TX * TY, 0); break;
+        case PFLBM_BF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<PFLBM_BF16>, TX * TY, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<PFLBM_FP16>, TX * TY, 0); break;
+    }
+    return e == cudaSuccess ? n : 1;
 }
 
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p)

@@ -44,6 +44,11 @@ class Params(ctypes.Structure):
                 ("alloc_ctx", ctypes.c_void_p)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("tiles_per_item", ctypes.c_int),
+                ("order", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
 class Wall(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("px", ctypes.c_double), ("py", ctypes.c_double),
                 ("nx", ctypes.c_double), ("ny", ctypes.c_double), ("r", ctypes.c_double),
@@ -83,6 +88,13 @@ _SIGS = {
     "pflbm_save": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "pflbm_load": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
     "pflbm_last_error": (ctypes.c_char_p, []),
+    "pflbm_schedule_default": (None, [ctypes.POINTER(Schedule)]),
+    "pflbm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_H),
+                                          ctypes.c_int, ctypes.POINTER(Schedule)]),
+    "pflbm_batch_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_H), ctypes.c_int]),
+    "pflbm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "pflbm_batch_info": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, ctypes.POINTER(ctypes.c_int64)]),
+    "pflbm_batch_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -296,3 +308,53 @@ class Solver:
     def load(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(lib().pflbm_load(self._h, buf, len(blob)))
+
+
+def schedule(ctas_per_sm=0, tiles_per_item=1, order=0, use_graph=1):
+    s = Schedule()
+    lib().pflbm_schedule_default(ctypes.byref(s))
+    s.ctas_per_sm, s.tiles_per_item, s.order, s.use_graph = (int(ctas_per_sm), int(tiles_per_item),
+                                                             int(order), int(use_graph))
+    return s
+
+
+class Batch:
+    """Several Solvers advanced together (``pflbm_batch_t``). The solvers must
+    share precision, device and stream; they stay alive while the batch
+    uses them."""
+
+    def __init__(self, solvers, sched=None):
+        self._solvers = list(solvers)
+        arr = (_H * len(self._solvers))(*[s.handle for s in self._solvers])
+        self._arr = arr
+        b = ctypes.c_void_p()
+        sc = sched if sched is not None else schedule()
+        _check(lib().pflbm_batch_create(ctypes.byref(b), arr, len(self._solvers), ctypes.byref(sc)))
+        self._b = b
+        self.sched = sc
+
+    def set(self, solvers):
+        self._solvers = list(solvers)
+        self._arr = (_H * len(self._solvers))(*[s.handle for s in self._solvers])
+        _check(lib().pflbm_batch_set(self._b, self._arr, len(self._solvers)))
+
+    def step(self, n=1):
+        _check(lib().pflbm_batch_step(self._b, int(n)))
+
+    def info(self):
+        nw, grid, nodes = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib().pflbm_batch_info(self._b, ctypes.byref(nw), ctypes.byref(grid),
+                                      ctypes.byref(nodes)))
+        return dict(n_work=nw.value, grid=grid.value, nodes=nodes.value)
+
+    def close(self):
+        b = getattr(self, "_b", None)
+        if b:
+            lib().pflbm_batch_destroy(b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
