@@ -172,6 +172,9 @@ void pflbm_lattice(int cx[9], int cy[9]);
 
 /* Synchronise the handle's stream and report ENUMERIC / ECUDA if any. */
 int pflbm_check(pflbm_t* h);
+/* The status last copied back from the device, without waiting: PFLBM_OK or
+ * PFLBM_ENUMERIC (may lag the device by the steps still in flight). */
+int pflbm_status(const pflbm_t* h);
 /* Steps taken since the last initialisation. */
 int64_t pflbm_steps(const pflbm_t* h);
 

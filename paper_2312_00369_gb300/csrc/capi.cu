@@ -548,6 +548,12 @@ int pflbm_check(pflbm_t* h)
 
 int64_t pflbm_steps(const pflbm_t* h) { return h ? h->steps : -1; }
 
+int pflbm_status(const pflbm_t* h)
+{
+    if (!h) return PFLBM_EINVAL;
+    return (h->hstatus && h->hstatus[0] != 0) ? PFLBM_ENUMERIC : PFLBM_OK;
+}
+
 namespace {
 struct Blob {
     uint64_t magic;

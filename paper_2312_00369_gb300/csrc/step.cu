@@ -156,6 +156,47 @@ __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
     __syncthreads();
 }
 
+// phi on the ring of width H around the tile (one position per thread).
+template <int PREC, int H>
+__device__ __forceinline__ void ring_phi(const StepArgs<PREC>& a, const uint8_t (*s_cls)[TX + 6],
+                                         typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0, int tid,
+                                         bool tiny)
+{
+    using C = typename Store<PREC>::C;
+    constexpr int RW = TX + 2 * H, NTOP = H * RW, NSIDE = H * TY;
+    static_assert(2 * NTOP + 2 * NSIDE <= TX * TY, "one ring position per thread");
+    if (tid >= 2 * NTOP + 2 * NSIDE) return;
+    int py, px;
+    if (tid < NTOP) {
+        py = 2 - H + tid / RW;
+        px = 2 - H + tid % RW;
+    } else if (tid < 2 * NTOP) {
+        const int t = tid - NTOP;
+        py = TY + 2 + t / RW;
+        px = 2 - H + t % RW;
+    } else if (tid < 2 * NTOP + NSIDE) {
+        const int t = tid - 2 * NTOP;
+        py = 2 + t / H;
+        px = 2 - H + t % H;
+    } else {
+        const int t = tid - 2 * NTOP - NSIDE;
+        py = 2 + t / H;
+        px = TX + 2 + t % H;
+    }
+    const int sy = py + 1, sx = px + 1;
+    C ph = C(0);
+    const uint8_t c = s_cls[sy][sx];
+    if (zeta_of(c)) {
+        const int gy = y0 - 2 + py, xr = x0 - 2 + px;
+        const int gx = tiny ? wrapn(xr, a.nx) : wrap1(xr, a.nx);
+        if (c & F_LINK)
+            ph = pulled_phi<PREC, true>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
+        else
+            ph = pulled_phi<PREC, false>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
+    }
+    s_phi[py][px] = ph;
+}
+
 // General prologue: class tile (halo 3) and phi tile with ghost values. A
 // tile needs phi two nodes out only when a ghost node lies next to one of its
 // nodes (the ghost average reaches one node further); otherwise one ring.
@@ -170,9 +211,12 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
     const int tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
 
+    // one conditional wrap covers the tile and its halo unless nx is tiny
+    const bool tiny = nx < TX + 8;
+    auto wx = [&](int x) { return tiny ? wrapn(x, nx) : wrap1(x, nx); };
     for (int p = tid; p < (TY + 6) * (TX + 6); p += TX * TY) {
         int py = p / (TX + 6), px = p - py * (TX + 6);
-        int gy = y0 - 3 + py, gx = wrapn(x0 - 3 + px, nx);
+        int gy = y0 - 3 + py, gx = wx(x0 - 3 + px);
         s_cls[py][px] = (gy < 0 || gy >= ny) ? (uint8_t)CLS_OUT : a.cls[gy * pitch + gx];
     }
     __syncthreads();
@@ -186,7 +230,7 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
     // own node (a tile that runs past x = nx - 1 holds wrapped nodes there:
     // they are computed like halo nodes but not collided)
     {
-        int gx = wrapn(x0 + tx, nx), gy = y0 + ty;
+        int gx = wx(x0 + tx), gy = y0 + ty;
         C ph = C(0);
         if (gy < ny && zeta_of(own)) {
             if (own & F_LINK)
@@ -197,23 +241,11 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
         }
         s_phi[ty + 2][tx + 2] = ph;
     }
-    // halo ring
-    const int lo = 2 - halo, wy = TY + 2 * halo, wx = TX + 2 * halo;
-    for (int p = tid; p < wy * wx; p += TX * TY) {
-        int py = p / wx + lo, px = p % wx + lo;
-        if (py >= 2 && py < TY + 2 && px >= 2 && px < TX + 2) continue;
-        int sy = py + 1, sx = px + 1;
-        C ph = C(0);
-        const uint8_t c = s_cls[sy][sx];
-        if (zeta_of(c)) {
-            int gy = y0 - 2 + py, gx = wrapn(x0 - 2 + px, nx);
-            if (c & F_LINK)
-                ph = pulled_phi<PREC, true>(a.in, s_cls, sy, sx, gx, gy, nx, pitch, a.plane);
-            else
-                ph = pulled_phi<PREC, false>(a.in, s_cls, sy, sx, gx, gy, nx, pitch, a.plane);
-        }
-        s_phi[py][px] = ph;
-    }
+    // halo ring of width 1 or 2: top rows, bottom rows, left and right columns
+    if (halo == 1)
+        ring_phi<PREC, 1>(a, s_cls, s_phi, x0, y0, tid, tiny);
+    else
+        ring_phi<PREC, 2>(a, s_cls, s_phi, x0, y0, tid, tiny);
     __syncthreads();
     if (halo == 1) return;
 
@@ -402,7 +434,7 @@ __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<PREC> a)
 // an item covers `group` tiles of one tile column, top to bottom. CTAs take
 // items w = blockIdx.x, blockIdx.x + gridDim.x, ...
 template <int PREC>
-__global__ void __launch_bounds__(TX * TY) k_step_batch(const StepArgs<PREC>* __restrict__ args,
+__global__ void __launch_bounds__(TX * TY, PREC == PFLBM_FP64 ? 3 : 5) k_step_batch(const StepArgs<PREC>* __restrict__ args,
                                                         const int2* __restrict__ work, int n_work, int group)
 {
     __shared__ uint8_t s_cls[TY + 6][TX + 6];

@@ -7,9 +7,11 @@ cannot be loaded, every call raises: there is no fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import re
+import weakref
 
 import numpy as np
 
@@ -58,6 +60,24 @@ class Wall(ctypes.Structure):
 
 _lib = None
 _H = ctypes.c_void_p
+# live handles, closed before the interpreter (and PyTorch, whose allocator
+# the handles call back into) shuts down
+_LIVE_BATCHES = weakref.WeakSet()
+_LIVE_SOLVERS = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    for b in list(_LIVE_BATCHES):
+        try:
+            b.close()
+        except Exception:
+            pass
+    for s in list(_LIVE_SOLVERS):
+        try:
+            s.close()
+        except Exception:
+            pass
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -84,6 +104,7 @@ _SIGS = {
     "pflbm_lattice": (None, [_ip, _ip]),
     "pflbm_check": (ctypes.c_int, [_H]),
     "pflbm_steps": (ctypes.c_int64, [_H]),
+    "pflbm_status": (ctypes.c_int, [_H]),
     "pflbm_footprint_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "pflbm_save": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "pflbm_load": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
@@ -171,7 +192,10 @@ class TorchAllocator:
 
     def free(self, ptr, nbytes, ctx):
         if ptr:
-            self.torch.cuda.caching_allocator_delete(ptr)
+            try:
+                self.torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
 
 
 class Solver:
@@ -219,6 +243,7 @@ class Solver:
         _check(L.pflbm_create_ex(ctypes.byref(h), ctypes.byref(p)))
         self._h = h
         self.W = W
+        _LIVE_SOLVERS.add(self)
 
     # -- lifetime ------------------------------------------------------------
     def close(self):
@@ -294,6 +319,13 @@ class Solver:
     def check(self):
         _check(lib().pflbm_check(self._h))
 
+    def status(self, wait=False):
+        """Status code (0 or ENUMERIC) without raising; wait=True synchronises
+        first, otherwise the last value copied back is returned."""
+        if wait:
+            return int(lib().pflbm_check(self._h))
+        return int(lib().pflbm_status(self._h))
+
     @property
     def steps(self):
         return int(lib().pflbm_steps(self._h))
@@ -332,6 +364,7 @@ class Batch:
         _check(lib().pflbm_batch_create(ctypes.byref(b), arr, len(self._solvers), ctypes.byref(sc)))
         self._b = b
         self.sched = sc
+        _LIVE_BATCHES.add(self)
 
     def set(self, solvers):
         self._solvers = list(solvers)
