@@ -207,8 +207,10 @@ typedef struct {
 /* Defaults: as many CTAs as fit, 1 tile per item, order 0, graphs on. */
 void pflbm_schedule_default(pflbm_schedule_t* s);
 /* Build a batch over hs[0..count-1] (schedule NULL: defaults). Allocates the
- * device work list and descriptors (through hs[0]'s allocator). EINVAL if the
- * handles differ in precision, device or stream, or repeat. */
+ * device work list and descriptors with cudaMalloc. EINVAL if the handles
+ * differ in precision, device or stream, or repeat. Members may be destroyed
+ * while the batch lives, as long as pflbm_batch_set drops them before the
+ * next pflbm_batch_step. */
 int pflbm_batch_create(pflbm_batch_t** out, pflbm_t* const* hs, int count, const pflbm_schedule_t* sched);
 /* Replace the members (same rules); reuses the device buffers when they are
  * large enough. */

@@ -236,9 +236,8 @@ int pflbm_batch_create(pflbm_batch_t** out, pflbm_t* const* hs, int count, const
     b->precision = hs[0]->precision;
     b->device = hs[0]->device;
     b->stream = hs[0]->stream;
-    b->alloc_fn = hs[0]->alloc_fn;
-    b->free_fn = hs[0]->free_fn;
-    b->alloc_ctx = hs[0]->alloc_ctx;
+    // the batch's own small buffers come from cudaMalloc: a member's
+    // allocator may belong to a handle that is destroyed while the batch lives
     pflbm_schedule_default(&b->sched);
     if (sched) b->sched = *sched;
     if (b->sched.tiles_per_item < 1) b->sched.tiles_per_item = 1;

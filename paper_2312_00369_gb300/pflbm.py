@@ -173,29 +173,40 @@ def pflbm_phi_mass_noalloc(d_phi, d_zeta, nx, ny, d_out, stream=None):
                                         None if stream is None else ctypes.c_void_p(stream)))
 
 
-class TorchAllocator:
-    """Device memory from PyTorch's caching allocator for one handle."""
+# One pair of allocator callbacks for the whole process (ctypes thunks must
+# outlive every handle that may call them); ctx selects (device, stream).
+_ALLOC_CTX = {}
 
-    def __init__(self, device, stream):
+
+def _torch_alloc(nbytes, ctx):
+    try:
         import torch
-        self.torch = torch
-        self.device = device
-        self.stream = stream
-        self._alloc = _ALLOC(self.alloc)
-        self._free = _FREE(self.free)
+        dev, stream = _ALLOC_CTX[int(ctx or 0)]
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream))
+    except Exception:
+        return None
 
-    def alloc(self, nbytes, ctx):
+
+def _torch_free(ptr, nbytes, ctx):
+    if ptr:
         try:
-            return int(self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            import torch
+            torch.cuda.caching_allocator_delete(ptr)
         except Exception:
-            return None
+            pass
 
-    def free(self, ptr, nbytes, ctx):
-        if ptr:
-            try:
-                self.torch.cuda.caching_allocator_delete(ptr)
-            except Exception:
-                pass
+
+_TORCH_ALLOC = _ALLOC(_torch_alloc)
+_TORCH_FREE = _FREE(_torch_free)
+
+
+def _alloc_ctx(device, stream):
+    key = len(_ALLOC_CTX) + 1
+    for k, v in _ALLOC_CTX.items():
+        if v == (device, stream):
+            return k
+    _ALLOC_CTX[key] = (device, stream)
+    return key
 
 
 class Solver:
@@ -234,11 +245,10 @@ class Solver:
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.device = dev
         p.stream = ctypes.c_void_p(stream.cuda_stream)
-        self._allocator = None
         if torch_memory:
-            self._allocator = TorchAllocator(dev, stream.cuda_stream)
-            p.alloc = self._allocator._alloc
-            p.free = self._allocator._free
+            p.alloc = _TORCH_ALLOC
+            p.free = _TORCH_FREE
+            p.alloc_ctx = ctypes.c_void_p(_alloc_ctx(dev, stream.cuda_stream))
         h = _H()
         _check(L.pflbm_create_ex(ctypes.byref(h), ctypes.byref(p)))
         self._h = h
