@@ -75,6 +75,19 @@ typedef struct {
     void* (*alloc)(size_t bytes, void* ctx);
     void (*free)(void* ptr, size_t bytes, void* ctx);
     void* alloc_ctx;
+    /* Variable viscosity (Sec. 2.1.1): nu(phi) = phi (nu_l - nu_g) + nu_g,
+     * tau_f(x) = nu(phi(x)) / c_s^2 + 1/2 (Sec. 2.1.2) at every node. Used
+     * when both are > 0; otherwise the uniform tau_f above. */
+    double nu_l, nu_g;
+    /* Body force F_b = rho g (Sec. 2.1.1, F = F_s + F_b in Eq. GGi):
+     * a uniform acceleration (gx, gy); 0 by default. */
+    double gx, gy;
+    /* The (1/2) dt^2 dG_i/dt term of Eq. BGK: 0 = backward difference
+     * (1/2)[G_i(t) - G_i(t-1)] (default); 1 = omitted, source G_i(t) only
+     * (no u.grad(phi) history is read or written). The paper does not say
+     * how the derivative is discretised; the backward difference lets
+     * period-2-in-time modes grow after ~2e4 steps in some cases. */
+    int dgdt_mode;
 } pflbm_params_t;
 
 /* Flat, inclined or circular wall for the contact-angle fit. type 0: the

@@ -44,6 +44,9 @@ def lib():
         L.or_create.argtypes = ([ctypes.c_int] * 3 + [_u8p, ctypes.c_double, _dp]
                                 + [ctypes.c_double] * 7)
         L.or_destroy.argtypes = [ctypes.c_void_p]
+        L.or_set_viscosity.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.or_set_body_force.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.or_set_dgdt.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_params.argtypes = [ctypes.c_void_p, _dp]
         L.or_geometry.argtypes = [ctypes.c_void_p, _u8p, _u8p, _dp, _dp, _u16p, _u16p]
         L.or_init_droplet.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 3
@@ -203,6 +206,15 @@ class Oracle:
         lib().or_geometry(self._h, _p(cls, _u8p), _p(zeta, _u8p), _p(eps), _p(av),
                           _p(un, _u16p), _p(db, _u16p))
         return dict(cls=cls, zeta=zeta, eps=eps, av=av, unknown=un, doubly=db)
+
+    def set_viscosity(self, nu_l, nu_g):
+        lib().or_set_viscosity(self._h, nu_l, nu_g)
+
+    def set_body_force(self, gx, gy):
+        lib().or_set_body_force(self._h, gx, gy)
+
+    def set_dgdt(self, mode):
+        lib().or_set_dgdt(self._h, int(mode))
 
     def init_droplet(self, x0, y0, R):
         lib().or_init_droplet(self._h, x0, y0, R)

@@ -27,6 +27,10 @@
  *      (zeta(x_b + c_i) = 0) it takes the node's own post-collision f*_{i'}.
  *   R7 initial state: u = 0, p = 0, so f_i = f_i^eq(0, 0) = 0 and
  *      g_i = g_i^eq(phi_0, mu_0).
+ *   R8 body force: F = F_s + F_b with F_b = rho g (a uniform acceleration);
+ *      variable viscosity: nu(phi) = phi (nu_l - nu_g) + nu_g (Sec. 2.1.1)
+ *      gives tau_f(x) = nu(phi(x)) / c_s^2 + 1/2 (Sec. 2.1.2), used in the
+ *      f collision and in the prefactor of Eq. GGi at that node.
  */
 #include "pflbm_oracle.h"
 
@@ -185,6 +189,9 @@ struct or_solver {
     long N;
     double sigma, W, M, tau_f, tau_g, rho_l, rho_g;
     double beta, kappa, alpha;
+    double nu_l, nu_g;   /* > 0: variable viscosity (reading R8) */
+    double gx, gy;       /* body acceleration */
+    int dgdt;            /* 0: (1/2) dG/dt as a backward difference (R4); 1: omitted */
     uint8_t* cls;
     uint8_t* zeta;
     double* eps;
@@ -368,6 +375,33 @@ void or_destroy(or_solver* s)
     free(s);
 }
 
+void or_set_viscosity(or_solver* s, double nu_l, double nu_g)
+{
+    s->nu_l = nu_l;
+    s->nu_g = nu_g;
+}
+
+void or_set_dgdt(or_solver* s, int mode)
+{
+    s->dgdt = mode;
+}
+
+void or_set_body_force(or_solver* s, double gx, double gy)
+{
+    s->gx = gx;
+    s->gy = gy;
+}
+
+/* tau_f at a node (reading R8). */
+static double tau_f_at(const or_solver* s, long k)
+{
+    if (s->nu_l > 0 && s->nu_g > 0) {
+        double nu = s->phi[k] * (s->nu_l - s->nu_g) + s->nu_g;
+        return nu / CS2 + 0.5;
+    }
+    return s->tau_f;
+}
+
 void or_params(const or_solver* s, double out[4])
 {
     out[0] = s->beta;
@@ -478,7 +512,8 @@ static void hydro_moments(or_solver* s)
         for (int i = 0; i < Q; ++i) fk[i] = s->f[(long)i * s->N + k];
         double rho = s->phi[k] * drho + s->rho_g;
         double drx = drho * s->gpx[k], dry = drho * s->gpy[k];
-        double Fx = s->mu[k] * s->gpx[k], Fy = s->mu[k] * s->gpy[k];
+        /* F = F_s + F_b, F_s = mu grad(phi), F_b = rho g */
+        double Fx = s->mu[k] * s->gpx[k] + rho * s->gx, Fy = s->mu[k] * s->gpy[k] + rho * s->gy;
         or_velocity_pressure(fk, rho, drx, dry, Fx, Fy, &s->ux[k], &s->uy[k], &s->p[k]);
     }
 }
@@ -590,14 +625,15 @@ static void one_step(or_solver* s)
         double ux = s->ux[k], uy = s->uy[k];
         double rho = ph * drho + s->rho_g;
         double drx = drho * s->gpx[k], dry = drho * s->gpy[k];
-        double Fx = mu * s->gpx[k], Fy = mu * s->gpy[k];
+        double Fx = mu * s->gpx[k] + rho * s->gx, Fy = mu * s->gpy[k] + rho * s->gy;
+        double tau = tau_f_at(s, k);
 
         double feq[Q], Fi[Q];
         or_feq(s->p[k], rho, ux, uy, feq);
-        or_force(s->tau_f, ux, uy, drx, dry, Fx, Fy, Fi);
+        or_force(tau, ux, uy, drx, dry, Fx, Fy, Fi);
         for (int i = 0; i < Q; ++i) {
             double fi = s->f[(long)i * N + k];
-            s->fpost[(long)i * N + k] = fi - (fi - feq[i]) / s->tau_f + Fi[i];
+            s->fpost[(long)i * N + k] = fi - (fi - feq[i]) / tau + Fi[i];
         }
 
         double s_now = ux * s->gpx[k] + uy * s->gpy[k];
@@ -608,7 +644,7 @@ static void one_step(or_solver* s)
         or_source(s_old, G_old);
         for (int i = 0; i < Q; ++i) {
             double gi = s->g[(long)i * N + k];
-            double src = G_now[i] + 0.5 * (G_now[i] - G_old[i]);
+            double src = (s->dgdt == 1) ? G_now[i] : G_now[i] + 0.5 * (G_now[i] - G_old[i]);
             s->gpost[(long)i * N + k] = gi - (gi - geq[i]) / s->tau_g + src;
             src_sum += src;
         }

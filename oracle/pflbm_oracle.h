@@ -64,6 +64,13 @@ or_solver* or_create(int nx, int ny, int wrap_y, const uint8_t* solid,
                      double sigma, double W, double M, double tau_f,
                      double rho_l, double rho_g, double tau_g);
 void or_destroy(or_solver* s);
+/* Variable viscosity nu(phi) = phi (nu_l - nu_g) + nu_g (both > 0; else the
+ * uniform tau_f of or_create) and a body acceleration g (F_b = rho g). */
+void or_set_viscosity(or_solver* s, double nu_l, double nu_g);
+void or_set_body_force(or_solver* s, double gx, double gy);
+/* Treatment of (1/2) dt^2 dG_i/dt in Eq. BGK: 0 backward difference
+ * (default, reading R4), 1 omitted (source G_i(t) only). */
+void or_set_dgdt(or_solver* s, int mode);
 /* Derived parameters: beta, kappa, tau_g, alpha (see or_create). */
 void or_params(const or_solver* s, double out[4]);
 /* Geometry: class per node, the paper's zeta, epsilon and a_v, and the

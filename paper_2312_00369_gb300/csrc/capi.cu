@@ -120,6 +120,12 @@ bool valid_params(const pflbm_params_t* p, std::string& why)
         return false;
     }
     if (p->tau_g > 0 && !(p->tau_g > 0.5)) { why = "tau_g must be > 1/2"; return false; }
+    if (!std::isfinite(p->nu_l) || !std::isfinite(p->nu_g) || !std::isfinite(p->gx) || !std::isfinite(p->gy) ||
+        p->nu_l < 0 || p->nu_g < 0) {
+        why = "nu_l, nu_g must be finite and >= 0; gx, gy finite";
+        return false;
+    }
+    if (p->dgdt_mode != 0 && p->dgdt_mode != 1) { why = "dgdt_mode must be 0 or 1"; return false; }
     if (p->precision < PFLBM_FP64 || p->precision > PFLBM_FP16) {
         why = "precision must be PFLBM_FP64, PFLBM_FP32, PFLBM_BF16 or PFLBM_FP16";
         return false;
@@ -296,6 +302,11 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
     q.alpha = prm->M / ((1.0 / 3.0) * (q.tau_g - 0.5));
     q.rho_l = prm->rho_l;
     q.rho_g = prm->rho_g;
+    q.nu_l = (prm->nu_l > 0 && prm->nu_g > 0) ? prm->nu_l : 0.0;
+    q.nu_g = (prm->nu_l > 0 && prm->nu_g > 0) ? prm->nu_g : 0.0;
+    q.gx = prm->gx;
+    q.gy = prm->gy;
+    q.dgdt_mode = prm->dgdt_mode;
 
     if (prm->stream) {
         h->stream = (cudaStream_t)prm->stream;

@@ -39,6 +39,9 @@ constexpr int TY = 8;
 
 struct Params {           // derived parameters (Sec. 2.1-2.2), in FP64
     double beta, kappa, alpha, tau_f, tau_g, rho_l, rho_g, W, sigma, M;
+    double nu_l, nu_g;    // both > 0: variable viscosity
+    double gx, gy;        // body acceleration
+    int dgdt_mode;        // 0 backward difference of G, 1 omitted
 };
 
 }  // namespace pfk

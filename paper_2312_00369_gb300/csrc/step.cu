@@ -44,6 +44,10 @@ struct StepArgs {
     int nx, ny, pitch;
     int plane;      // 18 * plane < 2^31 (checked at create)
     C beta4, kappa, rho_g, drho, omega_f, omega_g, force_pre, alpha;
+    C tau_g3h, dtau3;    // variable viscosity: tau_f = tau_g3h + dtau3 phi
+    C gx, gy;            // body acceleration
+    int varvisc;
+    int dgdt;            // 0: backward difference of G (history read/written); 1: omitted
     int* status;
     // macroscopic output (read-back kernel only), dense [ny][nx]
     double* o_phi;
@@ -285,7 +289,8 @@ __device__ __forceinline__ void collide_f_dir(const StepArgs<PREC>& a, typename 
                                               typename Store<PREC>::C ux, typename Store<PREC>::C uy,
                                               typename Store<PREC>::C uu, typename Store<PREC>::C Fx,
                                               typename Store<PREC>::C Fy, typename Store<PREC>::C drx,
-                                              typename Store<PREC>::C dry, int k)
+                                              typename Store<PREC>::C dry, typename Store<PREC>::C omega_f,
+                                              typename Store<PREC>::C force_pre, int k)
 {
     using T = Store<PREC>;
     using C = typename T::C;
@@ -294,8 +299,8 @@ __device__ __forceinline__ void collide_f_dir(const StepArgs<PREC>& a, typename 
     const C cF = C(cx(I)) * Fx + C(cy(I)) * Fy;
     const C cdr = C(cx(I)) * drx + C(cy(I)) * dry;
     const C feq = w * (C(3) * p + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
-    const C Fi = a.force_pre * w * C(3) * (cF + cu * cdr);
-    a.out.f[I * a.plane + k] = T::template st<I>(f_i + a.omega_f * (feq - f_i) + Fi);
+    const C Fi = force_pre * w * C(3) * (cF + cu * cdr);
+    a.out.f[I * a.plane + k] = T::template st<I>(f_i + omega_f * (feq - f_i) + Fi);
 }
 
 // g_i (i != 0) collision and store; returns the storage rounding residual
@@ -319,7 +324,8 @@ __device__ __forceinline__ typename Store<PREC>::C collide_g_dir(const StepArgs<
 
 // One tile (bx, by) of one lattice: the whole time step for its nodes.
 // Called by every thread of the CTA; the shared tiles are the caller's.
-template <int PREC, bool COLLIDE>
+// VV: 0 uniform tau_f, 1 variable viscosity, 2 decided by a.varvisc.
+template <int PREC, bool COLLIDE, int VV>
 __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int by, int ntx,
                                           uint8_t (*s_cls)[TX + 6], typename Store<PREC>::C (*s_phi)[TX + 4])
 {
@@ -356,10 +362,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     const C wet = (code & F_WET) ? a.wet[k] : C(0);
     const C mu = a.beta4 * ph * (ph - C(1)) * (ph - C(0.5)) - a.kappa * lap - wet * (ph - ph * ph);
 
-    // ---- coupling fields (Sec. 2.1.1) ----
+    // ---- coupling fields (Sec. 2.1.1): F = F_s + F_b, F_s = mu grad(phi), F_b = rho g ----
     const C rho = a.rho_g + a.drho * ph;
     const C drx = a.drho * gpx, dry = a.drho * gpy;
-    const C Fx = mu * gpx, Fy = mu * gpy;
+    const C Fx = mu * gpx + rho * a.gx, Fy = mu * gpy + rho * a.gy;
 
     // ---- hydrodynamic moments (Sec. 2.1.2) ----
     C f[9];
@@ -385,25 +391,31 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
         return;
     }
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
+    // relaxation of f: uniform, or tau_f(x) = nu(phi) / c_s^2 + 1/2 with
+    // nu(phi) = phi (nu_l - nu_g) + nu_g (Secs. 2.1.1, 2.1.2)
+    C omega_f = a.omega_f, force_pre = a.force_pre;
+    if (VV == 1 || (VV == 2 && a.varvisc)) {
+        omega_f = C(1) / (a.tau_g3h + a.dtau3 * ph);
+        force_pre = C(1) - C(0.5) * omega_f;
+    }
 
     // ---- f collision: f* = f + (f^eq - f)/tau_f + F_i ----
     {
         const C feq0 = C(-5) / C(3) * p - rho * (wgt<C>(0) * C(1.5)) * uu;
-        a.out.f[k] = T::template st<0>(f[0] + a.omega_f * (feq0 - f[0]));
+        a.out.f[k] = T::template st<0>(f[0] + omega_f * (feq0 - f[0]));
     }
-    collide_f_dir<PREC, 1>(a, f[1], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
-    collide_f_dir<PREC, 2>(a, f[2], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
-    collide_f_dir<PREC, 3>(a, f[3], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
-    collide_f_dir<PREC, 4>(a, f[4], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
-    collide_f_dir<PREC, 5>(a, f[5], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
-    collide_f_dir<PREC, 6>(a, f[6], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
-    collide_f_dir<PREC, 7>(a, f[7], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
-    collide_f_dir<PREC, 8>(a, f[8], p, rho, ux, uy, uu, Fx, Fy, drx, dry, k);
+    collide_f_dir<PREC, 1>(a, f[1], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    collide_f_dir<PREC, 2>(a, f[2], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    collide_f_dir<PREC, 3>(a, f[3], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    collide_f_dir<PREC, 4>(a, f[4], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    collide_f_dir<PREC, 5>(a, f[5], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    collide_f_dir<PREC, 6>(a, f[6], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    collide_f_dir<PREC, 7>(a, f[7], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    collide_f_dir<PREC, 8>(a, f[8], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
 
     // ---- g collision: g* = g + (g^eq - g)/tau_g + (3/2) G_i(t) - (1/2) G_i(t-1) ----
     const C s_now = ux * gpx + uy * gpy;
-    const C s_old = a.sprev[k];
-    const C src = C(1.5) * s_now - C(0.5) * s_old;
+    const C src = a.dgdt ? s_now : C(1.5) * s_now - C(0.5) * (C)a.sprev[k];
     const C am = a.alpha * mu;
     C resid = collide_g_dir<PREC, 1>(a, g[1], am, src, k);
     resid += collide_g_dir<PREC, 2>(a, g[2], am, src, k);
@@ -419,15 +431,15 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
         const C d0 = a.omega_g * (sum_moving(g) - (C(1) - wgt<C>(0)) * am) + wgt<C>(0) * C(-2) * src;
         a.out.g0[k] = T::g0_add(g0raw, T::kAbsorb ? d0 + resid : d0, a.status);
     }
-    a.sprev[k] = s_now;
+    if (!a.dgdt) a.sprev[k] = s_now;
 }
 
-template <int PREC, bool COLLIDE>
+template <int PREC, bool COLLIDE, int VV>
 __global__ void __launch_bounds__(TX * TY) k_step(StepArgs<PREC> a)
 {
     __shared__ uint8_t s_cls[TY + 6][TX + 6];
     __shared__ typename Store<PREC>::C s_phi[TY + 4][TX + 4];
-    step_tile<PREC, COLLIDE>(a, blockIdx.x, blockIdx.y, gridDim.x, s_cls, s_phi);
+    step_tile<PREC, COLLIDE, VV>(a, blockIdx.x, blockIdx.y, gridDim.x, s_cls, s_phi);
 }
 
 // Persistent step over many lattices: work item w = (instance, first tile);
@@ -455,7 +467,7 @@ __global__ void __launch_bounds__(TX * TY, PREC == PFLBM_FP64 ? 3 : 5) k_step_ba
         const int ntx = tiles_x(a.nx), nty = tiles_y(a.ny);
         const int bx = it.y % ntx, by0 = it.y / ntx;
         for (int gi = 0; gi < group && by0 + gi < nty; ++gi) {
-            step_tile<PREC, true>(a, bx, by0 + gi, ntx, s_cls, s_phi);
+            step_tile<PREC, true, 2>(a, bx, by0 + gi, ntx, s_cls, s_phi);
             __syncthreads();   // the next tile reuses the shared tiles and descriptor
         }
     }
@@ -486,6 +498,12 @@ StepArgs<PREC> make_args(pflbm_t* h)
     a.omega_g = (C)(1.0 / q.tau_g);
     a.force_pre = (C)(1.0 - 1.0 / (2.0 * q.tau_f));
     a.alpha = (C)q.alpha;
+    a.varvisc = (q.nu_l > 0 && q.nu_g > 0) ? 1 : 0;
+    a.dgdt = q.dgdt_mode;
+    a.tau_g3h = (C)(3.0 * q.nu_g + 0.5);
+    a.dtau3 = (C)(3.0 * (q.nu_l - q.nu_g));
+    a.gx = (C)q.gx;
+    a.gy = (C)q.gy;
     a.status = h->dstatus;
     return a;
 }
@@ -554,9 +572,10 @@ __global__ void k_init_mu(const uint8_t* __restrict__ cls, const C* __restrict__
     double wv = (code & F_WET) ? (double)wet[k] : 0.0;
     double m = 4.0 * q.beta * c * (c - 1.0) * (c - 0.5) - q.kappa * lap - wv * (c - c * c);
     mu[k] = m;
-    // u at t = 0 from f = 0: u = F / (2 rho); the history of the first step is u.grad(phi)
+    // u at t = 0 from f = 0: u = F / (2 rho), F = mu grad(phi) + rho g; the
+    // history of the first step is u.grad(phi)
     double rho = q.rho_g + (q.rho_l - q.rho_g) * c;
-    double ux = 0.5 * m * gpx / rho, uy = 0.5 * m * gpy / rho;
+    double ux = 0.5 * (m * gpx + rho * q.gx) / rho, uy = 0.5 * (m * gpy + rho * q.gy) / rho;
     sprev[k] = (C)(ux * gpx + uy * gpy);
 }
 
@@ -621,7 +640,10 @@ cudaError_t run_step_kernel(pflbm_t* h, double* o_phi, double* o_u, double* o_p)
     a.o_u = o_u;
     a.o_p = o_p;
     dim3 b(TX, TY), g(tiles_x(h->nx), tiles_y(h->ny));
-    k_step<PREC, COLLIDE><<<g, b, 0, h->stream>>>(a);
+    if (a.varvisc)
+        k_step<PREC, COLLIDE, 1><<<g, b, 0, h->stream>>>(a);
+    else
+        k_step<PREC, COLLIDE, 0><<<g, b, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,14 @@ def case_by_name(name):
         return wl.droplet_on_cylinder(theta=120.0, steps=200)
     if name == "crop":
         return wl.many_droplets_flat(nx=512, ny=256, n_drops=8, seed=2312, steps=400)
+    if name == "flat_visc_force":
+        c = wl.droplet_on_flat_wall(theta=75.0, steps=800)
+        c.meta = dict(nu_l=0.3, nu_g=0.05, gx=2e-6, gy=-1e-6)
+        return c
+    if name == "incline_nodgdt":
+        c = wl.droplet_on_incline(nx=130, ny=91, gamma=45.0, R=18.0, theta=110.0, steps=500)
+        c.meta = dict(dgdt=1)
+        return c
     if name == "tiny":
         s = np.ones((6, 3), np.uint8)
         s[2:4] = 0
@@ -40,11 +48,34 @@ def case_by_name(name):
     raise KeyError(name)
 
 
+def apply_options(o, case):
+    m = case.meta or {}
+    if m.get("nu_l") and m.get("nu_g"):
+        o.set_viscosity(m["nu_l"], m["nu_g"])
+    if m.get("gx") or m.get("gy"):
+        o.set_body_force(m.get("gx", 0.0), m.get("gy", 0.0))
+    if m.get("dgdt"):
+        o.set_dgdt(m["dgdt"])
+
+
+def solver_options(case):
+    """The same options as keyword arguments of the GPU Solver."""
+    m = case.meta or {}
+    out = {}
+    for k in ("nu_l", "nu_g", "gx", "gy"):
+        if k in m:
+            out[k] = m[k]
+    if "dgdt" in m:
+        out["dgdt_mode"] = m["dgdt"]
+    return out
+
+
 def run_case(name, steps=None, with_angle=False):
     case = case_by_name(name)
     steps = case.steps if steps is None else steps
     o = oracle.Oracle(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
                       **case.physical())
+    apply_options(o, case)
     for d in case.droplets:
         o.init_droplet(*d)
     o.step(steps)

@@ -26,6 +26,8 @@ _JOBS = {
     "crop": (oj.run_case, ("crop",)),
     "tiny": (oj.run_case, ("tiny",)),
     "block": (oj.run_case, ("block",)),
+    "flat_visc_force": (oj.run_case, ("flat_visc_force",)),
+    "incline_nodgdt": (oj.run_case, ("incline_nodgdt",)),
 }
 FULL = dict(nx=4096, ny=2048, n_drops=64, seed=2312)
 WIN_STEPS, WIN_HALF = 12, 40
@@ -55,7 +57,7 @@ def ref(name):
 def solver(case, precision, init=True):
     from paper_2312_00369_gb300.pflbm import Solver
     s = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
-               precision=precision, **case.physical())
+               precision=precision, **case.physical(), **oj.solver_options(case))
     if init:
         for d in case.droplets:
             s.init_droplet(*d)
@@ -129,7 +131,7 @@ def test_flat_wall_full_steps(precision):
 
 
 @pytest.mark.parametrize("name", ["incline30", "incline45_ragged", "cylinder", "tiny", "block",
-                                  "crop"])
+                                  "crop", "flat_visc_force", "incline_nodgdt"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_parity_cases(name, precision):
     compare(name, precision)
