@@ -88,6 +88,13 @@ typedef struct {
      * how the derivative is discretised; the backward difference lets
      * period-2-in-time modes grow after ~2e4 steps in some cases. */
     int dgdt_mode;
+    /* Appendix A, Table 2 (0 or 2: case 2, the paper's method). Cases 1
+     * and 3 move the wall energy into a Robin ghost condition
+     * n_w . grad(phi) = chi = -/+ sqrt(2 beta/kappa) cos(theta) (phi - phi^2)
+     * on flat walls (the ghost's mirror is the zeta = 1 node straight above
+     * or below; other ghosts keep the mean), with mu carrying the a_v wall
+     * term 0 times (case 1) or twice (case 3). */
+    int chi_case;
 } pflbm_params_t;
 
 /* Flat, inclined or circular wall for the contact-angle fit. type 0: the

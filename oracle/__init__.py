@@ -47,6 +47,7 @@ def lib():
         L.or_set_viscosity.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
         L.or_set_body_force.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
         L.or_set_dgdt.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_set_chi_case.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_params.argtypes = [ctypes.c_void_p, _dp]
         L.or_geometry.argtypes = [ctypes.c_void_p, _u8p, _u8p, _dp, _dp, _u16p, _u16p]
         L.or_init_droplet.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 3
@@ -215,6 +216,9 @@ class Oracle:
 
     def set_dgdt(self, mode):
         lib().or_set_dgdt(self._h, int(mode))
+
+    def set_chi_case(self, chi_case):
+        lib().or_set_chi_case(self._h, int(chi_case))
 
     def init_droplet(self, x0, y0, R):
         lib().or_init_droplet(self._h, x0, y0, R)

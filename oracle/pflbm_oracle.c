@@ -27,6 +27,13 @@
  *      (zeta(x_b + c_i) = 0) it takes the node's own post-collision f*_{i'}.
  *   R7 initial state: u = 0, p = 0, so f_i = f_i^eq(0, 0) = 0 and
  *      g_i = g_i^eq(phi_0, mu_0).
+ *   R9 Appendix A (Table 2) variants on flat walls: the ghost node takes the
+ *      value for which the wall-normal difference (phi_b - phi_g) equals
+ *      chi(phi_w) = c (phi_w - phi_w^2), phi_w = (phi_b + phi_g)/2, with phi_b
+ *      the zeta = 1 node straight above or below it (the normal of a flat
+ *      wall points to that node) and c = -sqrt(2 beta/kappa) cos(theta)
+ *      (case 1, mu without the a_v term) or +sqrt(2 beta/kappa) cos(theta)
+ *      (case 3, mu with twice the a_v term). Case 2 is the paper's method.
  *   R8 body force: F = F_s + F_b with F_b = rho g (a uniform acceleration);
  *      variable viscosity: nu(phi) = phi (nu_l - nu_g) + nu_g (Sec. 2.1.1)
  *      gives tau_f(x) = nu(phi(x)) / c_s^2 + 1/2 (Sec. 2.1.2), used in the
@@ -192,6 +199,7 @@ struct or_solver {
     double nu_l, nu_g;   /* > 0: variable viscosity (reading R8) */
     double gx, gy;       /* body acceleration */
     int dgdt;            /* 0: (1/2) dG/dt as a backward difference (R4); 1: omitted */
+    int chi_case;        /* Appendix A, Table 2: 1, 2 (default) or 3 (reading R9) */
     uint8_t* cls;
     uint8_t* zeta;
     double* eps;
@@ -348,6 +356,7 @@ or_solver* or_create(int nx, int ny, int wrap_y, const uint8_t* solid,
         s->costh[k] = cos(th * M_PI / 180.0);
     }
     s->replace_phi = 1;
+    s->chi_case = 2;
     return s;
 }
 
@@ -384,6 +393,11 @@ void or_set_viscosity(or_solver* s, double nu_l, double nu_g)
 void or_set_dgdt(or_solver* s, int mode)
 {
     s->dgdt = mode;
+}
+
+void or_set_chi_case(or_solver* s, int chi_case)
+{
+    s->chi_case = chi_case;
 }
 
 void or_set_body_force(or_solver* s, double gx, double gy)
@@ -468,6 +482,21 @@ static void ghost_fill(or_solver* s)
                 continue;
             }
             if (s->cls[k] != OR_GHOST) continue;
+            if (s->chi_case == 1 || s->chi_case == 3) {
+                /* reading R9: Robin condition n_w . grad(phi) = chi on a flat wall */
+                long up = nb(s, x, y, 0, 1), dn = nb(s, x, y, 0, -1);
+                int zu = (up >= 0 && s->zeta[up]), zd = (dn >= 0 && s->zeta[dn]);
+                if (zu != zd) {
+                    long b = zu ? up : dn;
+                    double c = (s->chi_case == 1 ? -1.0 : 1.0) * sqrt(2.0 * s->beta / s->kappa) * s->costh[b];
+                    double pb = s->phi[b];
+                    /* d = phi_b - phi_g solves d = c (phi_w - phi_w^2), phi_w = phi_b - d/2 */
+                    double A = c / 4.0, B = 1.0 - c * (pb - 0.5), C = c * (pb - pb * pb);
+                    double d = 2.0 * C / (B + sqrt(B * B + 4.0 * A * C));
+                    s->phi[k] = pb - d;
+                    continue;
+                }
+            }
             double num = 0.0, den = 0.0;
             for (int i = 0; i < Q; ++i) {
                 long m = nb(s, x, y, CX[i], CY[i]);
@@ -497,8 +526,10 @@ static void chemical_potential(or_solver* s)
                 }
             or_stencil(v, &s->gpx[k], &s->gpy[k], &s->lap[k]);
             double ph = s->phi[k];
+            /* Table 2: the wall term appears 0, 1 or 2 times (cases 1, 2, 3) */
+            double factor = (s->chi_case == 1) ? 0.0 : (s->chi_case == 3 ? 2.0 : 1.0);
             s->mu[k] = 4.0 * s->beta * ph * (ph - 1.0) * (ph - 0.5) - s->kappa * s->lap[k] -
-                       s->av[k] * root * s->costh[k] * (ph - ph * ph);
+                       factor * s->av[k] * root * s->costh[k] * (ph - ph * ph);
         }
 }
 

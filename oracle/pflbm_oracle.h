@@ -71,6 +71,9 @@ void or_set_body_force(or_solver* s, double gx, double gy);
 /* Treatment of (1/2) dt^2 dG_i/dt in Eq. BGK: 0 backward difference
  * (default, reading R4), 1 omitted (source G_i(t) only). */
 void or_set_dgdt(or_solver* s, int mode);
+/* Appendix A, Table 2: chi_case 2 (default) is the paper's method; 1 and 3
+ * move the wall energy into a Robin ghost condition on flat walls. */
+void or_set_chi_case(or_solver* s, int chi_case);
 /* Derived parameters: beta, kappa, tau_g, alpha (see or_create). */
 void or_params(const or_solver* s, double out[4]);
 /* Geometry: class per node, the paper's zeta, epsilon and a_v, and the

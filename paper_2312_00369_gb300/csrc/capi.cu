@@ -126,6 +126,7 @@ bool valid_params(const pflbm_params_t* p, std::string& why)
         return false;
     }
     if (p->dgdt_mode != 0 && p->dgdt_mode != 1) { why = "dgdt_mode must be 0 or 1"; return false; }
+    if (p->chi_case < 0 || p->chi_case > 3) { why = "chi_case must be 1, 2 or 3 (0: 2)"; return false; }
     if (p->precision < PFLBM_FP64 || p->precision > PFLBM_FP16) {
         why = "precision must be PFLBM_FP64, PFLBM_FP32, PFLBM_BF16 or PFLBM_FP16";
         return false;
@@ -307,6 +308,7 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
     q.gx = prm->gx;
     q.gy = prm->gy;
     q.dgdt_mode = prm->dgdt_mode;
+    q.chi_case = prm->chi_case == 0 ? 2 : prm->chi_case;
 
     if (prm->stream) {
         h->stream = (cudaStream_t)prm->stream;

@@ -56,7 +56,7 @@ __global__ void k_classify_2(uint8_t* __restrict__ cls, int nx, int ny, int pitc
 
 // Pass 3: a_v, the flag bits, and zero a_v elsewhere.
 __global__ void k_classify_3(uint8_t* __restrict__ cls, double* __restrict__ av, int nx,
-                             int ny, int pitch)
+                             int ny, int pitch, int chi_case)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -82,22 +82,41 @@ __global__ void k_classify_3(uint8_t* __restrict__ cls, double* __restrict__ av,
             flags |= F_WET;
         }
     }
+    if (c == CLS_GHOST && chi_case != 2) {
+        // Appendix A cases 1 and 3: a ghost node of a flat wall has exactly one
+        // zeta = 1 node straight above or below it; other ghosts keep the mean
+        bool up = y + 1 < ny && (cls[(size_t)(y + 1) * pitch + x] & CLS_MASK) <= CLS_BOUNDARY;
+        bool dn = y >= 1 && (cls[(size_t)(y - 1) * pitch + x] & CLS_MASK) <= CLS_BOUNDARY;
+        if (up != dn) flags = up ? F_GHOST_UP : F_GHOST_DOWN;
+    }
     av[k] = a;
     // pass 3 reads only the class bits of neighbours, so writing the flag
     // bits of this node concurrently is safe
     cls[k] = c | flags;
 }
 
+// Wetting coefficient per zeta = 1 node: factor a_v sqrt(2 kappa beta)
+// cos(theta), factor = 1 (the paper's method), 0 (Appendix A case 1) or 2
+// (case 3). Robin ghost nodes (cases 1 and 3) hold instead the coefficient
+// c = -/+ sqrt(2 beta / kappa) cos(theta) of chi = c (phi - phi^2), with the
+// angle of their mirror node.
 template <typename C>
 __global__ void k_wet(const uint8_t* __restrict__ cls, const double* __restrict__ av,
                       const float* __restrict__ theta, C* __restrict__ wet, double root,
-                      double theta_uniform, int nx, int ny, int pitch)
+                      double theta_uniform, int nx, int ny, int pitch, double factor, double chi_c)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= nx || y >= ny) return;
     size_t k = (size_t)y * pitch + x;
-    const double a = av[k];
+    const uint8_t code = cls[k];
+    if ((code & CLS_MASK) == CLS_GHOST && (code & (F_GHOST_UP | F_GHOST_DOWN))) {
+        size_t b = (code & F_GHOST_UP) ? k + pitch : k - pitch;
+        double thb = theta ? (double)theta[b] : theta_uniform;
+        wet[k] = (C)(chi_c * cos(thb * 3.14159265358979323846 / 180.0));
+        return;
+    }
+    const double a = av[k] * factor;
     if (a == 0.0) { wet[k] = (C)0; return; }
     double th = theta ? (double)theta[k] : theta_uniform;
     // Eq. chemical_potencial2: the wall term is a_v sqrt(2 kappa beta) cos(theta) (phi - phi^2)
@@ -165,7 +184,7 @@ cudaError_t launch_classify(pflbm_t* h)
     dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
     k_classify_1<<<g, b, 0, h->stream>>>(h->solid, h->cls, h->nx, h->ny, h->pitch);
     k_classify_2<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->pitch);
-    k_classify_3<<<g, b, 0, h->stream>>>(h->cls, h->av, h->nx, h->ny, h->pitch);
+    k_classify_3<<<g, b, 0, h->stream>>>(h->cls, h->av, h->nx, h->ny, h->pitch, h->prm.chi_case);
     return cudaGetLastError();
 }
 
@@ -173,12 +192,15 @@ cudaError_t launch_wet(pflbm_t* h)
 {
     dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
     double root = sqrt(2.0 * h->prm.kappa * h->prm.beta);
+    const int cc = h->prm.chi_case;
+    double factor = cc == 1 ? 0.0 : (cc == 3 ? 2.0 : 1.0);
+    double chi_c = (cc == 1 ? -1.0 : 1.0) * sqrt(2.0 * h->prm.beta / h->prm.kappa);
     if (h->precision == PFLBM_FP64)
         k_wet<double><<<g, b, 0, h->stream>>>(h->cls, h->av, h->theta, (double*)h->wet, root,
-                                              h->theta_uniform, h->nx, h->ny, h->pitch);
+                                              h->theta_uniform, h->nx, h->ny, h->pitch, factor, chi_c);
     else
         k_wet<float><<<g, b, 0, h->stream>>>(h->cls, h->av, h->theta, (float*)h->wet, root,
-                                             h->theta_uniform, h->nx, h->ny, h->pitch);
+                                             h->theta_uniform, h->nx, h->ny, h->pitch, factor, chi_c);
     return cudaGetLastError();
 }
 

@@ -26,9 +26,12 @@ template <typename C> __host__ __device__ constexpr C wgt(int i) {
 // Node byte: bits 0-1 class, bit 2 "a_v != 0" (read the wetting coefficient),
 // bit 3 "zeta = 1 with a zeta = 0 neighbour" (bounce-back links present),
 // bit 4 "ghost node in the 8-neighbourhood" (stencil reaches a ghost value).
+// For ghost nodes bits 2-3 mean instead "Robin ghost (Appendix A cases 1
+// and 3) whose flat-wall mirror node is straight above / below".
 enum : uint8_t {
     CLS_FLUID = 0, CLS_BOUNDARY = 1, CLS_GHOST = 2, CLS_INTERIOR = 3,
     CLS_MASK = 3, F_WET = 4, F_LINK = 8, F_NEARGHOST = 16,
+    F_GHOST_UP = 4, F_GHOST_DOWN = 8,
     CLS_OUT = 0xFF  // outside the lattice in y (tile halos only)
 };
 __host__ __device__ inline bool zeta_of(uint8_t c) { return c != CLS_OUT && (c & CLS_MASK) <= CLS_BOUNDARY; }
@@ -42,6 +45,7 @@ struct Params {           // derived parameters (Sec. 2.1-2.2), in FP64
     double nu_l, nu_g;    // both > 0: variable viscosity
     double gx, gy;        // body acceleration
     int dgdt_mode;        // 0 backward difference of G, 1 omitted
+    int chi_case;         // Appendix A, Table 2: 1, 2 (the paper's method) or 3
 };
 
 }  // namespace pfk

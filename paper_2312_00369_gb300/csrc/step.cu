@@ -160,6 +160,18 @@ __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
     __syncthreads();
 }
 
+// Ghost value of a flat wall under the Robin condition n_w . grad(phi) =
+// c (phi_w - phi_w^2) with phi_w = (phi_b + phi_g) / 2 (Appendix A cases 1
+// and 3): d = phi_b - phi_g solves (c/4) d^2 + (1 - c (phi_b - 1/2)) d
+// - c (phi_b - phi_b^2) = 0, taken in the form that is regular at c = 0.
+template <typename C>
+__host__ __device__ __forceinline__ C robin_ghost(C pb, C c)
+{
+    const C A = c * C(0.25), B = C(1) - c * (pb - C(0.5)), Cc = c * (pb - pb * pb);
+    const C d = C(2) * Cc / (B + sqrt(B * B + C(4) * A * Cc));
+    return pb - d;
+}
+
 // phi on the ring of width H around the tile (one position per thread).
 template <int PREC, int H>
 __device__ __forceinline__ void ring_phi(const StepArgs<PREC>& a, const uint8_t (*s_cls)[TX + 6],
@@ -253,11 +265,18 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
     __syncthreads();
     if (halo == 1) return;
 
-    // ghost nodes within one node of the tile: zeta-weighted 3x3 mean
+    // ghost nodes within one node of the tile: zeta-weighted 3x3 mean, or
+    // the Robin value of Appendix A cases 1 and 3 on flat walls
     for (int p = tid; p < (TY + 2) * (TX + 2); p += TX * TY) {
         int py = p / (TX + 2) + 1, px = p % (TX + 2) + 1;   // phi-tile coords 1..T+2
         uint8_t c = s_cls[py + 1][px + 1];
         if (c == CLS_OUT || (c & CLS_MASK) != CLS_GHOST) continue;
+        if (c & (F_GHOST_UP | F_GHOST_DOWN)) {
+            const C pb = s_phi[(c & F_GHOST_UP) ? py + 1 : py - 1][px];
+            const int gy = y0 - 2 + py, gx = wx(x0 - 2 + px);
+            s_phi[py][px] = robin_ghost<C>(pb, a.wet[gy * pitch + gx]);
+            continue;
+        }
         C num = C(0), den = C(0);
 #pragma unroll
         for (int j = 1; j < 9; ++j) {
@@ -533,15 +552,23 @@ __global__ void k_init_droplet(const uint8_t* __restrict__ cls, double* __restri
     if (v > phi[k]) phi[k] = v;
 }
 
-__global__ void k_ghost_fill(const uint8_t* __restrict__ cls, double* __restrict__ phi, int nx, int ny, int pitch)
+template <typename C>
+__global__ void k_ghost_fill(const uint8_t* __restrict__ cls, const C* __restrict__ wet, double* __restrict__ phi,
+                             int nx, int ny, int pitch)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= nx || y >= ny) return;
     size_t k = (size_t)y * pitch + x;
-    uint8_t c = cls[k] & CLS_MASK;
+    const uint8_t code = cls[k];
+    uint8_t c = code & CLS_MASK;
     if (c == CLS_INTERIOR) { phi[k] = 0.0; return; }
     if (c != CLS_GHOST) return;
+    if (code & (F_GHOST_UP | F_GHOST_DOWN)) {
+        // the mirror node is zeta = 1, never a ghost: no ordering hazard
+        phi[k] = robin_ghost<double>(phi[(code & F_GHOST_UP) ? k + pitch : k - pitch], (double)wet[k]);
+        return;
+    }
     double num = 0.0, den = 0.0;
     for (int j = 1; j < 9; ++j) {
         int yy = y + cy(j);
@@ -688,7 +715,10 @@ cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, 
 cudaError_t launch_init_populations(pflbm_t* h)
 {
     dim3 b(32, 8), g = grid2d(h->nx, h->ny, b);
-    k_ghost_fill<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch);
+    if (h->precision == PFLBM_FP64)
+        k_ghost_fill<double><<<g, b, 0, h->stream>>>(h->cls, (const double*)h->wet, h->phi0, h->nx, h->ny, h->pitch);
+    else
+        k_ghost_fill<float><<<g, b, 0, h->stream>>>(h->cls, (const float*)h->wet, h->phi0, h->nx, h->ny, h->pitch);
     switch (h->precision) {
         case PFLBM_FP64: return init_pop_prec<PFLBM_FP64>(h);
         case PFLBM_FP32: return init_pop_prec<PFLBM_FP32>(h);

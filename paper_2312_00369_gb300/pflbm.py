@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
                 ("tau_g", ctypes.c_double), ("precision", ctypes.c_int), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
                 ("alloc_ctx", ctypes.c_void_p), ("nu_l", ctypes.c_double), ("nu_g", ctypes.c_double),
-                ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("dgdt_mode", ctypes.c_int)]
+                ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("dgdt_mode", ctypes.c_int),
+                ("chi_case", ctypes.c_int)]
 
 
 class Schedule(ctypes.Structure):
@@ -222,7 +223,7 @@ class Solver:
     def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
                  rho_l=1.0, rho_g=0.1, tau_g=0.0, theta_field=None, precision="fp32",
                  device=None, stream=None, torch_memory=True, nu_l=0.0, nu_g=0.0, gx=0.0, gy=0.0,
-                 dgdt_mode=0):
+                 dgdt_mode=0, chi_case=2):
         import torch
         L = lib()
         solid = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -247,6 +248,7 @@ class Solver:
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.nu_l, p.nu_g, p.gx, p.gy = float(nu_l), float(nu_g), float(gx), float(gy)
         p.dgdt_mode = int(dgdt_mode)
+        p.chi_case = int(chi_case)
         p.device = dev
         p.stream = ctypes.c_void_p(stream.cuda_stream)
         if torch_memory:

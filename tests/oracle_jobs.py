@@ -34,6 +34,10 @@ def case_by_name(name):
         c = wl.droplet_on_incline(nx=130, ny=91, gamma=45.0, R=18.0, theta=110.0, steps=500)
         c.meta = dict(dgdt=1)
         return c
+    if name in ("flat_chi1", "flat_chi3"):
+        c = wl.droplet_on_flat_wall(theta=55.0 if name == "flat_chi1" else 125.0, steps=700)
+        c.meta = dict(chi_case=int(name[-1]))
+        return c
     if name == "tiny":
         s = np.ones((6, 3), np.uint8)
         s[2:4] = 0
@@ -56,6 +60,8 @@ def apply_options(o, case):
         o.set_body_force(m.get("gx", 0.0), m.get("gy", 0.0))
     if m.get("dgdt"):
         o.set_dgdt(m["dgdt"])
+    if m.get("chi_case"):
+        o.set_chi_case(m["chi_case"])
 
 
 def solver_options(case):
@@ -67,6 +73,8 @@ def solver_options(case):
             out[k] = m[k]
     if "dgdt" in m:
         out["dgdt_mode"] = m["dgdt"]
+    if "chi_case" in m:
+        out["chi_case"] = m["chi_case"]
     return out
 
 

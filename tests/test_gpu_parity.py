@@ -28,6 +28,8 @@ _JOBS = {
     "block": (oj.run_case, ("block",)),
     "flat_visc_force": (oj.run_case, ("flat_visc_force",)),
     "incline_nodgdt": (oj.run_case, ("incline_nodgdt",)),
+    "flat_chi1": (oj.run_case, ("flat_chi1",)),
+    "flat_chi3": (oj.run_case, ("flat_chi3",)),
 }
 FULL = dict(nx=4096, ny=2048, n_drops=64, seed=2312)
 WIN_STEPS, WIN_HALF = 12, 40
@@ -131,7 +133,8 @@ def test_flat_wall_full_steps(precision):
 
 
 @pytest.mark.parametrize("name", ["incline30", "incline45_ragged", "cylinder", "tiny", "block",
-                                  "crop", "flat_visc_force", "incline_nodgdt"])
+                                  "crop", "flat_visc_force", "incline_nodgdt", "flat_chi1",
+                                  "flat_chi3"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_parity_cases(name, precision):
     compare(name, precision)
