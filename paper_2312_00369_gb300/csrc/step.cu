@@ -593,16 +593,18 @@ __global__ void k_init_mu(const uint8_t* __restrict__ cls, const C* __restrict__
     double c = phi[k];
     double E = at(1, 0), Wv = at(-1, 0), N = at(0, 1), S = at(0, -1);
     double NE = at(1, 1), NW = at(-1, 1), SW = at(-1, -1), SE = at(1, -1);
-    double gpx = (E - Wv) / 3.0 + ((NE + SE) - (NW + SW)) / 12.0;
-    double gpy = (N - S) / 3.0 + ((NE + NW) - (SE + SW)) / 12.0;
-    double lap = ((E + Wv) + (N + S)) * (2.0 / 3.0) + ((NE + NW) + (SE + SW)) / 6.0 - c * (10.0 / 3.0);
+    // multiplications by rounded reciprocals: FP64 division is slow on this part
+    double gpx = (E - Wv) * (1.0 / 3.0) + ((NE + SE) - (NW + SW)) * (1.0 / 12.0);
+    double gpy = (N - S) * (1.0 / 3.0) + ((NE + NW) - (SE + SW)) * (1.0 / 12.0);
+    double lap = ((E + Wv) + (N + S)) * (2.0 / 3.0) + ((NE + NW) + (SE + SW)) * (1.0 / 6.0) - c * (10.0 / 3.0);
     double wv = (code & F_WET) ? (double)wet[k] : 0.0;
     double m = 4.0 * q.beta * c * (c - 1.0) * (c - 0.5) - q.kappa * lap - wv * (c - c * c);
     mu[k] = m;
     // u at t = 0 from f = 0: u = F / (2 rho), F = mu grad(phi) + rho g; the
     // history of the first step is u.grad(phi)
     double rho = q.rho_g + (q.rho_l - q.rho_g) * c;
-    double ux = 0.5 * (m * gpx + rho * q.gx) / rho, uy = 0.5 * (m * gpy + rho * q.gy) / rho;
+    const double half_inv_rho = 0.5 / rho;
+    double ux = (m * gpx + rho * q.gx) * half_inv_rho, uy = (m * gpy + rho * q.gy) * half_inv_rho;
     sprev[k] = (C)(ux * gpx + uy * gpy);
 }
 
