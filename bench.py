@@ -261,7 +261,7 @@ def run_serving(args, torch, rank, world, local):
     over = requests_from_stream(wl.request_stream(rate=2000.0, duration=T, seed=2024))
 
     def serve(cls, reqs, drain, **kw):
-        srv = cls(hbm_budget=budget, max_slots=args.max_slots, tick=args.tick, **kw)
+        srv = cls(hbm_budget=budget, max_slots=args.max_slots, tick=args.tick, dgdt_mode=args.dgdt, **kw)
         try:
             return srv.run(reqs, duration=T, drain=drain, max_wall=(4 * T if drain else T)).summary()
         finally:
@@ -281,7 +281,8 @@ def run_serving(args, torch, rank, world, local):
         "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": prec + " storage", "data": "synthetic",
         "config": {"workload": "serving", "seconds": T, "hbm_budget_gb": args.hbm_budget_gb,
-                   "max_slots": args.max_slots, "tick": args.tick, "precision": prec},
+                   "max_slots": args.max_slots, "tick": args.tick, "precision": prec,
+                   "dgdt_mode": args.dgdt},
         "value_is": "lattice updates per second processed by the batched server under the stated stream",
         "overloaded_2000_per_s": s_over,
         "overloaded_2000_per_s_plain_fp32": s_over_plain,
@@ -292,6 +293,52 @@ def run_serving(args, torch, rank, world, local):
         "throughput_ratio_batched_over_plain_saturated":
             s_over["processed_mlups"] / max(s_over_plain["processed_mlups"], 1e-9),
     }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_wsweep(args, torch, rank, world, local):
+    """Interface-width sweep of Sec. 3.2: droplet of radius 50 on the staircase
+    wall y = x/4 (gamma = atan 0.25) of a 256 x 256 lattice, theta = 90 and
+    120 deg, W = 4, 6, 8 (sigma, M, densities as elsewhere; FP32). All six
+    solves advance in one batch; the measured angle and its error are
+    reported per (W, theta)."""
+    import math
+    from paper_2312_00369_gb300 import workloads as wl
+    from paper_2312_00369_gb300.pflbm import Batch, Solver
+    gamma = math.degrees(math.atan(0.25))
+    stream = torch.cuda.Stream(device=local)
+    runs = []
+    with torch.cuda.stream(stream):
+        for W in (4.0, 6.0, 8.0):
+            for th in (90.0, 120.0):
+                c = wl.droplet_on_incline(nx=256, ny=256, gamma=gamma, R=50.0, theta=th, W=W)
+                sv = Solver(c.solid, theta_deg=th, precision=args.precision, device=local, stream=stream,
+                            dgdt_mode=args.dgdt, **c.physical())
+                for d in c.droplets:
+                    sv.init_droplet(*d)
+                runs.append((W, th, c, sv))
+    b = Batch([r[3] for r in runs])
+    steps = args.steps if args.steps > 1000 else 20000
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    table = {}
+    for W, th, c, sv in runs:
+        fit, circ, n = sv.contact_angle(dict(c.wall, exclude=1.5 * W))
+        table.setdefault(f"W={W:g}", {})[f"theta={th:g}"] = {"measured": fit, "error": fit - th, "points": n}
+    b.close()
+    for r in runs:
+        r[3].close()
+    nodes = sum(r[3].nx * r[3].ny for r in runs)
+    line = {"metric": "MLUPS", "value": nodes * steps / dt / 1e6, "unit": "MLUPS", "n_gpus": world,
+            "steps": steps, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "wsweep", "lattice": "256x256", "gamma_deg": gamma, "R": 50,
+                       "dgdt_mode": args.dgdt},
+            "contact_angle": table}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -310,6 +357,8 @@ def main():
     ap.add_argument("--hbm-budget-gb", type=float, default=64.0)
     ap.add_argument("--max-slots", type=int, default=512)
     ap.add_argument("--tick", type=int, default=200)
+    ap.add_argument("--dgdt", type=int, default=0, choices=[0, 1],
+                    help="(1/2) dG/dt: 0 backward difference, 1 omitted")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -326,8 +375,9 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    if args.workload in ("batched", "serving"):
-        (run_batched if args.workload == "batched" else run_serving)(args, torch, rank, world, local)
+    if args.workload in ("batched", "serving", "wsweep"):
+        {"batched": run_batched, "serving": run_serving, "wsweep": run_wsweep}[args.workload](
+            args, torch, rank, world, local)
         if world > 1:
             dist.destroy_process_group()
         return

@@ -108,7 +108,7 @@ class Server:
     batched = True
 
     def __init__(self, precision="bf16", hbm_budget=32 << 30, max_slots=512, tick=200,
-                 schedule=None, device=None, exclude_w=1.5):
+                 schedule=None, device=None, exclude_w=1.5, dgdt_mode=0):
         import torch
         self.torch = torch
         self.precision = precision
@@ -123,6 +123,7 @@ class Server:
         self.used = 0
         self.batch = None
         self.processed_lu = 0
+        self.dgdt_mode = dgdt_mode
 
     # -- admission ---------------------------------------------------------
     def footprint(self, req):
@@ -135,7 +136,8 @@ class Server:
         case = case_of(req)
         with self.torch.cuda.stream(self.stream):
             s = pflbm.Solver(case.solid, theta_deg=case.theta_deg, precision=self.precision,
-                             device=self.device, stream=self.stream, **case.physical())
+                             device=self.device, stream=self.stream, dgdt_mode=self.dgdt_mode,
+                             **case.physical())
             for d in case.droplets:
                 s.init_droplet(*d)
         self.slots.append(_Slot(req, case, s, req.steps, now))

@@ -34,6 +34,9 @@ def case_by_name(name):
         c = wl.droplet_on_incline(nx=130, ny=91, gamma=45.0, R=18.0, theta=110.0, steps=500)
         c.meta = dict(dgdt=1)
         return c
+    if name == "incline_w8":
+        return wl.droplet_on_incline(nx=130, ny=91, gamma=14.036243467926479, R=24.0, theta=120.0,
+                                     W=8.0, steps=300)
     if name in ("flat_chi1", "flat_chi3"):
         c = wl.droplet_on_flat_wall(theta=55.0 if name == "flat_chi1" else 125.0, steps=700)
         c.meta = dict(chi_case=int(name[-1]))

@@ -30,6 +30,7 @@ _JOBS = {
     "incline_nodgdt": (oj.run_case, ("incline_nodgdt",)),
     "flat_chi1": (oj.run_case, ("flat_chi1",)),
     "flat_chi3": (oj.run_case, ("flat_chi3",)),
+    "incline_w8": (oj.run_case, ("incline_w8",)),
 }
 FULL = dict(nx=4096, ny=2048, n_drops=64, seed=2312)
 WIN_STEPS, WIN_HALF = 12, 40
@@ -134,7 +135,7 @@ def test_flat_wall_full_steps(precision):
 
 @pytest.mark.parametrize("name", ["incline30", "incline45_ragged", "cylinder", "tiny", "block",
                                   "crop", "flat_visc_force", "incline_nodgdt", "flat_chi1",
-                                  "flat_chi3"])
+                                  "flat_chi3", "incline_w8"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_parity_cases(name, precision):
     compare(name, precision)
