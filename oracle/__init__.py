@@ -257,3 +257,157 @@ class Oracle:
     @property
     def steps(self):
         return lib().or_steps(self._h)
+
+
+# ------------------------------------------------------------------ 3D --
+_3d_ready = False
+
+
+def _lib3d():
+    global _3d_ready
+    L = lib()
+    if not _3d_ready:
+        vp = ctypes.c_void_p
+        L.or3_lattices.argtypes = [_ip, _dp, _ip, _dp]
+        L.or3_feq.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.or3_geq.argtypes = [ctypes.c_double] * 3 + [_dp]
+        L.or3_force.argtypes = [ctypes.c_double, _dp, _dp, _dp, _dp]
+        L.or3_source.argtypes = [ctypes.c_double, _dp]
+        L.or3_velocity_pressure.argtypes = [_dp, ctypes.c_double, _dp, _dp, _dp, _dp]
+        L.or3_stencil.argtypes = [_dp, _dp, _dp]
+        L.or3_create.restype = vp
+        L.or3_create.argtypes = [ctypes.c_int] * 4 + [_u8p] + [ctypes.c_double] * 8
+        L.or3_destroy.argtypes = [vp]
+        L.or3_params.argtypes = [vp, _dp]
+        L.or3_geometry.argtypes = [vp, _u8p, _dp]
+        L.or3_init_droplet.argtypes = [vp] + [ctypes.c_double] * 4
+        L.or3_init_phi.argtypes = [vp, _dp]
+        L.or3_step.argtypes = [vp, ctypes.c_long]
+        L.or3_get.argtypes = [vp, _dp, _dp, _dp]
+        L.or3_mass.restype = ctypes.c_double
+        L.or3_mass.argtypes = [vp]
+        L.or3_budget.argtypes = [vp, _dp]
+        L.or3_contact_angle_flat.restype = ctypes.c_int
+        L.or3_contact_angle_flat.argtypes = [_dp, _u8p] + [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_dp, _dp]
+        _3d_ready = True
+    return L
+
+
+def lattices3d():
+    c19 = np.zeros((19, 3), np.int32)
+    w19 = np.zeros(19)
+    c7 = np.zeros((7, 3), np.int32)
+    w7 = np.zeros(7)
+    _lib3d().or3_lattices(_p(c19, _ip), _p(w19), _p(c7, _ip), _p(w7))
+    return c19, w19, c7, w7
+
+
+def feq3(p, rho, u):
+    out = np.zeros(19)
+    _lib3d().or3_feq(p, rho, _p(np.ascontiguousarray(u, dtype=np.float64)), _p(out))
+    return out
+
+
+def geq3(phi, mu, alpha):
+    out = np.zeros(7)
+    _lib3d().or3_geq(phi, mu, alpha, _p(out))
+    return out
+
+
+def force3(tau_f, u, drho, F):
+    out = np.zeros(19)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (u, drho, F)]
+    _lib3d().or3_force(tau_f, _p(a[0]), _p(a[1]), _p(a[2]), _p(out))
+    return out
+
+
+def source3(s):
+    out = np.zeros(7)
+    _lib3d().or3_source(s, _p(out))
+    return out
+
+
+def velocity_pressure3(f, rho, drho, F):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (drho, F)]
+    u = np.zeros(3)
+    p = ctypes.c_double()
+    _lib3d().or3_velocity_pressure(_p(f), rho, _p(a[0]), _p(a[1]), _p(u), ctypes.byref(p))
+    return u, p.value
+
+
+def stencil3(v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    g = np.zeros(3)
+    lap = ctypes.c_double()
+    _lib3d().or3_stencil(_p(v), _p(g), ctypes.byref(lap))
+    return g, lap.value
+
+
+def contact_angle_flat3(phi, cls, zw, exclude):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    cls = np.ascontiguousarray(cls, dtype=np.uint8)
+    nz, ny, nx = phi.shape
+    th = ctypes.c_double()
+    sph = np.zeros(4)
+    n = _lib3d().or3_contact_angle_flat(_p(phi), _p(cls, _u8p), nx, ny, nz, zw, exclude,
+                                        ctypes.byref(th), _p(sph))
+    return th.value, sph, n
+
+
+class Oracle3D:
+    """Whole-domain FP64 3D solver (see pflbm_oracle3d.h); arrays are [nz, ny, nx]."""
+
+    def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
+                 rho_l=1.0, rho_g=0.1, tau_g=0.0, wrap_z=False):
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        self.nz, self.ny, self.nx = solid.shape
+        L = _lib3d()
+        self._h = L.or3_create(self.nx, self.ny, self.nz, int(wrap_z), _p(solid, _u8p), float(theta_deg),
+                               sigma, W, M, tau_f, rho_l, rho_g, tau_g)
+        if not self._h:
+            raise ValueError("or3_create rejected the arguments")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib3d().or3_destroy(h)
+            self._h = None
+
+    @property
+    def params(self):
+        out = np.zeros(4)
+        _lib3d().or3_params(self._h, _p(out))
+        return dict(beta=out[0], kappa=out[1], tau_g=out[2], alpha=out[3])
+
+    def geometry(self):
+        shp = (self.nz, self.ny, self.nx)
+        cls = np.zeros(shp, np.uint8)
+        av = np.zeros(shp)
+        _lib3d().or3_geometry(self._h, _p(cls, _u8p), _p(av))
+        return dict(cls=cls, av=av)
+
+    def init_droplet(self, x0, y0, z0, R):
+        _lib3d().or3_init_droplet(self._h, x0, y0, z0, R)
+
+    def init_phi(self, phi):
+        _lib3d().or3_init_phi(self._h, _p(np.ascontiguousarray(phi, dtype=np.float64)))
+
+    def step(self, n=1):
+        _lib3d().or3_step(self._h, int(n))
+
+    def get(self):
+        shp = (self.nz, self.ny, self.nx)
+        phi = np.zeros(shp)
+        u = np.zeros(shp + (3,))
+        p = np.zeros(shp)
+        _lib3d().or3_get(self._h, _p(phi), _p(u), _p(p))
+        return phi, u, p
+
+    def mass(self):
+        return _lib3d().or3_mass(self._h)
+
+    def budget(self):
+        out = np.zeros(4)
+        _lib3d().or3_budget(self._h, _p(out))
+        return out

@@ -1,7 +1,7 @@
 """Build the FP64 CPU oracle (test infrastructure) as a shared library.
 
 ``python oracle/build_oracle.py`` or ``build()`` compiles ``pflbm_oracle.c``
-with gcc into ``oracle/liboracle.so``. Floating-point contraction is switched
+and ``pflbm_oracle3d.c`` with gcc into ``oracle/liboracle.so``. Floating-point contraction is switched
 off so that the oracle rounds the same way on x86-64 and on AArch64 hosts.
 """
 import os
@@ -9,17 +9,17 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "pflbm_oracle.c")
+SRCS = [os.path.join(HERE, "pflbm_oracle.c"), os.path.join(HERE, "pflbm_oracle3d.c")]
+HDRS = [os.path.join(HERE, "pflbm_oracle.h"), os.path.join(HERE, "pflbm_oracle3d.h")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC),
-                                             os.path.getmtime(os.path.join(HERE, "pflbm_oracle.h")))):
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in SRCS + HDRS)):
         return LIB
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", LIB + ".tmp", SRC, "-lm"]
+    cmd = (["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", "-Wall", "-o", LIB + ".tmp"] + SRCS + ["-lm"])
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
