@@ -246,6 +246,59 @@ void pflbm_batch_destroy(pflbm_batch_t* b);
 /* Text of the calling thread's last error ("" if none). */
 const char* pflbm_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Three dimensions (Sec. 2.1.2-2.1.3 and 2.2.2 with their 3D lattices): f on
+ * D3Q19 (w = 1/3, 1/18, 1/36, c_s^2 = 1/3), g on D3Q7 (the paper's velocity
+ * matrix, w = 1/4, 1/8, c_s^2 = 1/4, so alpha = M / (c_s^2 (tau_g - 1/2))
+ * takes 1/4), gradients, Laplacian and a_v = |grad epsilon| with the D3Q19
+ * weights, and the ghost value as the zeta-weighted mean of the 27
+ * surrounding nodes (b = 27).
+ *
+ * Fields are [nz][ny][nx], node (x, y, z) at (z*ny + y)*nx + x. x and y are
+ * periodic; planes z = 0, 1, nz-2 and nz-1 must be solid. Velocity orders:
+ * D3Q19 rest, +x, -x, +y, -y, +z, -z, then (+x+y, -x-y, +x-y, -x+y, +x+z,
+ * -x-z, +x-z, -x+z, +y+z, -y-z, +y-z, -y+z); D3Q7 is the first seven.
+ * Classes as in 2D with the 18-neighbourhood of D3Q19 for "neighbour".
+ * Precision: PFLBM_FP64 or PFLBM_FP32 (g_0 in 32-bit fixed point as in 2D).
+ * The library allocates its device memory with cudaMalloc; the state takes
+ * 2 x 26 population planes of nz*ny*pitch elements (pitch = nx rounded up to
+ * 64) plus 8 further planes. Error behaviour as for the 2D calls.
+ * ------------------------------------------------------------------------ */
+typedef struct pflbm3d pflbm3d_t;
+
+typedef struct {
+    int nx, ny, nz;
+    const uint8_t* solid_mask;   /* [nz][ny][nx], nonzero = solid; copied */
+    double theta_deg, sigma, W, M, tau_f, rho_l, rho_g;
+    double tau_g;                /* <= 0: 1 */
+    int precision;               /* PFLBM_FP64 or PFLBM_FP32 */
+    int device;                  /* CUDA device; < 0: current */
+    void* stream;                /* cudaStream_t; NULL: a stream of its own */
+} pflbm3d_params_t;
+
+void pflbm3d_params_default(pflbm3d_params_t* p);
+int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p);
+void pflbm3d_destroy(pflbm3d_t* h);
+/* Initial field: tanh sphere of radius R centred at (x0, y0, z0) (Eq.
+ * initialphi), periodic in x and y; the first call after creation or a step
+ * replaces the field, later calls take the maximum. */
+int pflbm3d_init_droplet(pflbm3d_t* h, double x0, double y0, double z0, double R);
+/* Initial field from a host array [nz][ny][nx] (values on zeta = 0 nodes are
+ * ignored). */
+int pflbm3d_init_phi(pflbm3d_t* h, const double* phi);
+/* n time steps on the handle's stream (asynchronous). */
+int pflbm3d_step(pflbm3d_t* h, int64_t n);
+/* phi [N] (ghost values on ghost nodes, 0 inside the solid), u [N][3] and p
+ * [N] (0 off zeta = 1 nodes) into host arrays; any may be NULL. Synchronous. */
+int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p);
+/* sum of the g_i over zeta = 1 nodes, FP64, fixed order. Synchronous. */
+int pflbm3d_mass(pflbm3d_t* h, double* out);
+/* node classes (pflbm_node_class) and a_v into host arrays [N]; either may
+ * be NULL. Synchronous. */
+int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av);
+/* Waits for the stream; PFLBM_ENUMERIC if a NaN or |u| >= 0.3 was seen. */
+int pflbm3d_check(pflbm3d_t* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,833 @@
+// step3d.cu -- the three-dimensional form of the scheme (the pflbm3d_* entry
+// points of pflbm.h): f on D3Q19 (Eq. 3ci, w = 1/3, 1/18, 1/36, c_s^2 = 1/3),
+// g on D3Q7 (the paper's matrix, w = 1/4, 1/8, c_s^2 = 1/4, Sec. 2.1.3),
+// gradients, Laplacian and a_v with the D3Q19 weights (Eqs. gradient,
+// Laplace, avvv), the 27-neighbour ghost average of Sec. 2.2.2 (b = 27).
+//
+// A step is three kernels: (1) phi = sum of the pulled g on zeta = 1 nodes,
+// (2) ghost phi from the zeta-weighted 27-neighbour mean, (3) the fused
+// collide-and-store of f and g (pull scheme and modified bounce-back as in
+// 2D, see step.cu), which reads phi of the 18 neighbours for the stencils.
+// Nodes are stored [nz][ny][pitch]; x and y are periodic, z has walls.
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "storage.cuh"
+
+namespace pfk {
+int set_error(int code, const char* msg);
+}
+using namespace pfk;
+
+namespace {
+
+// D3Q19: rest, +x, -x, +y, -y, +z, -z, then the 12 edges in opposite pairs
+__host__ __device__ constexpr int q19x(int i)
+{
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int q19y(int i)
+{
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int q19z(int i)
+{
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int q19o(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+template <typename C> __host__ __device__ constexpr C q19w(int i)
+{
+    return i == 0 ? C(1) / C(3) : (i <= 6 ? C(1) / C(18) : C(1) / C(36));
+}
+// D3Q7 = the first seven D3Q19 velocities
+template <typename C> __host__ __device__ constexpr C q7w(int i) { return i == 0 ? C(1) / C(4) : C(1) / C(8); }
+
+__device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+template <int PREC>
+struct Args3 {
+    using T = Store<PREC>;
+    using S = typename T::S;
+    using C = typename T::C;
+    const uint8_t* cls;
+    const C* wet;
+    S* f_in;
+    S* g_in;
+    typename T::G0T* g0_in;
+    S* f_out;
+    S* g_out;
+    typename T::G0T* g0_out;
+    C* sprev;
+    C* phi;
+    int nx, ny, nz, pitch;
+    int plane;        // nz * ny * pitch, 26 planes fit in int
+    C beta4, kappa, rho_g, drho, omega_f, omega_g, force_pre, alpha;
+    int* status;
+    double* o_phi;
+    double* o_u;
+    double* o_p;
+};
+
+template <int PREC>
+__device__ __forceinline__ int nbr(const Args3<PREC>& a, int x, int y, int z, int dx, int dy, int dz)
+{
+    return ((z + dz) * a.ny + wrap1(y + dy, a.ny)) * a.pitch + wrap1(x + dx, a.nx);
+}
+
+// Pull of population I of a lattice with velocity I of D3Q19 at node k.
+template <int I, int PREC>
+__device__ __forceinline__ typename Store<PREC>::C pull3(const Args3<PREC>& a, const typename Store<PREC>::S* base,
+                                                         int x, int y, int z, int k, bool check)
+{
+    using T = Store<PREC>;
+    constexpr int X = q19x(I), Y = q19y(I), Z = q19z(I), O = q19o(I);
+    const int src = nbr(a, x, y, z, -X, -Y, -Z);
+    if (!check || zeta_of(a.cls[src])) return T::template ld<I>(base[I * a.plane + src]);
+    const int dst = nbr(a, x, y, z, X, Y, Z);
+    if (zeta_of(a.cls[dst])) return T::template ld<O>(base[O * a.plane + dst]);
+    return T::template ld<O>(base[O * a.plane + k]);
+}
+
+template <int PREC>
+__device__ __forceinline__ void pull_g7(const Args3<PREC>& a, int x, int y, int z, int k, bool check,
+                                        typename Store<PREC>::C v[7], typename Store<PREC>::G0T& raw0)
+{
+    raw0 = a.g0_in[k];
+    v[0] = Store<PREC>::g0(raw0);
+    v[1] = pull3<1, PREC>(a, a.g_in, x, y, z, k, check);
+    v[2] = pull3<2, PREC>(a, a.g_in, x, y, z, k, check);
+    v[3] = pull3<3, PREC>(a, a.g_in, x, y, z, k, check);
+    v[4] = pull3<4, PREC>(a, a.g_in, x, y, z, k, check);
+    v[5] = pull3<5, PREC>(a, a.g_in, x, y, z, k, check);
+    v[6] = pull3<6, PREC>(a, a.g_in, x, y, z, k, check);
+}
+
+template <typename C>
+__device__ __forceinline__ C sum6(const C v[7]) { return ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]); }
+
+// (1) phi on zeta = 1 nodes
+template <int PREC>
+__global__ void k3_phi(Args3<PREC> a)
+{
+    using C = typename Store<PREC>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int k = (z * a.ny + y) * a.pitch + x;
+    const uint8_t c = a.cls[k];
+    if (!zeta_of(c)) return;
+    C v[7];
+    typename Store<PREC>::G0T r;
+    pull_g7<PREC>(a, x, y, z, k, (c & F_LINK) != 0, v, r);
+    a.phi[k] = v[0] + sum6(v);
+}
+
+// (2) ghost phi: zeta-weighted mean of the 27-neighbourhood; interior 0
+template <int PREC>
+__global__ void k3_ghost(Args3<PREC> a)
+{
+    using C = typename Store<PREC>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int k = (z * a.ny + y) * a.pitch + x;
+    const uint8_t c = a.cls[k] & CLS_MASK;
+    if (c == CLS_INTERIOR) { a.phi[k] = C(0); return; }
+    if (c != CLS_GHOST) return;
+    C num = C(0), den = C(0);
+    for (int dz = -1; dz <= 1; ++dz) {
+        if (z + dz < 0 || z + dz >= a.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int m = nbr(a, x, y, z, dx, dy, dz);
+                if (zeta_of(a.cls[m])) { num += a.phi[m]; den += C(1); }
+            }
+    }
+    a.phi[k] = num / den;
+}
+
+template <int PREC, int I>
+__device__ __forceinline__ void collide_f3(const Args3<PREC>& a, typename Store<PREC>::C fi,
+                                           typename Store<PREC>::C p, typename Store<PREC>::C rho,
+                                           const typename Store<PREC>::C u[3], typename Store<PREC>::C uu,
+                                           const typename Store<PREC>::C F[3], const typename Store<PREC>::C dr[3],
+                                           int k)
+{
+    using C = typename Store<PREC>::C;
+    constexpr int X = q19x(I), Y = q19y(I), Z = q19z(I);
+    const C w = q19w<C>(I);
+    const C cu = C(X) * u[0] + C(Y) * u[1] + C(Z) * u[2];
+    const C cF = C(X) * F[0] + C(Y) * F[1] + C(Z) * F[2];
+    const C cd = C(X) * dr[0] + C(Y) * dr[1] + C(Z) * dr[2];
+    const C feq = w * (C(3) * p + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
+    const C Fi = a.force_pre * w * C(3) * (cF + cu * cd);
+    a.f_out[I * a.plane + k] = Store<PREC>::template st<I>(fi + a.omega_f * (feq - fi) + Fi);
+}
+
+// (3) the fused collide-and-store (COLLIDE) or the macroscopic read-back
+template <int PREC, bool COLLIDE>
+__global__ void __launch_bounds__(256) k3_step(Args3<PREC> a)
+{
+    using T = Store<PREC>;
+    using C = typename T::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int k = (z * a.ny + y) * a.pitch + x;
+    const uint8_t code = a.cls[k];
+    if (!zeta_of(code)) {
+        if (!COLLIDE) {
+            const size_t o = ((size_t)z * a.ny + y) * a.nx + x;
+            if (a.o_phi) a.o_phi[o] = (double)a.phi[k];
+            if (a.o_u) { a.o_u[3 * o] = 0.0; a.o_u[3 * o + 1] = 0.0; a.o_u[3 * o + 2] = 0.0; }
+            if (a.o_p) a.o_p[o] = 0.0;
+        }
+        return;
+    }
+    const bool check = (code & F_LINK) != 0;
+    // ---- stencils on phi (D3Q19 weights), chemical potential ----
+    const C ph = a.phi[k];
+    C gp[3] = {C(0), C(0), C(0)}, lap = C(0);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const C v = a.phi[nbr(a, x, y, z, q19x(i), q19y(i), q19z(i))];
+        const C w3 = C(3) * q19w<C>(i);
+        gp[0] += w3 * C(q19x(i)) * v;
+        gp[1] += w3 * C(q19y(i)) * v;
+        gp[2] += w3 * C(q19z(i)) * v;
+        lap += C(2) * w3 * (v - ph);
+    }
+    const C wet = (code & F_WET) ? a.wet[k] : C(0);
+    const C mu = a.beta4 * ph * (ph - C(1)) * (ph - C(0.5)) - a.kappa * lap - wet * (ph - ph * ph);
+    const C rho = a.rho_g + a.drho * ph;
+    const C dr[3] = {a.drho * gp[0], a.drho * gp[1], a.drho * gp[2]};
+    const C F[3] = {mu * gp[0], mu * gp[1], mu * gp[2]};
+    // ---- hydrodynamics ----
+    C f[19];
+    f[0] = T::template ld<0>(a.f_in[k]);
+    f[1] = pull3<1, PREC>(a, a.f_in, x, y, z, k, check);
+    f[2] = pull3<2, PREC>(a, a.f_in, x, y, z, k, check);
+    f[3] = pull3<3, PREC>(a, a.f_in, x, y, z, k, check);
+    f[4] = pull3<4, PREC>(a, a.f_in, x, y, z, k, check);
+    f[5] = pull3<5, PREC>(a, a.f_in, x, y, z, k, check);
+    f[6] = pull3<6, PREC>(a, a.f_in, x, y, z, k, check);
+    f[7] = pull3<7, PREC>(a, a.f_in, x, y, z, k, check);
+    f[8] = pull3<8, PREC>(a, a.f_in, x, y, z, k, check);
+    f[9] = pull3<9, PREC>(a, a.f_in, x, y, z, k, check);
+    f[10] = pull3<10, PREC>(a, a.f_in, x, y, z, k, check);
+    f[11] = pull3<11, PREC>(a, a.f_in, x, y, z, k, check);
+    f[12] = pull3<12, PREC>(a, a.f_in, x, y, z, k, check);
+    f[13] = pull3<13, PREC>(a, a.f_in, x, y, z, k, check);
+    f[14] = pull3<14, PREC>(a, a.f_in, x, y, z, k, check);
+    f[15] = pull3<15, PREC>(a, a.f_in, x, y, z, k, check);
+    f[16] = pull3<16, PREC>(a, a.f_in, x, y, z, k, check);
+    f[17] = pull3<17, PREC>(a, a.f_in, x, y, z, k, check);
+    f[18] = pull3<18, PREC>(a, a.f_in, x, y, z, k, check);
+    C m[3] = {C(0), C(0), C(0)}, fsum = C(0);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        m[0] += C(q19x(i)) * f[i];
+        m[1] += C(q19y(i)) * f[i];
+        m[2] += C(q19z(i)) * f[i];
+        fsum += f[i];
+    }
+    const C ir = C(1) / rho;
+    const C u[3] = {(m[0] + C(0.5) * F[0]) * ir, (m[1] + C(0.5) * F[1]) * ir, (m[2] + C(0.5) * F[2]) * ir};
+    const C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    // p = c_s^2/(1 - w_0) [...] = (1/2) [sum_{i!=0} f_i + u.grad(rho)/2 + rho s_0], s_0 = -uu/2
+    const C p = C(0.5) * (fsum + C(0.5) * (u[0] * dr[0] + u[1] * dr[1] + u[2] * dr[2]) - C(0.5) * rho * uu);
+    if (!COLLIDE) {
+        const size_t o = ((size_t)z * a.ny + y) * a.nx + x;
+        if (a.o_phi) a.o_phi[o] = (double)ph;
+        if (a.o_u) { a.o_u[3 * o] = u[0]; a.o_u[3 * o + 1] = u[1]; a.o_u[3 * o + 2] = u[2]; }
+        if (a.o_p) a.o_p[o] = (double)p;
+        return;
+    }
+    if (!(uu < C(0.09))) atomicOr(a.status, 1);
+    a.f_out[k] = T::template st<0>(f[0] + a.omega_f * ((C(-2) * p - C(0.5) * rho * uu) - f[0]));
+    collide_f3<PREC, 1>(a, f[1], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 2>(a, f[2], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 3>(a, f[3], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 4>(a, f[4], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 5>(a, f[5], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 6>(a, f[6], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 7>(a, f[7], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 8>(a, f[8], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 9>(a, f[9], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 10>(a, f[10], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 11>(a, f[11], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 12>(a, f[12], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 13>(a, f[13], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 14>(a, f[14], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 15>(a, f[15], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 16>(a, f[16], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 17>(a, f[17], p, rho, u, uu, F, dr, k);
+    collide_f3<PREC, 18>(a, f[18], p, rho, u, uu, F, dr, k);
+    // ---- phase lattice (D3Q7): G_i = w_i h_i (3/2 s - 1/2 s_prev), h_0 = -5/2, h_i = -1/2 ----
+    C g[7];
+    typename T::G0T raw0;
+    pull_g7<PREC>(a, x, y, z, k, check, g, raw0);
+    const C s_now = u[0] * gp[0] + u[1] * gp[1] + u[2] * gp[2];
+    const C src = C(1.5) * s_now - C(0.5) * a.sprev[k];
+    const C am = a.alpha * mu;
+#pragma unroll
+    for (int i = 1; i < 7; ++i) {
+        const C w = q7w<C>(i);
+        a.g_out[i * a.plane + k] = T::template st<1>(g[i] + a.omega_g * (w * am - g[i]) + w * C(-0.5) * src);
+    }
+    const C d0 = a.omega_g * (sum6(g) - C(0.75) * am) + q7w<C>(0) * C(-2.5) * src;
+    a.g0_out[k] = T::g0_add(raw0, d0, a.status);
+    a.sprev[k] = s_now;
+}
+
+// ---- geometry: classes (D3Q19 neighbourhood), a_v = |n| / 12 with the
+// integer n = sum 36 w_i c_i eps (36 w = 2 axes, 1 edges), flags ----
+__global__ void k3_cls1(const uint8_t* solid, uint8_t* cls, int nx, int ny, int nz, int pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const size_t k = ((size_t)z * ny + y) * pitch + x;
+    if (!solid[k]) { cls[k] = CLS_FLUID; return; }
+    bool touch = false;
+    for (int i = 1; i < 19; ++i) {
+        int zz = z + q19z(i);
+        if (zz < 0 || zz >= nz) continue;
+        size_t m = ((size_t)zz * ny + wrap1(y + q19y(i), ny)) * pitch + wrap1(x + q19x(i), nx);
+        if (!solid[m]) touch = true;
+    }
+    cls[k] = touch ? CLS_BOUNDARY : CLS_INTERIOR;
+}
+
+__global__ void k3_cls2(uint8_t* cls, int nx, int ny, int nz, int pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const size_t k = ((size_t)z * ny + y) * pitch + x;
+    if (cls[k] != CLS_INTERIOR) return;
+    for (int i = 1; i < 19; ++i) {
+        int zz = z + q19z(i);
+        if (zz < 0 || zz >= nz) continue;
+        size_t m = ((size_t)zz * ny + wrap1(y + q19y(i), ny)) * pitch + wrap1(x + q19x(i), nx);
+        if ((cls[m] & CLS_MASK) <= CLS_BOUNDARY) { cls[k] = CLS_GHOST; return; }
+    }
+}
+
+__global__ void k3_cls3(uint8_t* cls, double* av, int nx, int ny, int nz, int pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const size_t k = ((size_t)z * ny + y) * pitch + x;
+    const uint8_t c = cls[k] & CLS_MASK;
+    double a = 0.0;
+    uint8_t flags = 0;
+    if (c <= CLS_BOUNDARY) {
+        int n[3] = {0, 0, 0};
+        for (int i = 1; i < 19; ++i) {
+            size_t m = ((size_t)(z + q19z(i)) * ny + wrap1(y + q19y(i), ny)) * pitch + wrap1(x + q19x(i), nx);
+            const uint8_t cn = cls[m] & CLS_MASK;
+            const int w36 = i <= 6 ? 2 : 1, eps = cn == CLS_FLUID ? 1 : 0;
+            n[0] += w36 * q19x(i) * eps;
+            n[1] += w36 * q19y(i) * eps;
+            n[2] += w36 * q19z(i) * eps;
+            if (cn > CLS_BOUNDARY) flags |= F_LINK;
+        }
+        if (n[0] | n[1] | n[2]) {
+            a = sqrt((double)(n[0] * n[0] + n[1] * n[1] + n[2] * n[2])) / 12.0;
+            flags |= F_WET;
+        }
+    }
+    av[k] = a;
+    cls[k] = c | flags;
+}
+
+template <typename C>
+__global__ void k3_wet(const double* av, C* wet, size_t n, double coef)
+{
+    size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (k < n) wet[k] = (C)(av[k] * coef);
+}
+
+// ---- initial state (FP64 arithmetic) ----
+__global__ void k3_droplet(const uint8_t* cls, double* phi, int nx, int ny, int nz, int pitch, double x0, double y0,
+                           double z0, double R, double W, int replace)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const size_t k = ((size_t)z * ny + y) * pitch + x;
+    if (!zeta_of(cls[k])) { if (replace) phi[k] = 0.0; return; }
+    double dx = fabs(x - x0), dy = fabs(y - y0);
+    dx = fmod(dx, (double)nx); if (dx > 0.5 * nx) dx = nx - dx;
+    dy = fmod(dy, (double)ny); if (dy > 0.5 * ny) dy = ny - dy;
+    const double dz = z - z0, r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double v = 0.5 + 0.5 * tanh(2.0 * (R - r) / W);
+    if (replace || v > phi[k]) phi[k] = v;
+}
+
+__global__ void k3_ghost_init(const uint8_t* cls, double* phi, int nx, int ny, int nz, int pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const size_t k = ((size_t)z * ny + y) * pitch + x;
+    const uint8_t c = cls[k] & CLS_MASK;
+    if (c == CLS_INTERIOR) { phi[k] = 0.0; return; }
+    if (c != CLS_GHOST) return;
+    double num = 0.0, den = 0.0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        if (z + dz < 0 || z + dz >= nz) continue;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                size_t m = ((size_t)(z + dz) * ny + wrap1(y + dy, ny)) * pitch + wrap1(x + dx, nx);
+                if (zeta_of(cls[m])) { num += phi[m]; den += 1.0; }
+            }
+    }
+    phi[k] = num / den;
+}
+
+template <int PREC>
+__global__ void k3_init_pop(Args3<PREC> a, const double* phi0, double* mu0, Params q)
+{
+    using T = Store<PREC>;
+    using C = typename T::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int k = (z * a.ny + y) * a.pitch + x;
+    for (int i = 0; i < 19; ++i) a.f_in[i * a.plane + k] = T::template st<0>(C(0));
+    for (int i = 1; i < 7; ++i) a.g_in[i * a.plane + k] = T::template st<1>(C(0));
+    a.g0_in[k] = T::g0_from_double(0.0);
+    a.sprev[k] = C(0);
+    const uint8_t code = a.cls[k];
+    if (!zeta_of(code)) return;
+    // mu of the initial field (Eq. chemical_potencial2), FP64
+    const double ph = phi0[k];
+    double gp[3] = {0, 0, 0}, lap = 0.0;
+    for (int i = 1; i < 19; ++i) {
+        const double v = phi0[nbr(a, x, y, z, q19x(i), q19y(i), q19z(i))];
+        const double w3 = 3.0 * q19w<double>(i);
+        gp[0] += w3 * q19x(i) * v;
+        gp[1] += w3 * q19y(i) * v;
+        gp[2] += w3 * q19z(i) * v;
+        lap += 2.0 * w3 * (v - ph);
+    }
+    const double wet = (code & F_WET) ? (double)a.wet[k] : 0.0;
+    const double mu = 4.0 * q.beta * ph * (ph - 1.0) * (ph - 0.5) - q.kappa * lap - wet * (ph - ph * ph);
+    mu0[k] = mu;
+    const double rho = q.rho_g + (q.rho_l - q.rho_g) * ph, h = 0.5 / rho;
+    a.sprev[k] = (C)((mu * gp[0] * gp[0] + mu * gp[1] * gp[1] + mu * gp[2] * gp[2]) * h);
+    a.g0_in[k] = T::g0_from_double(ph - 0.75 * q.alpha * mu);
+}
+
+// g_i (i != 0) of the first pull: g_i^eq(mu) at x + c_i, or at x itself when
+// x + c_i is not a zeta = 1 node (doubly-unknown rule), like the 2D init.
+template <int PREC>
+__global__ void k3_init_g(Args3<PREC> a, const double* mu0, double alpha)
+{
+    using T = Store<PREC>;
+    using C = typename T::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int k = (z * a.ny + y) * a.pitch + x;
+    if (!zeta_of(a.cls[k])) return;
+    for (int i = 1; i < 7; ++i) {
+        int m = nbr(a, x, y, z, q19x(i), q19y(i), q19z(i));
+        if (!zeta_of(a.cls[m])) m = k;
+        a.g_in[i * a.plane + k] = T::template st<1>((C)(0.125 * alpha * mu0[m]));
+    }
+}
+
+// FP64 mass: sum of pulled g over zeta = 1 nodes, block partials, fixed order
+template <int PREC>
+__global__ void __launch_bounds__(256) k3_mass(Args3<PREC> a, double* partial)
+{
+    __shared__ double sh[8];
+    double acc = 0.0;
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    for (long long t = blockIdx.x * 256LL + threadIdx.x; t < N; t += (long long)gridDim.x * 256) {
+        const int x = (int)(t % a.nx), y = (int)((t / a.nx) % a.ny), z = (int)(t / ((long long)a.nx * a.ny));
+        const int k = (z * a.ny + y) * a.pitch + x;
+        const uint8_t c = a.cls[k];
+        if (!zeta_of(c)) continue;
+        const bool check = (c & F_LINK) != 0;
+        double v = Store<PREC>::g0_double(a.g0_in[k]);
+        v += (double)pull3<1, PREC>(a, a.g_in, x, y, z, k, check) + (double)pull3<2, PREC>(a, a.g_in, x, y, z, k, check);
+        v += (double)pull3<3, PREC>(a, a.g_in, x, y, z, k, check) + (double)pull3<4, PREC>(a, a.g_in, x, y, z, k, check);
+        v += (double)pull3<5, PREC>(a, a.g_in, x, y, z, k, check) + (double)pull3<6, PREC>(a, a.g_in, x, y, z, k, check);
+        acc += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double r = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = r;
+    }
+}
+
+__global__ void k3_sum(const double* partial, int n, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += partial[i];
+        *out = s;
+    }
+}
+
+constexpr int kMassBlocks = 1216;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the handle and the C ABI
+// ---------------------------------------------------------------------------
+struct pflbm3d {
+    int nx = 0, ny = 0, nz = 0, pitch = 0, precision = PFLBM_FP32, device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Params prm{};
+    double theta = 90.0;
+    uint8_t* cls = nullptr;
+    uint8_t* solid = nullptr;
+    double* av = nullptr;
+    void* wet = nullptr;
+    void* pop[2] = {nullptr, nullptr};
+    void* sprev = nullptr;
+    void* phi = nullptr;
+    double* phi0 = nullptr;
+    double* mu0 = nullptr;
+    double* red = nullptr;
+    double* out = nullptr;
+    int* dstatus = nullptr;
+    int cur = 0;
+    bool replace_phi = true, init_pending = false;
+    int64_t steps = 0;
+};
+
+namespace {
+
+size_t pop3_bytes(int prec, size_t plane)
+{
+    return prec == PFLBM_FP64 ? 26 * plane * 8 : 26 * plane * 4;  // g_0 plane holds its storage form
+}
+
+template <int PREC>
+Args3<PREC> make3(pflbm3d_t* h, int in)
+{
+    using T = Store<PREC>;
+    using C = typename T::C;
+    Args3<PREC> a{};
+    const size_t plane = (size_t)h->nz * h->ny * h->pitch;
+    auto planes = [&](void* base, typename T::S*& f, typename T::S*& g, typename T::G0T*& g0) {
+        f = (typename T::S*)base;
+        g = f + 19 * plane;
+        g0 = (typename T::G0T*)g;
+    };
+    planes(h->pop[in], a.f_in, a.g_in, a.g0_in);
+    planes(h->pop[in ^ 1], a.f_out, a.g_out, a.g0_out);
+    a.cls = h->cls;
+    a.wet = (const C*)h->wet;
+    a.sprev = (C*)h->sprev;
+    a.phi = (C*)h->phi;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.nz = h->nz;
+    a.pitch = h->pitch;
+    a.plane = (int)plane;
+    const Params& q = h->prm;
+    a.beta4 = (C)(4.0 * q.beta);
+    a.kappa = (C)q.kappa;
+    a.rho_g = (C)q.rho_g;
+    a.drho = (C)(q.rho_l - q.rho_g);
+    a.omega_f = (C)(1.0 / q.tau_f);
+    a.omega_g = (C)(1.0 / q.tau_g);
+    a.force_pre = (C)(1.0 - 0.5 / q.tau_f);
+    a.alpha = (C)q.alpha;
+    a.status = h->dstatus;
+    return a;
+}
+
+dim3 grid3(const pflbm3d_t* h) { return dim3((h->nx + 31) / 32, (h->ny + 7) / 8, h->nz); }
+
+template <int PREC>
+cudaError_t step3_prec(pflbm3d_t* h)
+{
+    Args3<PREC> a = make3<PREC>(h, h->cur);
+    dim3 b(32, 8), g = grid3(h);
+    k3_phi<PREC><<<g, b, 0, h->stream>>>(a);
+    k3_ghost<PREC><<<g, b, 0, h->stream>>>(a);
+    k3_step<PREC, true><<<g, b, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t macro3_prec(pflbm3d_t* h, double* phi, double* u, double* p)
+{
+    Args3<PREC> a = make3<PREC>(h, h->cur);
+    a.o_phi = phi;
+    a.o_u = u;
+    a.o_p = p;
+    dim3 b(32, 8), g = grid3(h);
+    k3_phi<PREC><<<g, b, 0, h->stream>>>(a);
+    k3_ghost<PREC><<<g, b, 0, h->stream>>>(a);
+    k3_step<PREC, false><<<g, b, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t init3_prec(pflbm3d_t* h)
+{
+    Args3<PREC> a = make3<PREC>(h, h->cur);
+    dim3 b(32, 8), g = grid3(h);
+    k3_ghost_init<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->nz, h->pitch);
+    k3_init_pop<PREC><<<g, b, 0, h->stream>>>(a, h->phi0, h->mu0, h->prm);
+    k3_init_g<PREC><<<g, b, 0, h->stream>>>(a, h->mu0, h->prm.alpha);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t mass3_prec(pflbm3d_t* h, double* d_out)
+{
+    Args3<PREC> a = make3<PREC>(h, h->cur);
+    k3_mass<PREC><<<kMassBlocks, 256, 0, h->stream>>>(a, h->red);
+    k3_sum<<<1, 32, 0, h->stream>>>(h->red, kMassBlocks, d_out);
+    return cudaGetLastError();
+}
+
+#define P3(call64, call32) (h->precision == PFLBM_FP64 ? (call64) : (call32))
+
+int fail3(int code, const std::string& m) { return set_error(code, m.c_str()); }
+
+#define CK3(call)                                                        \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return fail3(PFLBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int materialize3(pflbm3d_t* h)
+{
+    if (!h->init_pending) return PFLBM_OK;
+    CK3(P3(init3_prec<PFLBM_FP64>(h), init3_prec<PFLBM_FP32>(h)));
+    CK3(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    h->init_pending = false;
+    return PFLBM_OK;
+}
+
+void release3(pflbm3d_t* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void* bufs[] = {h->cls, h->solid, h->av, h->wet, h->pop[0], h->pop[1], h->sprev, h->phi, h->phi0, h->mu0,
+                    h->red, h->out, h->dstatus};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pflbm3d_params_default(pflbm3d_params_t* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->theta_deg = 90.0;
+    p->sigma = 0.01;
+    p->W = 4.0;
+    p->M = 0.1;
+    p->tau_f = 0.8;
+    p->rho_l = 1.0;
+    p->rho_g = 0.1;
+    p->tau_g = 1.0;
+    p->precision = PFLBM_FP32;
+    p->device = -1;
+}
+
+int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
+{
+    if (!out || !p) return fail3(PFLBM_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (p->nx < 3 || p->ny < 3 || p->nz < 5 || !p->solid_mask) return fail3(PFLBM_EINVAL, "need nx, ny >= 3, nz >= 5 and a mask");
+    if (!(p->W > 0) || !(p->M > 0) || !(p->tau_f > 0.5) || !(p->rho_l > 0) || !(p->rho_g > 0) || !(p->sigma >= 0) ||
+        (p->tau_g > 0 && !(p->tau_g > 0.5)) || !std::isfinite(p->theta_deg))
+        return fail3(PFLBM_EINVAL, "invalid physical parameters");
+    if (p->precision != PFLBM_FP64 && p->precision != PFLBM_FP32)
+        return fail3(PFLBM_EINVAL, "3D supports PFLBM_FP64 and PFLBM_FP32");
+    const int pitch = (p->nx + 63) / 64 * 64;
+    const size_t plane = (size_t)p->nz * p->ny * pitch;
+    if (26.0 * (double)plane >= 2147483647.0) return fail3(PFLBM_EINVAL, "lattice too large");
+    const size_t N = (size_t)p->nx * p->ny * p->nz, pl = (size_t)p->nx * p->ny;
+    for (size_t k = 0; k < pl; ++k)
+        if (!p->solid_mask[k] || !p->solid_mask[pl + k] || !p->solid_mask[(p->nz - 2) * pl + k] ||
+            !p->solid_mask[(p->nz - 1) * pl + k])
+            return fail3(PFLBM_EBADMASK, "planes 0, 1, nz-2 and nz-1 of the solid mask must be solid");
+    pflbm3d_t* h = new (std::nothrow) pflbm3d();
+    if (!h) return fail3(PFLBM_ENOMEM, "host allocation failed");
+    h->nx = p->nx;
+    h->ny = p->ny;
+    h->nz = p->nz;
+    h->pitch = pitch;
+    h->precision = p->precision;
+    int dev = p->device;
+    if (dev < 0) cudaGetDevice(&dev);
+    h->device = dev;
+    cudaSetDevice(dev);
+    Params& q = h->prm;
+    q.sigma = p->sigma;
+    q.W = p->W;
+    q.M = p->M;
+    q.beta = 12.0 * p->sigma / p->W;
+    q.kappa = 1.5 * p->sigma * p->W;
+    q.tau_f = p->tau_f;
+    q.tau_g = p->tau_g > 0 ? p->tau_g : 1.0;
+    q.alpha = p->M / (0.25 * (q.tau_g - 0.5));   // Eq. mobility with the D3Q7 c_s^2 = 1/4
+    q.rho_l = p->rho_l;
+    q.rho_g = p->rho_g;
+    h->theta = p->theta_deg;
+    if (p->stream) {
+        h->stream = (cudaStream_t)p->stream;
+    } else {
+        cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        h->own_stream = true;
+    }
+    const size_t cs = p->precision == PFLBM_FP64 ? 8 : 4;
+    struct B { void** ptr; size_t bytes; } bufs[] = {
+        {(void**)&h->cls, plane}, {(void**)&h->solid, plane}, {(void**)&h->av, plane * 8}, {&h->wet, plane * cs},
+        {&h->pop[0], pop3_bytes(p->precision, plane)}, {&h->pop[1], pop3_bytes(p->precision, plane)},
+        {&h->sprev, plane * cs}, {&h->phi, plane * cs}, {(void**)&h->phi0, plane * 8}, {(void**)&h->mu0, plane * 8},
+        {(void**)&h->red, kMassBlocks * 8 + 64}, {(void**)&h->dstatus, 16}};
+    for (auto& b : bufs) {
+        if (cudaMalloc(b.ptr, b.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            release3(h);
+            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+        }
+    }
+    cudaMemsetAsync(h->pop[0], 0, pop3_bytes(p->precision, plane), h->stream);
+    cudaMemsetAsync(h->pop[1], 0, pop3_bytes(p->precision, plane), h->stream);
+    cudaMemsetAsync(h->phi, 0, plane * cs, h->stream);
+    cudaMemsetAsync(h->phi0, 0, plane * 8, h->stream);
+    cudaMemsetAsync(h->dstatus, 0, 16, h->stream);
+    cudaMemsetAsync(h->solid, 1, plane, h->stream);
+    cudaMemcpy2DAsync(h->solid, pitch, p->solid_mask, p->nx, p->nx, (size_t)p->ny * p->nz, cudaMemcpyHostToDevice,
+                      h->stream);
+    dim3 b(32, 8), g = grid3(h);
+    k3_cls1<<<g, b, 0, h->stream>>>(h->solid, h->cls, h->nx, h->ny, h->nz, pitch);
+    k3_cls2<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch);
+    k3_cls3<<<g, b, 0, h->stream>>>(h->cls, h->av, h->nx, h->ny, h->nz, pitch);
+    const double coef = sqrt(2.0 * q.kappa * q.beta) * cos(h->theta * 3.14159265358979323846 / 180.0);
+    const unsigned nb = (unsigned)((plane + 255) / 256);
+    if (p->precision == PFLBM_FP64)
+        k3_wet<double><<<nb, 256, 0, h->stream>>>(h->av, (double*)h->wet, plane, coef);
+    else
+        k3_wet<float><<<nb, 256, 0, h->stream>>>(h->av, (float*)h->wet, plane, coef);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        release3(h);
+        return fail3(PFLBM_ECUDA, cudaGetErrorString(e));
+    }
+    (void)N;
+    *out = h;
+    return PFLBM_OK;
+}
+
+void pflbm3d_destroy(pflbm3d_t* h) { release3(h); }
+
+int pflbm3d_init_droplet(pflbm3d_t* h, double x0, double y0, double z0, double R)
+{
+    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    dim3 b(32, 8), g = grid3(h);
+    k3_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->nz, h->pitch, x0, y0, z0, R, h->prm.W,
+                                       h->replace_phi ? 1 : 0);
+    CK3(cudaGetLastError());
+    h->replace_phi = false;
+    h->init_pending = true;
+    h->steps = 0;
+    return PFLBM_OK;
+}
+
+int pflbm3d_init_phi(pflbm3d_t* h, const double* phi)
+{
+    if (!h || !phi) return fail3(PFLBM_EINVAL, "NULL argument");
+    CK3(cudaMemcpy2DAsync(h->phi0, h->pitch * 8, phi, h->nx * 8, h->nx * 8, (size_t)h->ny * h->nz,
+                          cudaMemcpyHostToDevice, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    h->replace_phi = false;
+    h->init_pending = true;
+    h->steps = 0;
+    return PFLBM_OK;
+}
+
+int pflbm3d_step(pflbm3d_t* h, int64_t n)
+{
+    if (!h || n < 0) return fail3(PFLBM_EINVAL, "invalid arguments");
+    if (int rc = materialize3(h)) return rc;
+    for (int64_t t = 0; t < n; ++t) {
+        CK3(P3(step3_prec<PFLBM_FP64>(h), step3_prec<PFLBM_FP32>(h)));
+        h->cur ^= 1;
+        h->steps += 1;
+    }
+    if (n > 0) h->replace_phi = true;
+    return PFLBM_OK;
+}
+
+int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p)
+{
+    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    if (int rc = materialize3(h)) return rc;
+    const size_t N = (size_t)h->nx * h->ny * h->nz;
+    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        h->out = nullptr;
+        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+    }
+    double *dphi = h->out, *du = h->out + N, *dp = h->out + 4 * N;
+    CK3(P3(macro3_prec<PFLBM_FP64>(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr),
+           macro3_prec<PFLBM_FP32>(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr)));
+    if (phi) CK3(cudaMemcpyAsync(phi, dphi, N * 8, cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK3(cudaMemcpyAsync(u, du, 3 * N * 8, cudaMemcpyDeviceToHost, h->stream));
+    if (p) CK3(cudaMemcpyAsync(p, dp, N * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    return PFLBM_OK;
+}
+
+int pflbm3d_mass(pflbm3d_t* h, double* out)
+{
+    if (!h || !out) return fail3(PFLBM_EINVAL, "NULL argument");
+    if (int rc = materialize3(h)) return rc;
+    double* d = h->red + kMassBlocks + 4;
+    CK3(P3(mass3_prec<PFLBM_FP64>(h, d), mass3_prec<PFLBM_FP32>(h, d)));
+    CK3(cudaMemcpyAsync(out, d, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    return PFLBM_OK;
+}
+
+int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av)
+{
+    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    if (cls) {
+        CK3(cudaMemcpy2DAsync(cls, h->nx, h->cls, h->pitch, h->nx, (size_t)h->ny * h->nz, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK3(cudaStreamSynchronize(h->stream));
+        for (size_t k = 0; k < (size_t)h->nx * h->ny * h->nz; ++k) cls[k] &= CLS_MASK;
+    }
+    if (av)
+        CK3(cudaMemcpy2DAsync(av, h->nx * 8, h->av, h->pitch * 8, h->nx * 8, (size_t)h->ny * h->nz,
+                              cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    return PFLBM_OK;
+}
+
+int pflbm3d_check(pflbm3d_t* h)
+{
+    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    CK3(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CK3(cudaMemcpy(&st, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    return st ? fail3(PFLBM_ENUMERIC, "NaN or |u| >= 0.3 detected on the device") : PFLBM_OK;
+}
+
+}  // extern "C"

@@ -48,6 +48,15 @@ class Params(ctypes.Structure):
                 ("chi_case", ctypes.c_int)]
 
 
+class Params3D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("solid_mask", ctypes.POINTER(ctypes.c_uint8)),
+                ("theta_deg", ctypes.c_double), ("sigma", ctypes.c_double), ("W", ctypes.c_double),
+                ("M", ctypes.c_double), ("tau_f", ctypes.c_double), ("rho_l", ctypes.c_double),
+                ("rho_g", ctypes.c_double), ("tau_g", ctypes.c_double), ("precision", ctypes.c_int),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
 class Schedule(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int), ("tiles_per_item", ctypes.c_int),
                 ("order", ctypes.c_int), ("use_graph", ctypes.c_int)]
@@ -118,6 +127,16 @@ _SIGS = {
     "pflbm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "pflbm_batch_info": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, ctypes.POINTER(ctypes.c_int64)]),
     "pflbm_batch_destroy": (None, [ctypes.c_void_p]),
+    "pflbm3d_params_default": (None, [ctypes.POINTER(Params3D)]),
+    "pflbm3d_create": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(Params3D)]),
+    "pflbm3d_destroy": (None, [_H]),
+    "pflbm3d_init_droplet": (ctypes.c_int, [_H] + [ctypes.c_double] * 4),
+    "pflbm3d_init_phi": (ctypes.c_int, [_H, _dp]),
+    "pflbm3d_step": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "pflbm3d_get": (ctypes.c_int, [_H, _dp, _dp, _dp]),
+    "pflbm3d_mass": (ctypes.c_int, [_H, _dp]),
+    "pflbm3d_geometry": (ctypes.c_int, [_H, _u8p, _dp]),
+    "pflbm3d_check": (ctypes.c_int, [_H]),
 }
 
 
@@ -125,7 +144,7 @@ def declared_functions(header: str = HEADER):
     """Names of the functions include/pflbm.h declares."""
     text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(pflbm_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(pflbm(?:3d)?_[a-z0-9_]+)\s*\(", text)))
 
 
 def lib():
@@ -407,3 +426,80 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Solver3D:
+    """One three-dimensional lattice (``pflbm3d_t``): f on D3Q19, g on D3Q7.
+
+    ``solid``: uint8 [nz, ny, nx] mask (1 = solid; planes z = 0, 1, nz-2,
+    nz-1 solid). ``precision``: "fp64" or "fp32". The library allocates its
+    own device memory; work runs on ``stream`` (default: the current stream).
+    """
+
+    def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
+                 rho_l=1.0, rho_g=0.1, tau_g=0.0, precision="fp32", device=None, stream=None):
+        import torch
+        L = lib()
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        self.nz, self.ny, self.nx = solid.shape
+        self.precision = precision
+        dev = torch.cuda.current_device() if device is None else int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        p = Params3D()
+        L.pflbm3d_params_default(ctypes.byref(p))
+        p.nx, p.ny, p.nz = self.nx, self.ny, self.nz
+        p.solid_mask = _p(solid, _u8p)
+        p.theta_deg, p.sigma, p.W, p.M, p.tau_f = float(theta_deg), sigma, W, M, tau_f
+        p.rho_l, p.rho_g, p.tau_g = rho_l, rho_g, tau_g
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.device = dev
+        p.stream = ctypes.c_void_p(stream.cuda_stream)
+        h = _H()
+        _check(L.pflbm3d_create(ctypes.byref(h), ctypes.byref(p)))
+        self._h = h
+        _LIVE_SOLVERS.add(self)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().pflbm3d_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_droplet(self, x0, y0, z0, R):
+        _check(lib().pflbm3d_init_droplet(self._h, float(x0), float(y0), float(z0), float(R)))
+
+    def init_phi(self, phi):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        assert phi.shape == (self.nz, self.ny, self.nx)
+        _check(lib().pflbm3d_init_phi(self._h, _p(phi)))
+
+    def step(self, n=1):
+        _check(lib().pflbm3d_step(self._h, int(n)))
+
+    def get(self):
+        shp = (self.nz, self.ny, self.nx)
+        phi, u, p = np.empty(shp), np.empty(shp + (3,)), np.empty(shp)
+        _check(lib().pflbm3d_get(self._h, _p(phi), _p(u), _p(p)))
+        return phi, u, p
+
+    def mass(self):
+        m = ctypes.c_double()
+        _check(lib().pflbm3d_mass(self._h, ctypes.byref(m)))
+        return m.value
+
+    def geometry(self):
+        shp = (self.nz, self.ny, self.nx)
+        cls, av = np.empty(shp, np.uint8), np.empty(shp)
+        _check(lib().pflbm3d_geometry(self._h, _p(cls, _u8p), _p(av)))
+        return {"cls": cls, "av": av}
+
+    def check(self):
+        _check(lib().pflbm3d_check(self._h))

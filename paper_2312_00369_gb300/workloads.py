@@ -217,3 +217,75 @@ def request_stream(rate=2000.0, duration=60.0, seed=2024, n_max=None):
                         theta=float(rng.uniform(30.0, 150.0)),
                         steps=int(rng.integers(1000, 20001))))
     return out
+
+
+# --------------------------------------------------------------------------
+# Three dimensions: masks are uint8 [nz, ny, nx]; x and y periodic; planes
+# 0, 1, nz-2, nz-1 solid. The effective flat wall is z = z_b - 1/2 for a top
+# solid plane z_b, as in 2D.
+# --------------------------------------------------------------------------
+
+@dataclass
+class Case3D:
+    name: str
+    solid: np.ndarray                      # uint8 [nz, ny, nx]
+    droplets: list                         # [(x0, y0, z0, R), ...]
+    zw: float                              # effective flat wall (sphere fit)
+    theta_deg: float = 90.0
+    sigma: float = 0.01
+    W: float = 4.0
+    M: float = 0.1
+    tau_f: float = 0.8
+    rho_l: float = 1.0
+    rho_g: float = 0.1
+    steps: int = 1000
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return tuple(int(v) for v in self.solid.shape)
+
+    def physical(self) -> dict:
+        return dict(sigma=self.sigma, W=self.W, M=self.M, tau_f=self.tau_f,
+                    rho_l=self.rho_l, rho_g=self.rho_g)
+
+
+def box3d(nx: int, ny: int, nz: int, bottom: int = 2, top: int = 2):
+    """Solid planes [0, bottom) and [nz-top, nz); returns (solid, zw)."""
+    assert bottom >= 2 and top >= 2
+    s = np.zeros((nz, ny, nx), np.uint8)
+    s[:bottom] = 1
+    s[nz - top:] = 1
+    return s, bottom - 1 - 0.5
+
+
+def droplet_on_flat_wall_3d(nx=64, ny=64, nz=40, R=16.0, theta=60.0, steps=5000, **phys) -> Case3D:
+    """Hemispherical droplet of radius R centred on the effective bottom wall."""
+    s, zw = box3d(nx, ny, nz)
+    kw = dict(sigma=0.01, W=4.0, M=0.1, tau_f=0.8, rho_l=1.0, rho_g=0.1)
+    kw.update(phys)
+    return Case3D("flat3d", s, [(nx / 2.0, ny / 2.0, zw, R)], zw, theta_deg=theta, steps=steps, **kw)
+
+
+def droplet_on_sphere_3d(n=32, Rs=6.0, R=7.0, theta=90.0, steps=1000, **phys) -> Case3D:
+    """Droplet of radius R on top of a solid sphere of radius Rs at the domain
+    centre (a curved wall with every link configuration of D3Q19)."""
+    s, zw = box3d(n, n, n)
+    c = n / 2.0
+    z, y, x = np.mgrid[0:n, 0:n, 0:n]
+    s |= (((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2) < Rs * Rs).astype(np.uint8)
+    kw = dict(sigma=0.01, W=4.0, M=0.1, tau_f=0.8, rho_l=1.0, rho_g=0.1)
+    kw.update(phys)
+    return Case3D("sphere3d", s, [(c, c, c + Rs, R)], zw, theta_deg=theta, steps=steps,
+                  meta=dict(Rs=Rs), **kw)
+
+
+def many_droplets_3d(nx=512, ny=512, nz=128, n_drops=64, seed=2312, r_lo=12.0, r_hi=24.0,
+                     theta=60.0, steps=1000) -> Case3D:
+    """Flat bottom wall with ``n_drops`` hemispherical droplets of radius
+    U[r_lo, r_hi] centred on the wall at (x, y) ~ U[0, nx) x U[0, ny)."""
+    rng = np.random.default_rng(seed)
+    s, zw = box3d(nx, ny, nz)
+    d = [(float(rng.uniform(0, nx)), float(rng.uniform(0, ny)), zw, float(rng.uniform(r_lo, r_hi)))
+         for _ in range(n_drops)]
+    return Case3D("many_flat3d", s, d, zw, theta_deg=theta, steps=steps, meta=dict(seed=seed))

@@ -127,3 +127,30 @@ def window_run(case_name_kwargs, x_centre, half, steps):
     o.step(steps)
     phi, u, p = o.get()
     return dict(phi=phi[:, half], u=u[:, half], p=p[:, half])
+
+
+# ---- three dimensions ------------------------------------------------------
+
+def case3d_by_name(name):
+    if name == "flat3d":          # ragged in x (40 = 32 + 8) and in y (20 = 8 + 8 + 4)
+        s, zw = wl.box3d(40, 20, 20)
+        return wl.Case3D("flat3d", s, [(20.0, 10.0, zw, 7.0)], zw, theta_deg=60.0, steps=300)
+    if name == "flat3d_two":      # two overlapping droplets (pointwise maximum), theta > 90
+        s, zw = wl.box3d(40, 20, 20)
+        return wl.Case3D("flat3d_two", s, [(14.0, 10.0, zw, 6.0), (25.0, 9.0, zw, 5.0)], zw,
+                         theta_deg=120.0, steps=200)
+    if name == "sphere3d":
+        return wl.droplet_on_sphere_3d(n=32, Rs=6.0, R=7.0, theta=75.0, steps=200)
+    raise KeyError(name)
+
+
+def run3d_case(name, steps=None):
+    c = case3d_by_name(name)
+    o = oracle.Oracle3D(c.solid, theta_deg=c.theta_deg, **c.physical())
+    for d in c.droplets:
+        o.init_droplet(*d)
+    m0 = o.mass()
+    o.step(c.steps if steps is None else steps)
+    phi, u, p = o.get()
+    g = o.geometry()
+    return dict(phi=phi, u=u, p=p, mass0=m0, mass=o.mass(), cls=g["cls"], av=g["av"])

@@ -35,3 +35,15 @@ def test_host_only_entry_points():
     assert L.pflbm_create_ex(ctypes.byref(h), ctypes.byref(P)) == pflbm.EINVAL
     assert L.pflbm_step(None, 1) == pflbm.EINVAL
     assert b"NULL handle" in L.pflbm_last_error()
+
+
+def test_host_only_checks_3d():
+    L = pflbm.lib()
+    h = pflbm._H()
+    P = pflbm.Params3D()
+    L.pflbm3d_params_default(ctypes.byref(P))
+    assert P.precision == pflbm.FP32 and P.tau_f == 0.8 and P.device == -1
+    # nx = 0 and no mask: refused before any CUDA call
+    assert L.pflbm3d_create(ctypes.byref(h), ctypes.byref(P)) == pflbm.EINVAL
+    assert L.pflbm3d_step(None, 1) == pflbm.EINVAL
+    assert L.pflbm3d_mass(None, None) == pflbm.EINVAL

@@ -1,0 +1,87 @@
+"""GPU parity of the three-dimensional path (D3Q19 f, D3Q7 g, 27-neighbour
+ghost average) against the FP64 3D oracle, through the C ABI.
+
+Bars: node classes bit-exact, a_v to rounding; phi within 1e-10 (FP64) and
+1e-5 (FP32) after the stated steps; mass as the oracle's.
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from tests import oracle_jobs as oj
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": dict(phi=1e-10, u=1e-12, p=1e-12, mass=1e-9), "fp32": dict(phi=1e-5, u=1e-6, p=1e-6, mass=1e-4)}
+CASES = ["flat3d", "flat3d_two", "sphere3d"]
+
+_pool = None
+_fut = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def oracle_pool():
+    global _pool
+    _pool = mp.get_context("spawn").Pool(processes=len(CASES))
+    for name in CASES:
+        _fut[name] = _pool.apply_async(oj.run3d_case, (name,))
+    yield
+    _pool.close()
+    _pool.join()
+
+
+def ref(name):
+    return _fut[name].get(timeout=900)
+
+
+def gpu_run(name, precision):
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.case3d_by_name(name)
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision=precision, **c.physical())
+    for d in c.droplets:
+        s.init_droplet(*d)
+    m0 = s.mass()
+    s.step(c.steps)
+    s.check()
+    phi, u, p = s.get()
+    g = s.geometry()
+    out = dict(phi=phi, u=u, p=p, mass0=m0, mass=s.mass(), cls=g["cls"], av=g["av"])
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_geometry_3d(name):
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.case3d_by_name(name)
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp64", **c.physical())
+    g = s.geometry()
+    s.close()
+    r = ref(name)
+    assert np.array_equal(g["cls"], r["cls"])
+    assert np.max(np.abs(g["av"] - r["av"])) < 1e-15
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", CASES)
+def test_parity_3d(name, precision):
+    r = ref(name)
+    g = gpu_run(name, precision)
+    t = TOL[precision]
+    zeta = r["cls"] <= 1
+    dphi = np.max(np.abs(g["phi"] - r["phi"]))
+    assert dphi <= t["phi"], dphi
+    assert np.max(np.abs(g["u"] - r["u"])[zeta]) <= t["u"]
+    assert np.max(np.abs(g["p"] - r["p"])[zeta]) <= t["p"]
+    assert abs(g["mass0"] - r["mass0"]) <= t["mass"] and abs(g["mass"] - r["mass"]) <= t["mass"]
+    # the droplet moved: the comparison is not of two initial states
+    assert np.max(np.abs(r["u"])) > 1e-6
+
+
+def test_rejects_bad_mask_3d():
+    from paper_2312_00369_gb300 import pflbm
+    s = np.zeros((12, 8, 8), np.uint8)
+    with pytest.raises(pflbm.PflbmError):
+        pflbm.Solver3D(s)
