@@ -9,7 +9,8 @@ collisions, streaming with bounce-back). The state (1.2 GB) is far larger
 than L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--precision fp32|fp64] [--workload many_flat|flat|incline|cylinder]
+                    [--precision fp32|fp64] [--workload many_flat|flat|incline|cylinder|
+                     batched|serving|wsweep|many_flat3d]
 
 Prints one JSON line (rank 0). Under torchrun each rank runs an independent
 replica of the workload (the solver does not shard: replicas only).
@@ -36,10 +37,10 @@ BYTES_PER_LU = {"fp64": 2 * 9 * 2 * 8 + 2 * 8 + 1, "fp32": 2 * 9 * 2 * 4 + 2 * 4
                 "bf16": 2 * (17 * 2 + 4) + 2 * 4 + 1, "fp16": 2 * (17 * 2 + 4) + 2 * 4 + 1}
 
 
-def step_source_sha256():
+def step_source_sha256(files=("step.cu", "storage.cuh", "pflbm_internal.cuh")):
     import hashlib
     h = hashlib.sha256()
-    for f in ("step.cu", "storage.cuh", "pflbm_internal.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2312_00369_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -148,13 +149,18 @@ def oracle_sample(case, seconds=12.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    case = make_case(args.workload)
-    mlups, desc = oracle_sample(case, seconds=max(3.0, min(20.0, 2.0 * args.steps)))
+    if args.workload == "many_flat3d":
+        mlups, desc = oracle_sample_3d(seconds=max(3.0, min(20.0, 2.0 * args.steps)))
+        cfg = {"workload": "many_flat3d", "nx": 512, "ny": 512, "nz": 128}
+    else:
+        case = make_case(args.workload)
+        mlups, desc = oracle_sample(case, seconds=max(3.0, min(20.0, 2.0 * args.steps)))
+        cfg = {"workload": case.name, "nx": case.nx, "ny": case.ny}
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": case.name, "nx": case.nx, "ny": case.ny},
+        "config": cfg,
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -343,6 +349,133 @@ def run_wsweep(args, torch, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+# three dimensions (D3Q19 f, D3Q7 g): every f_i and g_i read and written
+# once, the history read and written once, one node byte
+BYTES_PER_LU_3D = {"fp64": 2 * (19 + 7) * 8 + 2 * 8 + 1, "fp32": 2 * (19 + 7) * 4 + 2 * 4 + 1}
+
+
+def oracle_sample_3d(seconds=10.0):
+    """Time the FP64 3D CPU oracle (single thread, as it stands) on a bounded
+    sample: a 64 x 64 x 32 box with 4 droplets of the same generator."""
+    import oracle
+    from paper_2312_00369_gb300 import workloads as wl
+    sub = wl.many_droplets_3d(nx=64, ny=64, nz=32, n_drops=4, r_lo=6.0, r_hi=10.0)
+    o = oracle.Oracle3D(sub.solid, theta_deg=sub.theta_deg, **sub.physical())
+    for d in sub.droplets:
+        o.init_droplet(*d)
+    n = int(np.prod(sub.shape))
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(2)
+        steps += 2
+    dt = time.perf_counter() - t0
+    return n * steps / dt / 1e6, f"64x64x32 box of the same generator (4 droplets), {steps} steps"
+
+
+def run_3d(args, torch, rank, world, local):
+    """512 x 512 x 128 box, flat bottom wall, 64 droplets of radius U[12, 24],
+    theta = 60 deg; one bench step = one time step (3 launches: order
+    parameter, ghost fill, fused collide-and-stream)."""
+    import torch.distributed as dist
+    from paper_2312_00369_gb300 import workloads as wl
+    from paper_2312_00369_gb300.pflbm import Solver3D, lib
+    prec = args.precision if args.precision in ("fp32", "fp64") else "fp32"
+    nx, ny, nz = (int(v) for v in args.size3d.split("x"))
+    case = wl.many_droplets_3d(nx=nx, ny=ny, nz=nz)
+    N = int(np.prod(case.shape))
+    stream = torch.cuda.Stream(device=local)
+    lib()
+    with torch.cuda.stream(stream):
+        s = Solver3D(case.solid, theta_deg=case.theta_deg, precision=prec, device=local, stream=stream,
+                     **case.physical())
+        for d in case.droplets:
+            s.init_droplet(*d)
+        s.step(args.warmup)
+        s.check()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        s.check()
+        s.close()
+    ms_t = torch.tensor([ms], device=f"cuda:{local}")
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_per_step = ms / args.steps
+    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    peak, peak_kind = load_peaks()
+    bpl = BYTES_PER_LU_3D[prec]
+    achieved = bpl * N / (ms_per_step * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile) and case.shape == (128, 512, 512):
+        try:
+            t = json.load(open(tfile)).get(f"many_flat3d:{prec}")
+            if t and t.get("step_source_sha256") == step_source_sha256(
+                    ("step3d.cu", "storage.cuh", "pflbm_internal.cuh")):
+                traffic = t["bytes_per_launch"]
+        except Exception:
+            traffic = None
+
+    e2e_steps = args.e2e_steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        s2 = Solver3D(case.solid, theta_deg=case.theta_deg, precision=prec, device=local, stream=stream,
+                      **case.physical())
+        for d in case.droplets:
+            s2.init_droplet(*d)
+        s2.step(e2e_steps)
+        phi, u, p = s2.get()
+        s2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc = oracle_sample_3d()
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64"}[prec], "data": "synthetic",
+            "config": {"workload": case.name, "nx": case.shape[2], "ny": case.shape[1], "nz": case.shape[0],
+                       "droplets": len(case.droplets), "precision": prec,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state %.1f GB > L2, no flush needed" % (2 * 26 * (4 if prec == "fp32" else 8) * N / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "bytes_per_lu": bpl, "kernel": "whole step (3 launches)"},
+            "hbm_roofline_mlups": peak * 1e9 / bpl / 1e6,
+            "e2e": {"value": world * N * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": case.solid.nbytes / e2e_steps,
+                    "d2h_bytes_per_step": (phi.nbytes + u.nbytes + p.nbytes) / e2e_steps,
+                    "steps_per_solve": e2e_steps,
+                    "includes": "create (mask upload, geometry), droplet init, steps, get"},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,6 +490,7 @@ def main():
     ap.add_argument("--hbm-budget-gb", type=float, default=64.0)
     ap.add_argument("--max-slots", type=int, default=512)
     ap.add_argument("--tick", type=int, default=200)
+    ap.add_argument("--size3d", default="512x512x128", help="nx x ny x nz of many_flat3d")
     ap.add_argument("--dgdt", type=int, default=0, choices=[0, 1],
                     help="(1/2) dG/dt: 0 backward difference, 1 omitted")
     args = ap.parse_args()
@@ -375,8 +509,9 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    if args.workload in ("batched", "serving", "wsweep"):
-        {"batched": run_batched, "serving": run_serving, "wsweep": run_wsweep}[args.workload](
+    if args.workload in ("batched", "serving", "wsweep", "many_flat3d"):
+        {"batched": run_batched, "serving": run_serving, "wsweep": run_wsweep,
+         "many_flat3d": run_3d}[args.workload](
             args, torch, rank, world, local)
         if world > 1:
             dist.destroy_process_group()

@@ -22,7 +22,11 @@ int set_error(int code, const char* msg);
 }
 using namespace pfk;
 
-namespace {
+#ifndef PFLBM3D_STEP_MINB
+#define PFLBM3D_STEP_MINB 4   // resident 256-thread CTAs per SM asked of the FP32 step kernel
+#endif
+
+namespace pfk3 {
 
 // D3Q19: rest, +x, -x, +y, -y, +z, -z, then the 12 edges in opposite pairs
 __host__ __device__ constexpr int q19x(int i)
@@ -111,9 +115,10 @@ __device__ __forceinline__ void pull_g7(const Args3<PREC>& a, int x, int y, int 
 template <typename C>
 __device__ __forceinline__ C sum6(const C v[7]) { return ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]); }
 
-// (1) phi on zeta = 1 nodes
+// (1) phi on zeta = 1 nodes. Warps without a bounce-back link take the
+// branch-free pull (all loads independent).
 template <int PREC>
-__global__ void k3_phi(Args3<PREC> a)
+__global__ void __launch_bounds__(256) k3_phi(Args3<PREC> a)
 {
     using C = typename Store<PREC>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
@@ -123,21 +128,23 @@ __global__ void k3_phi(Args3<PREC> a)
     if (!zeta_of(c)) return;
     C v[7];
     typename Store<PREC>::G0T r;
-    pull_g7<PREC>(a, x, y, z, k, (c & F_LINK) != 0, v, r);
+    if (__any_sync(__activemask(), (c & F_LINK) != 0))
+        pull_g7<PREC>(a, x, y, z, k, (c & F_LINK) != 0, v, r);
+    else
+        pull_g7<PREC>(a, x, y, z, k, false, v, r);
     a.phi[k] = v[0] + sum6(v);
 }
 
-// (2) ghost phi: zeta-weighted mean of the 27-neighbourhood; interior 0
+// (2) ghost phi: zeta-weighted mean of the 27-neighbourhood, over the list
+// of ghost nodes (interior nodes keep phi = 0 from creation)
 template <int PREC>
-__global__ void k3_ghost(Args3<PREC> a)
+__global__ void __launch_bounds__(256) k3_ghost(Args3<PREC> a, const int* __restrict__ ghosts, int n_ghosts)
 {
     using C = typename Store<PREC>::C;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-    if (x >= a.nx || y >= a.ny) return;
-    const int k = (z * a.ny + y) * a.pitch + x;
-    const uint8_t c = a.cls[k] & CLS_MASK;
-    if (c == CLS_INTERIOR) { a.phi[k] = C(0); return; }
-    if (c != CLS_GHOST) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_ghosts) return;
+    const int k = ghosts[t];
+    const int x = k % a.pitch, y = (k / a.pitch) % a.ny, z = k / (a.pitch * a.ny);
     C num = C(0), den = C(0);
     for (int dz = -1; dz <= 1; ++dz) {
         if (z + dz < 0 || z + dz >= a.nz) continue;
@@ -168,26 +175,15 @@ __device__ __forceinline__ void collide_f3(const Args3<PREC>& a, typename Store<
     a.f_out[I * a.plane + k] = Store<PREC>::template st<I>(fi + a.omega_f * (feq - fi) + Fi);
 }
 
-// (3) the fused collide-and-store (COLLIDE) or the macroscopic read-back
-template <int PREC, bool COLLIDE>
-__global__ void __launch_bounds__(256) k3_step(Args3<PREC> a)
+// (3) the fused collide-and-store (COLLIDE) or the macroscopic read-back of
+// one zeta = 1 node; CHECK = false is the branch-free pull of a node without
+// bounce-back links
+template <int PREC, bool COLLIDE, bool CHECK>
+__device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, int z, int k, uint8_t code)
 {
     using T = Store<PREC>;
     using C = typename T::C;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-    if (x >= a.nx || y >= a.ny) return;
-    const int k = (z * a.ny + y) * a.pitch + x;
-    const uint8_t code = a.cls[k];
-    if (!zeta_of(code)) {
-        if (!COLLIDE) {
-            const size_t o = ((size_t)z * a.ny + y) * a.nx + x;
-            if (a.o_phi) a.o_phi[o] = (double)a.phi[k];
-            if (a.o_u) { a.o_u[3 * o] = 0.0; a.o_u[3 * o + 1] = 0.0; a.o_u[3 * o + 2] = 0.0; }
-            if (a.o_p) a.o_p[o] = 0.0;
-        }
-        return;
-    }
-    const bool check = (code & F_LINK) != 0;
+    const bool check = CHECK && (code & F_LINK) != 0;
     // ---- stencils on phi (D3Q19 weights), chemical potential ----
     const C ph = a.phi[k];
     C gp[3] = {C(0), C(0), C(0)}, lap = C(0);
@@ -283,6 +279,40 @@ __global__ void __launch_bounds__(256) k3_step(Args3<PREC> a)
     a.sprev[k] = s_now;
 }
 
+template <int PREC, bool COLLIDE>
+__global__ void __launch_bounds__(256, PREC == PFLBM_FP64 ? 1 : PFLBM3D_STEP_MINB) k3_step(Args3<PREC> a)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int k = (z * a.ny + y) * a.pitch + x;
+    const uint8_t code = a.cls[k];
+    if (!zeta_of(code)) {
+        if (!COLLIDE) {
+            const size_t o = ((size_t)z * a.ny + y) * a.nx + x;
+            if (a.o_phi) a.o_phi[o] = (double)a.phi[k];
+            if (a.o_u) { a.o_u[3 * o] = 0.0; a.o_u[3 * o + 1] = 0.0; a.o_u[3 * o + 2] = 0.0; }
+            if (a.o_p) a.o_p[o] = 0.0;
+        }
+        return;
+    }
+    if (__any_sync(__activemask(), (code & F_LINK) != 0))
+        step_node<PREC, COLLIDE, true>(a, x, y, z, k, code);
+    else
+        step_node<PREC, COLLIDE, false>(a, x, y, z, k, code);
+}
+
+// ghost nodes: count, then list (any order: each ghost value depends on
+// zeta = 1 nodes only)
+__global__ void k3_ghost_collect(const uint8_t* cls, int nx, int ny, int nz, int pitch, int* count, int* list)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const int k = (z * ny + y) * pitch + x;
+    if ((cls[k] & CLS_MASK) != CLS_GHOST) return;
+    const int i = atomicAdd(count, 1);
+    if (list) list[i] = k;
+}
+
 // ---- geometry: classes (D3Q19 neighbourhood), a_v = |n| / 12 with the
 // integer n = sum 36 w_i c_i eps (36 w = 2 axes, 1 edges), flags ----
 __global__ void k3_cls1(const uint8_t* solid, uint8_t* cls, int nx, int ny, int nz, int pitch)
@@ -351,19 +381,26 @@ __global__ void k3_wet(const double* av, C* wet, size_t n, double coef)
 }
 
 // ---- initial state (FP64 arithmetic) ----
-__global__ void k3_droplet(const uint8_t* cls, double* phi, int nx, int ny, int nz, int pitch, double x0, double y0,
-                           double z0, double R, double W, int replace)
+// Outside r = R + 10 W the tanh profile is exactly 0 in FP64, so only the
+// droplet's bounding box (periodic in x and y) is evaluated; a replacing
+// call clears the field first.
+__global__ void k3_droplet(const uint8_t* cls, double* phi, int nx, int ny, int pitch, int xlo, int xw, int ylo,
+                           int yw, int zlo, double x0, double y0, double z0, double R, double W)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-    if (x >= nx || y >= ny) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = zlo + blockIdx.z;
+    if (i >= xw || j >= yw) return;
+    int x = (xlo + i) % nx, y = (ylo + j) % ny;
+    if (x < 0) x += nx;
+    if (y < 0) y += ny;
     const size_t k = ((size_t)z * ny + y) * pitch + x;
-    if (!zeta_of(cls[k])) { if (replace) phi[k] = 0.0; return; }
+    if (!zeta_of(cls[k])) return;
     double dx = fabs(x - x0), dy = fabs(y - y0);
     dx = fmod(dx, (double)nx); if (dx > 0.5 * nx) dx = nx - dx;
     dy = fmod(dy, (double)ny); if (dy > 0.5 * ny) dy = ny - dy;
     const double dz = z - z0, r = sqrt(dx * dx + dy * dy + dz * dz);
     const double v = 0.5 + 0.5 * tanh(2.0 * (R - r) / W);
-    if (replace || v > phi[k]) phi[k] = v;
+    if (v > phi[k]) phi[k] = v;
 }
 
 __global__ void k3_ghost_init(const uint8_t* cls, double* phi, int nx, int ny, int nz, int pitch)
@@ -477,7 +514,8 @@ __global__ void k3_sum(const double* partial, int n, double* out)
 
 constexpr int kMassBlocks = 1216;
 
-}  // namespace
+}  // namespace pfk3
+using namespace pfk3;
 
 // ---------------------------------------------------------------------------
 // the handle and the C ABI
@@ -500,6 +538,8 @@ struct pflbm3d {
     double* red = nullptr;
     double* out = nullptr;
     int* dstatus = nullptr;
+    int* ghosts = nullptr;      // indices of the ghost nodes
+    int n_ghosts = 0;
     int cur = 0;
     bool replace_phi = true, init_pending = false;
     int64_t steps = 0;
@@ -556,7 +596,7 @@ cudaError_t step3_prec(pflbm3d_t* h)
     Args3<PREC> a = make3<PREC>(h, h->cur);
     dim3 b(32, 8), g = grid3(h);
     k3_phi<PREC><<<g, b, 0, h->stream>>>(a);
-    k3_ghost<PREC><<<g, b, 0, h->stream>>>(a);
+    if (h->n_ghosts) k3_ghost<PREC><<<(h->n_ghosts + 255) / 256, 256, 0, h->stream>>>(a, h->ghosts, h->n_ghosts);
     k3_step<PREC, true><<<g, b, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
@@ -570,7 +610,7 @@ cudaError_t macro3_prec(pflbm3d_t* h, double* phi, double* u, double* p)
     a.o_p = p;
     dim3 b(32, 8), g = grid3(h);
     k3_phi<PREC><<<g, b, 0, h->stream>>>(a);
-    k3_ghost<PREC><<<g, b, 0, h->stream>>>(a);
+    if (h->n_ghosts) k3_ghost<PREC><<<(h->n_ghosts + 255) / 256, 256, 0, h->stream>>>(a, h->ghosts, h->n_ghosts);
     k3_step<PREC, false><<<g, b, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
@@ -619,7 +659,7 @@ void release3(pflbm3d_t* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* bufs[] = {h->cls, h->solid, h->av, h->wet, h->pop[0], h->pop[1], h->sprev, h->phi, h->phi0, h->mu0,
-                    h->red, h->out, h->dstatus};
+                    h->red, h->out, h->dstatus, h->ghosts};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -659,7 +699,7 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
     const int pitch = (p->nx + 63) / 64 * 64;
     const size_t plane = (size_t)p->nz * p->ny * pitch;
     if (26.0 * (double)plane >= 2147483647.0) return fail3(PFLBM_EINVAL, "lattice too large");
-    const size_t N = (size_t)p->nx * p->ny * p->nz, pl = (size_t)p->nx * p->ny;
+    const size_t pl = (size_t)p->nx * p->ny;
     for (size_t k = 0; k < pl; ++k)
         if (!p->solid_mask[k] || !p->solid_mask[pl + k] || !p->solid_mask[(p->nz - 2) * pl + k] ||
             !p->solid_mask[(p->nz - 1) * pl + k])
@@ -724,12 +764,26 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
         k3_wet<double><<<nb, 256, 0, h->stream>>>(h->av, (double*)h->wet, plane, coef);
     else
         k3_wet<float><<<nb, 256, 0, h->stream>>>(h->av, (float*)h->wet, plane, coef);
+    int* cnt = h->dstatus + 1;
+    cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
+    k3_ghost_collect<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch, cnt, nullptr);
+    cudaMemcpyAsync(&h->n_ghosts, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && h->n_ghosts > 0) {
+        if (cudaMalloc((void**)&h->ghosts, (size_t)h->n_ghosts * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            release3(h);
+            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+        }
+        cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
+        k3_ghost_collect<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch, cnt, h->ghosts);
+        cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
+        e = cudaStreamSynchronize(h->stream);
+    }
     if (e != cudaSuccess) {
         release3(h);
         return fail3(PFLBM_ECUDA, cudaGetErrorString(e));
     }
-    (void)N;
     *out = h;
     return PFLBM_OK;
 }
@@ -739,10 +793,29 @@ void pflbm3d_destroy(pflbm3d_t* h) { release3(h); }
 int pflbm3d_init_droplet(pflbm3d_t* h, double x0, double y0, double z0, double R)
 {
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
-    dim3 b(32, 8), g = grid3(h);
-    k3_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->nz, h->pitch, x0, y0, z0, R, h->prm.W,
-                                       h->replace_phi ? 1 : 0);
-    CK3(cudaGetLastError());
+    if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(z0) || !std::isfinite(R))
+        return fail3(PFLBM_EINVAL, "non-finite droplet");
+    if (h->replace_phi) CK3(cudaMemsetAsync(h->phi0, 0, (size_t)h->nz * h->ny * h->pitch * 8, h->stream));
+    const double reach = fabs(R) + 10.0 * h->prm.W;
+    auto span = [&](double c, int n, int& lo, int& w) {
+        lo = 0;
+        w = n;
+        if (2.0 * reach + 2.0 < n && fabs(c) < 1e8) {
+            lo = (int)floor(c - reach);
+            w = (int)(ceil(c + reach) - floor(c - reach)) + 1;
+        }
+    };
+    int xlo, xw, ylo, yw;
+    span(x0, h->nx, xlo, xw);
+    span(y0, h->ny, ylo, yw);
+    const int zlo = (int)fmin((double)h->nz, fmax(0.0, floor(z0 - reach)));
+    const int zhi = (int)fmax(-1.0, fmin((double)h->nz - 1, ceil(z0 + reach)));
+    if (zlo <= zhi) {
+        dim3 b(32, 8), g((xw + 31) / 32, (yw + 7) / 8, zhi - zlo + 1);
+        k3_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yw, zlo, x0, y0,
+                                           z0, R, h->prm.W);
+        CK3(cudaGetLastError());
+    }
     h->replace_phi = false;
     h->init_pending = true;
     h->steps = 0;
