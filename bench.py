@@ -387,7 +387,7 @@ def run_3d(args, torch, rank, world, local):
     lib()
     with torch.cuda.stream(stream):
         s = Solver3D(case.solid, theta_deg=case.theta_deg, precision=prec, device=local, stream=stream,
-                     **case.physical())
+                     step_path=args.path3d, **case.physical())
         for d in case.droplets:
             s.init_droplet(*d)
         s.step(args.warmup)
@@ -422,7 +422,7 @@ def run_3d(args, torch, rank, world, local):
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile) and case.shape == (128, 512, 512):
         try:
-            t = json.load(open(tfile)).get(f"many_flat3d:{prec}")
+            t = json.load(open(tfile)).get(f"many_flat3d:{prec}:{args.path3d}")
             if t and t.get("step_source_sha256") == step_source_sha256(
                     ("step3d.cu", "storage.cuh", "pflbm_internal.cuh")):
                 traffic = t["bytes_per_launch"]
@@ -434,7 +434,7 @@ def run_3d(args, torch, rank, world, local):
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         s2 = Solver3D(case.solid, theta_deg=case.theta_deg, precision=prec, device=local, stream=stream,
-                      **case.physical())
+                      step_path=args.path3d, **case.physical())
         for d in case.droplets:
             s2.init_droplet(*d)
         s2.step(e2e_steps)
@@ -457,19 +457,21 @@ def run_3d(args, torch, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp64": "f64"}[prec], "data": "synthetic",
             "config": {"workload": case.name, "nx": case.shape[2], "ny": case.shape[1], "nz": case.shape[0],
-                       "droplets": len(case.droplets), "precision": prec,
+                       "droplets": len(case.droplets), "precision": prec, "step_path": args.path3d,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state %.1f GB > L2, no flush needed" % (2 * 26 * (4 if prec == "fp32" else 8) * N / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "bytes_per_lu": bpl, "kernel": "whole step (3 launches)"},
+                         "bytes_per_lu": bpl,
+                         "kernel": "whole step (k3_fused, 1 launch)" if args.path3d == "fused"
+                         else "whole step (k3_phi, k3_ghost, k3_step: 3 launches)"},
             "hbm_roofline_mlups": peak * 1e9 / bpl / 1e6,
             "e2e": {"value": world * N * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": case.solid.nbytes / e2e_steps,
                     "d2h_bytes_per_step": (phi.nbytes + u.nbytes + p.nbytes) / e2e_steps,
                     "steps_per_solve": e2e_steps,
                     "includes": "create (mask upload, geometry), droplet init, steps, get"},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": (1 if args.path3d == "fused" else 3) * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -491,6 +493,8 @@ def main():
     ap.add_argument("--max-slots", type=int, default=512)
     ap.add_argument("--tick", type=int, default=200)
     ap.add_argument("--size3d", default="512x512x128", help="nx x ny x nz of many_flat3d")
+    ap.add_argument("--path3d", default="auto", choices=["auto", "fused", "three_pass"],
+                    help="3D step: one fused launch or three launches")
     ap.add_argument("--dgdt", type=int, default=0, choices=[0, 1],
                     help="(1/2) dG/dt: 0 backward difference, 1 omitted")
     args = ap.parse_args()

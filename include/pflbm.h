@@ -274,7 +274,16 @@ typedef struct {
     int precision;               /* PFLBM_FP64 or PFLBM_FP32 */
     int device;                  /* CUDA device; < 0: current */
     void* stream;                /* cudaStream_t; NULL: a stream of its own */
+    int step_path;               /* enum pflbm3d_step_path; the results agree to a few ulps */
+    int fused_zc;                /* planes per CTA of the fused step; <= 0: chosen by the library */
 } pflbm3d_params_t;
+
+/* How a 3D step runs. PFLBM3D_FUSED: one launch; each CTA marches a 32 x 8
+ * column through z, recomputing phi and the ghost values of its halo in
+ * shared memory. PFLBM3D_THREE_PASS: phi, ghost values and the
+ * collide-and-store as three launches through a phi array in HBM.
+ * PFLBM3D_AUTO (0): the faster of the two on GB300 (three launches). */
+enum pflbm3d_step_path { PFLBM3D_AUTO = 0, PFLBM3D_FUSED = 1, PFLBM3D_THREE_PASS = 2 };
 
 void pflbm3d_params_default(pflbm3d_params_t* p);
 int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p);

@@ -178,18 +178,22 @@ __device__ __forceinline__ void collide_f3(const Args3<PREC>& a, typename Store<
 // (3) the fused collide-and-store (COLLIDE) or the macroscopic read-back of
 // one zeta = 1 node; CHECK = false is the branch-free pull of a node without
 // bounce-back links
-template <int PREC, bool COLLIDE, bool CHECK>
-__device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, int z, int k, uint8_t code)
+// phi_at(i): phi at x + c_i (i = 0: the node itself); load_g(v, raw0): the
+// pulled g of the node. Both step kernels share this body, so their results
+// are identical.
+template <int PREC, bool COLLIDE, bool CHECK, typename PhiAt, typename LoadG>
+__device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, int z, int k, uint8_t code,
+                                          PhiAt phi_at, LoadG load_g)
 {
     using T = Store<PREC>;
     using C = typename T::C;
     const bool check = CHECK && (code & F_LINK) != 0;
     // ---- stencils on phi (D3Q19 weights), chemical potential ----
-    const C ph = a.phi[k];
+    const C ph = phi_at(0);
     C gp[3] = {C(0), C(0), C(0)}, lap = C(0);
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const C v = a.phi[nbr(a, x, y, z, q19x(i), q19y(i), q19z(i))];
+        const C v = phi_at(i);
         const C w3 = C(3) * q19w<C>(i);
         gp[0] += w3 * C(q19x(i)) * v;
         gp[1] += w3 * C(q19y(i)) * v;
@@ -265,7 +269,7 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     // ---- phase lattice (D3Q7): G_i = w_i h_i (3/2 s - 1/2 s_prev), h_0 = -5/2, h_i = -1/2 ----
     C g[7];
     typename T::G0T raw0;
-    pull_g7<PREC>(a, x, y, z, k, check, g, raw0);
+    load_g(g, raw0);
     const C s_now = u[0] * gp[0] + u[1] * gp[1] + u[2] * gp[2];
     const C src = C(1.5) * s_now - C(0.5) * a.sprev[k];
     const C am = a.alpha * mu;
@@ -295,10 +299,213 @@ __global__ void __launch_bounds__(256, PREC == PFLBM_FP64 ? 1 : PFLBM3D_STEP_MIN
         }
         return;
     }
+    auto phi_at = [&](int i) {
+        return i == 0 ? a.phi[k] : a.phi[nbr(a, x, y, z, q19x(i), q19y(i), q19z(i))];
+    };
     if (__any_sync(__activemask(), (code & F_LINK) != 0))
-        step_node<PREC, COLLIDE, true>(a, x, y, z, k, code);
+        step_node<PREC, COLLIDE, true>(a, x, y, z, k, code, phi_at,
+                                       [&](typename Store<PREC>::C (&v)[7], typename Store<PREC>::G0T& r) {
+                                           pull_g7<PREC>(a, x, y, z, k, (code & F_LINK) != 0, v, r);
+                                       });
     else
-        step_node<PREC, COLLIDE, false>(a, x, y, z, k, code);
+        step_node<PREC, COLLIDE, false>(a, x, y, z, k, code, phi_at,
+                                        [&](typename Store<PREC>::C (&v)[7], typename Store<PREC>::G0T& r) {
+                                            pull_g7<PREC>(a, x, y, z, k, false, v, r);
+                                        });
+}
+
+// ---------------------------------------------------------------------------
+// The fused step: one CTA owns a TX x TY column of nodes and marches through
+// planes [zb, zb + zc). Shared memory holds, per plane:
+//   P: phi on a window with a halo of 2 in x and y (36 x 12): the pulled-g
+//      sum on zeta = 1 nodes, the 27-neighbour mean on ghost nodes (filled in
+//      place: it reads zeta = 1 entries only), 0 elsewhere; and the node
+//      bytes. Ring of 5 planes.
+//   G: the pulled g of the CTA's own nodes, kept by the thread that owns the
+//      node until its collision two planes later. Ring of 4 planes.
+// Iteration z: P(z + 2) | sync | ghost fill of plane z + 1 | sync | step(z).
+// The ghost fill and the 2-wide halo are only done where a ghost lies in the
+// 34 x 10 window of the plane (per-tile plane flags from creation), and the
+// second barrier only after a fill. Slot reuse: iteration z + 1 writes P
+// slot (z + 3) mod 5, which no thread reads after iteration z's first
+// barrier.
+// ---------------------------------------------------------------------------
+constexpr int FW2 = TX + 4, FH2 = TY + 4, FN2 = FW2 * FH2;   // 36 x 12
+constexpr int FT = TX * TY;
+constexpr int FRING1 = 2 * (TX + 2) + 2 * TY;                // 84 halo-1 ring nodes
+constexpr int FRING2 = 2 * (TX + 4) + 2 * (TY + 2);          // 92 more for halo 2
+constexpr int FP = 5;
+
+template <int PREC>
+struct FusedSmem {
+    using C = typename Store<PREC>::C;
+    using G0T = typename Store<PREC>::G0T;
+    C P[FP][FN2];
+    C G[4][6][FT];
+    G0T G0[4][FT];
+    int xmap[FW2];      // periodic x of window column
+    int ymap[FH2];      // periodic y of window row
+    uint8_t cls[FP][FN2];
+};
+
+template <int PREC>
+size_t fused_smem_bytes() { return sizeof(FusedSmem<PREC>); }
+
+__device__ __forceinline__ int pslot(int z) { return (z + FP) % FP; }   // z >= -2
+
+// window position of ring node r (halo-1 ring first, then the halo-2 ring)
+__device__ __forceinline__ int ring_pos(int r)
+{
+    if (r < FRING1) {
+        if (r < TX + 2) return 1 * FW2 + (r + 1);
+        r -= TX + 2;
+        if (r < TX + 2) return (TY + 2) * FW2 + (r + 1);
+        r -= TX + 2;
+        if (r < TY) return (r + 2) * FW2 + 1;
+        r -= TY;
+        return (r + 2) * FW2 + (TX + 2);
+    }
+    r -= FRING1;
+    if (r < TX + 4) return r;
+    r -= TX + 4;
+    if (r < TX + 4) return (TY + 3) * FW2 + r;
+    r -= TX + 4;
+    if (r < TY + 2) return (r + 1) * FW2;
+    r -= TY + 2;
+    return (r + 1) * FW2 + (TX + 3);
+}
+
+// phi (and, for own nodes, g) of window position w of plane zp
+template <int PREC, bool OWN>
+__device__ __forceinline__ void fused_phi_node(const Args3<PREC>& a, FusedSmem<PREC>& sm, int zp, int w, int t)
+{
+    using C = typename Store<PREC>::C;
+    const int sp = pslot(zp);
+    if (zp < 0 || zp >= a.nz) {
+        sm.cls[sp][w] = CLS_INTERIOR;
+        sm.P[sp][w] = C(0);
+        return;
+    }
+    const int gx = sm.xmap[w % FW2], gy = sm.ymap[w / FW2];
+    const int k = (zp * a.ny + gy) * a.pitch + gx;
+    const uint8_t c = a.cls[k];
+    sm.cls[sp][w] = c;
+    if (!zeta_of(c)) {
+        sm.P[sp][w] = C(0);
+        return;
+    }
+    C v[7];
+    typename Store<PREC>::G0T r;
+    if (__any_sync(__activemask(), (c & F_LINK) != 0))
+        pull_g7<PREC>(a, gx, gy, zp, k, (c & F_LINK) != 0, v, r);
+    else
+        pull_g7<PREC>(a, gx, gy, zp, k, false, v, r);
+    sm.P[sp][w] = v[0] + sum6(v);
+    if (OWN) {
+        const int sg = zp & 3;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) sm.G[sg][j][t] = v[j + 1];
+        sm.G0[sg][t] = r;
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void fused_phi_plane(const Args3<PREC>& a, FusedSmem<PREC>& sm, int zp, bool halo2)
+{
+    const int t = threadIdx.y * TX + threadIdx.x;
+    fused_phi_node<PREC, true>(a, sm, zp, (threadIdx.y + 2) * FW2 + threadIdx.x + 2, t);
+    const int nring = halo2 ? FRING1 + FRING2 : FRING1;
+    for (int r = t; r < nring; r += FT) fused_phi_node<PREC, false>(a, sm, zp, ring_pos(r), t);
+}
+
+// ghost values of plane zq on the 34 x 10 window, in place
+template <int PREC>
+__device__ __forceinline__ void fused_fill_plane(const Args3<PREC>& a, FusedSmem<PREC>& sm, int zq)
+{
+    using C = typename Store<PREC>::C;
+    const int sq = pslot(zq);
+    for (int i = threadIdx.y * TX + threadIdx.x; i < (TX + 2) * (TY + 2); i += FT) {
+        const int w = (i / (TX + 2) + 1) * FW2 + (i % (TX + 2)) + 1;
+        if ((sm.cls[sq][w] & CLS_MASK) != CLS_GHOST) continue;
+        // same summation order as k3_ghost
+        C num = C(0), den = C(0);
+        for (int dz = -1; dz <= 1; ++dz) {
+            if (zq + dz < 0 || zq + dz >= a.nz) continue;
+            const int s2 = pslot(zq + dz);
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int m = w + dy * FW2 + dx;
+                    if (zeta_of(sm.cls[s2][m])) { num += sm.P[s2][m]; den += C(1); }
+                }
+        }
+        sm.P[sq][w] = num / den;
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256, PREC == PFLBM_FP64 ? 1 : PFLBM3D_STEP_MINB)
+k3_fused(Args3<PREC> a, int zc, const uint8_t* __restrict__ gflag)
+{
+    using C = typename Store<PREC>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedSmem<PREC>& sm = *reinterpret_cast<FusedSmem<PREC>*>(smem_raw);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tiles = gridDim.x * gridDim.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
+    const int zb = 1 + blockIdx.z * zc, ze = min(zb + zc, a.nz - 1);   // zeta = 1 planes are 1 .. nz-2
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
+    const int x = x0 + tx, y = y0 + ty;
+    // ghost in the 34 x 10 window of plane z (planes outside the lattice: none)
+    auto ghosts_at = [&](int z) { return z >= 0 && z < a.nz && gflag[(size_t)z * tiles + tile] != 0; };
+    auto halo2_at = [&](int z) { return ghosts_at(z - 1) || ghosts_at(z) || ghosts_at(z + 1); };
+    if (t < FW2) sm.xmap[t] = ((x0 - 2 + t) % a.nx + a.nx) % a.nx;
+    if (t < FH2) sm.ymap[t] = ((y0 - 2 + t) % a.ny + a.ny) % a.ny;
+    __syncthreads();
+    for (int zp = zb - 2; zp <= zb + 1; ++zp) fused_phi_plane<PREC>(a, sm, zp, halo2_at(zp));
+    __syncthreads();
+    if (ghosts_at(zb - 1)) fused_fill_plane<PREC>(a, sm, zb - 1);
+    if (ghosts_at(zb)) fused_fill_plane<PREC>(a, sm, zb);
+    __syncthreads();
+    for (int z = zb; z < ze; ++z) {
+        fused_phi_plane<PREC>(a, sm, z + 2, halo2_at(z + 2));
+        __syncthreads();
+        if (ghosts_at(z + 1)) {
+            fused_fill_plane<PREC>(a, sm, z + 1);
+            __syncthreads();
+        }
+        if (x < a.nx && y < a.ny) {
+            const uint8_t code = sm.cls[pslot(z)][(ty + 2) * FW2 + tx + 2];
+            if (zeta_of(code)) {
+                const int k = (z * a.ny + y) * a.pitch + x;
+                const int w = (ty + 2) * FW2 + tx + 2;
+                auto phi_at = [&](int i) { return sm.P[pslot(z + q19z(i))][w + q19y(i) * FW2 + q19x(i)]; };
+                const int sg = z & 3;
+                auto load_g = [&](C (&v)[7], typename Store<PREC>::G0T& r) {
+                    r = sm.G0[sg][t];
+                    v[0] = Store<PREC>::g0(r);
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) v[j + 1] = sm.G[sg][j][t];
+                };
+                if (__any_sync(__activemask(), (code & F_LINK) != 0))
+                    step_node<PREC, true, true>(a, x, y, z, k, code, phi_at, load_g);
+                else
+                    step_node<PREC, true, false>(a, x, y, z, k, code, phi_at, load_g);
+            }
+        }
+    }
+}
+
+// per tile and plane: 1 if a ghost node lies in the tile's 34 x 10 window
+__global__ void k3_ghost_flags(const uint8_t* cls, int nx, int ny, int nz, int pitch, int tiles_x, uint8_t* gflag)
+{
+    const int tile = blockIdx.x, z = blockIdx.y;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    int any = 0;
+    for (int i = threadIdx.x; i < (TX + 2) * (TY + 2); i += blockDim.x) {
+        const int x = ((x0 - 1 + i % (TX + 2)) % nx + nx) % nx, y = ((y0 - 1 + i / (TX + 2)) % ny + ny) % ny;
+        if ((cls[((size_t)z * ny + y) * pitch + x] & CLS_MASK) == CLS_GHOST) any = 1;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) gflag[(size_t)z * gridDim.x + tile] = (uint8_t)any;
 }
 
 // ghost nodes: count, then list (any order: each ghost value depends on
@@ -540,6 +747,9 @@ struct pflbm3d {
     int* dstatus = nullptr;
     int* ghosts = nullptr;      // indices of the ghost nodes
     int n_ghosts = 0;
+    bool fused = true;          // one-launch step (k3_fused) or three launches
+    uint8_t* gflag = nullptr;   // [nz][tiles]: a ghost in the tile's 34 x 10 window
+    int fused_zc = 0;           // planes per CTA of the fused step
     int cur = 0;
     bool replace_phi = true, init_pending = false;
     int64_t steps = 0;
@@ -595,6 +805,12 @@ cudaError_t step3_prec(pflbm3d_t* h)
 {
     Args3<PREC> a = make3<PREC>(h, h->cur);
     dim3 b(32, 8), g = grid3(h);
+    if (h->fused) {
+        const int chunks = (h->nz - 2 + h->fused_zc - 1) / h->fused_zc;
+        dim3 gf((h->nx + TX - 1) / TX, (h->ny + TY - 1) / TY, chunks);
+        k3_fused<PREC><<<gf, b, fused_smem_bytes<PREC>(), h->stream>>>(a, h->fused_zc, h->gflag);
+        return cudaGetLastError();
+    }
     k3_phi<PREC><<<g, b, 0, h->stream>>>(a);
     if (h->n_ghosts) k3_ghost<PREC><<<(h->n_ghosts + 255) / 256, 256, 0, h->stream>>>(a, h->ghosts, h->n_ghosts);
     k3_step<PREC, true><<<g, b, 0, h->stream>>>(a);
@@ -659,7 +875,7 @@ void release3(pflbm3d_t* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* bufs[] = {h->cls, h->solid, h->av, h->wet, h->pop[0], h->pop[1], h->sprev, h->phi, h->phi0, h->mu0,
-                    h->red, h->out, h->dstatus, h->ghosts};
+                    h->red, h->out, h->dstatus, h->ghosts, h->gflag};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -764,6 +980,46 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
         k3_wet<double><<<nb, 256, 0, h->stream>>>(h->av, (double*)h->wet, plane, coef);
     else
         k3_wet<float><<<nb, 256, 0, h->stream>>>(h->av, (float*)h->wet, plane, coef);
+    // step path: the fused z-marching kernel unless asked otherwise
+    if (p->step_path != PFLBM3D_AUTO && p->step_path != PFLBM3D_FUSED && p->step_path != PFLBM3D_THREE_PASS) {
+        release3(h);
+        return fail3(PFLBM_EINVAL, "unknown step_path");
+    }
+    h->fused = p->step_path == PFLBM3D_FUSED;
+    if (h->fused) {
+        const size_t sb = p->precision == PFLBM_FP64 ? fused_smem_bytes<PFLBM_FP64>() : fused_smem_bytes<PFLBM_FP32>();
+        cudaError_t ea = p->precision == PFLBM_FP64
+            ? cudaFuncSetAttribute(k3_fused<PFLBM_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb)
+            : cudaFuncSetAttribute(k3_fused<PFLBM_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+        int per_sm = 0, sms = 0;
+        if (ea == cudaSuccess)
+            ea = p->precision == PFLBM_FP64
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fused<PFLBM_FP64>, 256, sb)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fused<PFLBM_FP32>, 256, sb);
+        if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ea != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            release3(h);
+            return fail3(PFLBM_ECUDA, "fused 3D step kernel cannot be resident");
+        }
+        const long long tiles = (long long)((h->nx + TX - 1) / TX) * ((h->ny + TY - 1) / TY);
+        const int nzz = h->nz - 2;
+        int zc = p->fused_zc;
+        if (zc <= 0) {
+            // about six waves of resident CTAs, 8 to 64 planes per CTA
+            zc = (int)(((long long)nzz * tiles) / (6LL * sms * per_sm));
+            zc = zc < 8 ? 8 : (zc > 64 ? 64 : zc);
+        }
+        h->fused_zc = zc > nzz ? nzz : zc;
+        const int tiles_x = (h->nx + TX - 1) / TX;
+        if (cudaMalloc((void**)&h->gflag, (size_t)tiles * h->nz) != cudaSuccess) {
+            cudaGetLastError();
+            release3(h);
+            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+        }
+        k3_ghost_flags<<<dim3((unsigned)tiles, h->nz), 128, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch,
+                                                                             tiles_x, h->gflag);
+    }
     int* cnt = h->dstatus + 1;
     cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
     k3_ghost_collect<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch, cnt, nullptr);

@@ -54,7 +54,8 @@ class Params3D(ctypes.Structure):
                 ("theta_deg", ctypes.c_double), ("sigma", ctypes.c_double), ("W", ctypes.c_double),
                 ("M", ctypes.c_double), ("tau_f", ctypes.c_double), ("rho_l", ctypes.c_double),
                 ("rho_g", ctypes.c_double), ("tau_g", ctypes.c_double), ("precision", ctypes.c_int),
-                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("step_path", ctypes.c_int),
+                ("fused_zc", ctypes.c_int)]
 
 
 class Schedule(ctypes.Structure):
@@ -432,12 +433,14 @@ class Solver3D:
     """One three-dimensional lattice (``pflbm3d_t``): f on D3Q19, g on D3Q7.
 
     ``solid``: uint8 [nz, ny, nx] mask (1 = solid; planes z = 0, 1, nz-2,
-    nz-1 solid). ``precision``: "fp64" or "fp32". The library allocates its
-    own device memory; work runs on ``stream`` (default: the current stream).
+    nz-1 solid). ``precision``: "fp64" or "fp32". ``step_path``: "auto",
+    "fused" (one launch per step) or "three_pass". The library allocates its own device
+    memory; work runs on ``stream`` (default: the current stream).
     """
 
     def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
-                 rho_l=1.0, rho_g=0.1, tau_g=0.0, precision="fp32", device=None, stream=None):
+                 rho_l=1.0, rho_g=0.1, tau_g=0.0, precision="fp32", device=None, stream=None,
+                 step_path="auto", fused_zc=0):
         import torch
         L = lib()
         solid = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -456,6 +459,8 @@ class Solver3D:
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.device = dev
         p.stream = ctypes.c_void_p(stream.cuda_stream)
+        p.step_path = {"auto": 0, "fused": 1, "three_pass": 2}[step_path]
+        p.fused_zc = int(fused_zc)
         h = _H()
         _check(L.pflbm3d_create(ctypes.byref(h), ctypes.byref(p)))
         self._h = h

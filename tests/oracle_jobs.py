@@ -141,6 +141,9 @@ def case3d_by_name(name):
                          theta_deg=120.0, steps=200)
     if name == "sphere3d":
         return wl.droplet_on_sphere_3d(n=32, Rs=6.0, R=7.0, theta=75.0, steps=200)
+    if name == "tiny3d":          # smaller than one tile and its halo in x and y
+        s, zw = wl.box3d(3, 4, 9)
+        return wl.Case3D("tiny3d", s, [(1.0, 2.0, zw, 3.0)], zw, theta_deg=50.0, steps=60)
     raise KeyError(name)
 
 

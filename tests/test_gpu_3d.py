@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TOL = {"fp64": dict(phi=1e-10, u=1e-12, p=1e-12, mass=1e-9), "fp32": dict(phi=1e-5, u=1e-6, p=1e-6, mass=1e-4)}
-CASES = ["flat3d", "flat3d_two", "sphere3d"]
+CASES = ["flat3d", "flat3d_two", "sphere3d", "tiny3d"]
 
 _pool = None
 _fut = {}
@@ -36,14 +36,15 @@ def ref(name):
     return _fut[name].get(timeout=900)
 
 
-def gpu_run(name, precision):
+def gpu_run(name, precision, path="fused", zc=0, steps=None):
     from paper_2312_00369_gb300 import pflbm
     c = oj.case3d_by_name(name)
-    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision=precision, **c.physical())
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision=precision, step_path=path, fused_zc=zc,
+                       **c.physical())
     for d in c.droplets:
         s.init_droplet(*d)
     m0 = s.mass()
-    s.step(c.steps)
+    s.step(c.steps if steps is None else steps)
     s.check()
     phi, u, p = s.get()
     g = s.geometry()
@@ -64,11 +65,12 @@ def test_geometry_3d(name):
     assert np.max(np.abs(g["av"] - r["av"])) < 1e-15
 
 
+@pytest.mark.parametrize("path", ["fused", "three_pass"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", CASES)
-def test_parity_3d(name, precision):
+def test_parity_3d(name, precision, path):
     r = ref(name)
-    g = gpu_run(name, precision)
+    g = gpu_run(name, precision, path)
     t = TOL[precision]
     zeta = r["cls"] <= 1
     dphi = np.max(np.abs(g["phi"] - r["phi"]))
@@ -78,6 +80,27 @@ def test_parity_3d(name, precision):
     assert abs(g["mass0"] - r["mass0"]) <= t["mass"] and abs(g["mass"] - r["mass"]) <= t["mass"]
     # the droplet moved: the comparison is not of two initial states
     assert np.max(np.abs(r["u"])) > 1e-6
+
+
+ULP_BOUND = {"fp64": dict(phi=2e-15, u=1e-16, p=1e-16), "fp32": dict(phi=1e-6, u=1e-8, p=1e-8)}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,zc", [("flat3d", 1), ("flat3d", 0), ("flat3d", 100), ("sphere3d", 3),
+                                     ("tiny3d", 2)])
+def test_fused_equals_three_pass(name, zc, precision):
+    # The two step paths inline the same arithmetic, so a difference can only
+    # come from the compiler pairing multiply-adds differently: phi is equal
+    # after one step and within a few ulps after 40, whatever the number of
+    # planes each CTA of the fused path marches.
+    a = gpu_run(name, precision, "three_pass", steps=1)
+    b = gpu_run(name, precision, "fused", zc=zc, steps=1)
+    assert np.array_equal(a["phi"], b["phi"])
+    a = gpu_run(name, precision, "three_pass", steps=40)
+    b = gpu_run(name, precision, "fused", zc=zc, steps=40)
+    for key, bound in ULP_BOUND[precision].items():
+        assert np.max(np.abs(a[key] - b[key])) <= bound, key
+    assert abs(a["mass"] - b["mass"]) <= 1e3 * bound * abs(a["mass"]) * 1e-3 + ULP_BOUND[precision]["phi"] * a["phi"].size
 
 
 def test_rejects_bad_mask_3d():
