@@ -1,0 +1,54 @@
+"""Full-length inclined- and curved-wall cases against stored FP64 oracle runs.
+
+Staircase wall at 30 deg on 400 x 200 with theta in {30, 60, 90, 120, 150}
+and a cylinder of radius 100 on 512 x 512 with theta = 90 (Secs. 3.2, 3.3),
+20000 steps each, the (1/2) dG/dt term omitted (dgdt mode 1). The stored
+values come from ``tests/golden/make_config1_oracle.py``, which calls only
+the oracle. Compared: the contact angle of the fitted circle (within 0.5 deg
+of the oracle's), phi on every 4th node, and the phi mass.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config1_oracle.npz")
+CASES = [("incline", th) for th in (30.0, 60.0, 90.0, 120.0, 150.0)] + [("cylinder", 90.0)]
+TOL = {"fp64": dict(phi=1e-10, theta=0.5, mass=1e-9), "fp32": dict(phi=1e-5, theta=0.5, mass=1e-3)}
+
+
+@pytest.fixture(scope="module")
+def golden():
+    if not os.path.exists(GOLDEN):
+        pytest.skip("config1_oracle.npz not generated")
+    return dict(np.load(GOLDEN))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind,theta", CASES)
+def test_config1_against_oracle(golden, kind, theta, precision):
+    from paper_2312_00369_gb300 import pflbm
+    from paper_2312_00369_gb300 import workloads as wl
+    key = f"{kind}_{int(theta)}"
+    steps = int(golden[f"{key}:steps"])
+    assert int(golden[f"{key}:dgdt"]) == 1
+    c = (wl.droplet_on_incline(theta=theta, steps=steps) if kind == "incline"
+         else wl.droplet_on_cylinder(theta=theta, steps=steps))
+    s = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision=precision, dgdt_mode=1, **c.physical())
+    for d in c.droplets:
+        s.init_droplet(*d)
+    s.step(steps)
+    s.check()
+    th, _, n = s.contact_angle(dict(c.wall, exclude=1.5 * c.W))
+    phi, _, _ = s.get()
+    m = s.mass()
+    s.close()
+    t = TOL[precision]
+    dphi = float(np.max(np.abs(phi[::4, ::4] - golden[f"{key}:phi_sub"])))
+    assert dphi <= t["phi"], dphi
+    assert abs(th - float(golden[f"{key}:theta"])) <= t["theta"], (th, float(golden[f"{key}:theta"]))
+    assert n > 0
+    assert abs(m - float(golden[f"{key}:mass"])) <= t["mass"]
