@@ -17,7 +17,10 @@ torch = pytest.importorskip("torch")
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config1_oracle.npz")
 CASES = [("incline", th) for th in (30.0, 60.0, 90.0, 120.0, 150.0)] + [("cylinder", 90.0)]
-TOL = {"fp64": dict(phi=1e-10, theta=0.5, mass=1e-9), "fp32": dict(phi=1e-5, theta=0.5, mass=1e-3)}
+# mass: relative. In FP32 the six moving g_i are rounded to 2^-24 relative at
+# every node and step; over 2e4 steps this drifts the mass by ~1e-6 relative
+# (measured 1.0e-6 to 1.7e-6), inside the 1e-5 bar of the other FP32 tests.
+TOL = {"fp64": dict(phi=1e-10, theta=0.5, mass=1e-12), "fp32": dict(phi=1e-5, theta=0.5, mass=1e-5)}
 
 
 @pytest.fixture(scope="module")
@@ -51,4 +54,5 @@ def test_config1_against_oracle(golden, kind, theta, precision):
     assert dphi <= t["phi"], dphi
     assert abs(th - float(golden[f"{key}:theta"])) <= t["theta"], (th, float(golden[f"{key}:theta"]))
     assert n > 0
-    assert abs(m - float(golden[f"{key}:mass"])) <= t["mass"]
+    m0 = float(golden[f"{key}:mass"])
+    assert abs(m - m0) <= t["mass"] * abs(m0), (m, m0)
