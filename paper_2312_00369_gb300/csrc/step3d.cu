@@ -26,6 +26,10 @@ using namespace pfk;
 #define PFLBM3D_STEP_MINB 4   // resident 256-thread CTAs per SM asked of the FP32 step kernel
 #endif
 
+#ifndef PFLBM3D_FUSED_STEP_FIRST
+#define PFLBM3D_FUSED_STEP_FIRST 0   // order of the two halves of a fused-step iteration
+#endif
+
 namespace pfk3 {
 
 // D3Q19: rest, +x, -x, +y, -y, +z, -z, then the 12 edges in opposite pairs
@@ -157,12 +161,23 @@ __global__ void __launch_bounds__(256) k3_ghost(Args3<PREC> a, const int* __rest
     a.phi[k] = num / den;
 }
 
+// Collision of the opposite pair (I, I + 1) of D3Q19. With c = c_I, f^eq
+// (Eqs. feq_i, Siu) and the forcing of Eq. GGi split into a part even in c
+// and a part odd in c:
+//   omega f^eq_i + F_i = w (S +- A),
+//   S = omega (3 p + rho (9/2 (c.u)^2 - 3/2 u.u)) + 3 (1 - 1/(2 tau)) (c.u)(c.grad rho),
+//   A = 3 omega rho (c.u) + 3 (1 - 1/(2 tau)) (c.F),
+// so f*_I = (1 - omega) f_I + w (S + A) and f*_{I+1} = (1 - omega) f_{I+1} + w (S - A).
+// K holds the per-node constants: base = omega (3 p - 3/2 rho u.u),
+// c45 = 9/2 omega rho, c3 = 3 omega rho, pre3 = 3 (1 - 1/(2 tau)).
+template <typename C>
+struct PairK { C base, c45, c3, pre3, omf; };
+
 template <int PREC, int I>
-__device__ __forceinline__ void collide_f3(const Args3<PREC>& a, typename Store<PREC>::C fi,
-                                           typename Store<PREC>::C p, typename Store<PREC>::C rho,
-                                           const typename Store<PREC>::C u[3], typename Store<PREC>::C uu,
-                                           const typename Store<PREC>::C F[3], const typename Store<PREC>::C dr[3],
-                                           int k)
+__device__ __forceinline__ void collide_pair(const Args3<PREC>& a, typename Store<PREC>::C fI,
+                                             typename Store<PREC>::C fO, const PairK<typename Store<PREC>::C>& K,
+                                             const typename Store<PREC>::C u[3], const typename Store<PREC>::C F[3],
+                                             const typename Store<PREC>::C dr[3], int k)
 {
     using C = typename Store<PREC>::C;
     constexpr int X = q19x(I), Y = q19y(I), Z = q19z(I);
@@ -170,9 +185,10 @@ __device__ __forceinline__ void collide_f3(const Args3<PREC>& a, typename Store<
     const C cu = C(X) * u[0] + C(Y) * u[1] + C(Z) * u[2];
     const C cF = C(X) * F[0] + C(Y) * F[1] + C(Z) * F[2];
     const C cd = C(X) * dr[0] + C(Y) * dr[1] + C(Z) * dr[2];
-    const C feq = w * (C(3) * p + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
-    const C Fi = a.force_pre * w * C(3) * (cF + cu * cd);
-    a.f_out[I * a.plane + k] = Store<PREC>::template st<I>(fi + a.omega_f * (feq - fi) + Fi);
+    const C S = w * (K.base + cu * (K.c45 * cu + K.pre3 * cd));
+    const C A = w * (K.c3 * cu + K.pre3 * cF);
+    a.f_out[I * a.plane + k] = Store<PREC>::template st<I>(K.omf * fI + (S + A));
+    a.f_out[(I + 1) * a.plane + k] = Store<PREC>::template st<I + 1>(K.omf * fO + (S - A));
 }
 
 // (3) the fused collide-and-store (COLLIDE) or the macroscopic read-back of
@@ -189,16 +205,18 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     using C = typename T::C;
     const bool check = CHECK && (code & F_LINK) != 0;
     // ---- stencils on phi (D3Q19 weights), chemical potential ----
+    // opposite pairs: grad += 3 w c (v_I - v_O), lap += 6 w (v_I + v_O - 2 phi)
     const C ph = phi_at(0);
     C gp[3] = {C(0), C(0), C(0)}, lap = C(0);
 #pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        const C v = phi_at(i);
+    for (int i = 1; i < 19; i += 2) {
+        const C vp = phi_at(i), vm = phi_at(i + 1);
         const C w3 = C(3) * q19w<C>(i);
-        gp[0] += w3 * C(q19x(i)) * v;
-        gp[1] += w3 * C(q19y(i)) * v;
-        gp[2] += w3 * C(q19z(i)) * v;
-        lap += C(2) * w3 * (v - ph);
+        const C d = w3 * (vp - vm);
+        if (q19x(i)) gp[0] += C(q19x(i)) * d;
+        if (q19y(i)) gp[1] += C(q19y(i)) * d;
+        if (q19z(i)) gp[2] += C(q19z(i)) * d;
+        lap += C(2) * w3 * ((vp + vm) - C(2) * ph);
     }
     const C wet = (code & F_WET) ? a.wet[k] : C(0);
     const C mu = a.beta4 * ph * (ph - C(1)) * (ph - C(0.5)) - a.kappa * lap - wet * (ph - ph * ph);
@@ -228,11 +246,12 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     f[18] = pull3<18, PREC>(a, a.f_in, x, y, z, k, check);
     C m[3] = {C(0), C(0), C(0)}, fsum = C(0);
 #pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        m[0] += C(q19x(i)) * f[i];
-        m[1] += C(q19y(i)) * f[i];
-        m[2] += C(q19z(i)) * f[i];
-        fsum += f[i];
+    for (int i = 1; i < 19; i += 2) {
+        const C d = f[i] - f[i + 1];
+        if (q19x(i)) m[0] += C(q19x(i)) * d;
+        if (q19y(i)) m[1] += C(q19y(i)) * d;
+        if (q19z(i)) m[2] += C(q19z(i)) * d;
+        fsum += f[i] + f[i + 1];
     }
     const C ir = C(1) / rho;
     const C u[3] = {(m[0] + C(0.5) * F[0]) * ir, (m[1] + C(0.5) * F[1]) * ir, (m[2] + C(0.5) * F[2]) * ir};
@@ -248,24 +267,21 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     }
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
     a.f_out[k] = T::template st<0>(f[0] + a.omega_f * ((C(-2) * p - C(0.5) * rho * uu) - f[0]));
-    collide_f3<PREC, 1>(a, f[1], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 2>(a, f[2], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 3>(a, f[3], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 4>(a, f[4], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 5>(a, f[5], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 6>(a, f[6], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 7>(a, f[7], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 8>(a, f[8], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 9>(a, f[9], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 10>(a, f[10], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 11>(a, f[11], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 12>(a, f[12], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 13>(a, f[13], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 14>(a, f[14], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 15>(a, f[15], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 16>(a, f[16], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 17>(a, f[17], p, rho, u, uu, F, dr, k);
-    collide_f3<PREC, 18>(a, f[18], p, rho, u, uu, F, dr, k);
+    PairK<C> K;
+    K.base = a.omega_f * (C(3) * p - C(1.5) * rho * uu);
+    K.c45 = a.omega_f * C(4.5) * rho;
+    K.c3 = a.omega_f * C(3) * rho;
+    K.pre3 = C(3) * a.force_pre;
+    K.omf = C(1) - a.omega_f;
+    collide_pair<PREC, 1>(a, f[1], f[2], K, u, F, dr, k);
+    collide_pair<PREC, 3>(a, f[3], f[4], K, u, F, dr, k);
+    collide_pair<PREC, 5>(a, f[5], f[6], K, u, F, dr, k);
+    collide_pair<PREC, 7>(a, f[7], f[8], K, u, F, dr, k);
+    collide_pair<PREC, 9>(a, f[9], f[10], K, u, F, dr, k);
+    collide_pair<PREC, 11>(a, f[11], f[12], K, u, F, dr, k);
+    collide_pair<PREC, 13>(a, f[13], f[14], K, u, F, dr, k);
+    collide_pair<PREC, 15>(a, f[15], f[16], K, u, F, dr, k);
+    collide_pair<PREC, 17>(a, f[17], f[18], K, u, F, dr, k);
     // ---- phase lattice (D3Q7): G_i = w_i h_i (3/2 s - 1/2 s_prev), h_0 = -5/2, h_i = -1/2 ----
     C g[7];
     typename T::G0T raw0;
@@ -273,11 +289,10 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     const C s_now = u[0] * gp[0] + u[1] * gp[1] + u[2] * gp[2];
     const C src = C(1.5) * s_now - C(0.5) * a.sprev[k];
     const C am = a.alpha * mu;
+    // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu - src / 2), the same for i = 1..6
+    const C gm = q7w<C>(1) * (a.omega_g * am - C(0.5) * src), omg = C(1) - a.omega_g;
 #pragma unroll
-    for (int i = 1; i < 7; ++i) {
-        const C w = q7w<C>(i);
-        a.g_out[i * a.plane + k] = T::template st<1>(g[i] + a.omega_g * (w * am - g[i]) + w * C(-0.5) * src);
-    }
+    for (int i = 1; i < 7; ++i) a.g_out[i * a.plane + k] = T::template st<1>(omg * g[i] + gm);
     const C d0 = a.omega_g * (sum6(g) - C(0.75) * am) + q7w<C>(0) * C(-2.5) * src;
     a.g0_out[k] = T::g0_add(raw0, d0, a.status);
     a.sprev[k] = s_now;
@@ -322,13 +337,11 @@ __global__ void __launch_bounds__(256, PREC == PFLBM_FP64 ? 1 : PFLBM3D_STEP_MIN
 //      place: it reads zeta = 1 entries only), 0 elsewhere; and the node
 //      bytes. Ring of 5 planes.
 //   G: the pulled g of the CTA's own nodes, kept by the thread that owns the
-//      node until its collision two planes later. Ring of 4 planes.
-// Iteration z: P(z + 2) | sync | ghost fill of plane z + 1 | sync | step(z).
-// The ghost fill and the 2-wide halo are only done where a ghost lies in the
-// 34 x 10 window of the plane (per-tile plane flags from creation), and the
-// second barrier only after a fill. Slot reuse: iteration z + 1 writes P
-// slot (z + 3) mod 5, which no thread reads after iteration z's first
-// barrier.
+//      node until its collision three planes later. Ring of 4 planes.
+// Iteration z: P(z + 3) and step(z) | sync | ghost fill of plane z + 2 |
+// sync. The ghost fill and the 2-wide halo are only done where a ghost lies
+// in the 34 x 10 window of the plane (per-tile plane flags from creation),
+// and the second barrier only after a fill.
 // ---------------------------------------------------------------------------
 constexpr int FW2 = TX + 4, FH2 = TY + 4, FN2 = FW2 * FH2;   // 36 x 12
 constexpr int FT = TX * TY;
@@ -460,18 +473,18 @@ k3_fused(Args3<PREC> a, int zc, const uint8_t* __restrict__ gflag)
     if (t < FW2) sm.xmap[t] = ((x0 - 2 + t) % a.nx + a.nx) % a.nx;
     if (t < FH2) sm.ymap[t] = ((y0 - 2 + t) % a.ny + a.ny) % a.ny;
     __syncthreads();
-    for (int zp = zb - 2; zp <= zb + 1; ++zp) fused_phi_plane<PREC>(a, sm, zp, halo2_at(zp));
+    // warm-up: P(zb-2) .. P(zb+2), then the ghost values of zb-1 .. zb+1
+    for (int zp = zb - 2; zp <= zb + 2; ++zp) fused_phi_plane<PREC>(a, sm, zp, halo2_at(zp));
     __syncthreads();
-    if (ghosts_at(zb - 1)) fused_fill_plane<PREC>(a, sm, zb - 1);
-    if (ghosts_at(zb)) fused_fill_plane<PREC>(a, sm, zb);
+    for (int zq = zb - 1; zq <= zb + 1; ++zq)
+        if (ghosts_at(zq)) fused_fill_plane<PREC>(a, sm, zq);
     __syncthreads();
+    // Iteration z: step(z) and P(z + 3) in one phase (their loads overlap),
+    // barrier, ghost values of plane z + 2, barrier if any were filled.
+    // P(z + 3) takes slot (z - 2) mod 5, which step(z) does not read; the
+    // planes in use are z - 1 .. z + 3.
     for (int z = zb; z < ze; ++z) {
-        fused_phi_plane<PREC>(a, sm, z + 2, halo2_at(z + 2));
-        __syncthreads();
-        if (ghosts_at(z + 1)) {
-            fused_fill_plane<PREC>(a, sm, z + 1);
-            __syncthreads();
-        }
+        if (!PFLBM3D_FUSED_STEP_FIRST) fused_phi_plane<PREC>(a, sm, z + 3, halo2_at(z + 3));
         if (x < a.nx && y < a.ny) {
             const uint8_t code = sm.cls[pslot(z)][(ty + 2) * FW2 + tx + 2];
             if (zeta_of(code)) {
@@ -490,6 +503,12 @@ k3_fused(Args3<PREC> a, int zc, const uint8_t* __restrict__ gflag)
                 else
                     step_node<PREC, true, false>(a, x, y, z, k, code, phi_at, load_g);
             }
+        }
+        if (PFLBM3D_FUSED_STEP_FIRST) fused_phi_plane<PREC>(a, sm, z + 3, halo2_at(z + 3));
+        __syncthreads();
+        if (ghosts_at(z + 2)) {
+            fused_fill_plane<PREC>(a, sm, z + 2);
+            __syncthreads();
         }
     }
 }
