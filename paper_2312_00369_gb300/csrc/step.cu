@@ -302,24 +302,36 @@ __device__ __forceinline__ void stencils(C (*s_phi)[TX + 4], int py, int px, C& 
     lap = ((E + W) + (N + Sx)) * (C(2) / C(3)) + ((NE + NW) + (SE + SW)) * (C(1) / C(6)) - c * (C(10) / C(3));
 }
 
-template <int PREC, int I>
-__device__ __forceinline__ void collide_f_dir(const StepArgs<PREC>& a, typename Store<PREC>::C f_i,
-                                              typename Store<PREC>::C p, typename Store<PREC>::C rho,
-                                              typename Store<PREC>::C ux, typename Store<PREC>::C uy,
-                                              typename Store<PREC>::C uu, typename Store<PREC>::C Fx,
-                                              typename Store<PREC>::C Fy, typename Store<PREC>::C drx,
-                                              typename Store<PREC>::C dry, typename Store<PREC>::C omega_f,
-                                              typename Store<PREC>::C force_pre, int k)
+// Collision of the opposite pair (I, O) of D2Q9. With c = c_I, f^eq (Eqs.
+// feq_i, Siu) and the forcing of Eq. GGi split into a part even in c and a
+// part odd in c:
+//   omega f^eq_i + F_i = w (S +- A),
+//   S = omega (3 p + rho (9/2 (c.u)^2 - 3/2 u.u)) + 3 (1 - 1/(2 tau)) (c.u)(c.grad rho),
+//   A = 3 omega rho (c.u) + 3 (1 - 1/(2 tau)) (c.F),
+// so f*_I = (1 - omega) f_I + w (S + A) and f*_O = (1 - omega) f_O + w (S - A).
+// K holds the per-node constants base = omega (3 p - 3/2 rho u.u),
+// c45 = 9/2 omega rho, c3 = 3 omega rho, pre3 = 3 (1 - 1/(2 tau)), omf = 1 - omega.
+template <typename C>
+struct PairK { C base, c45, c3, pre3, omf; };
+
+template <int PREC, int I, int O>
+__device__ __forceinline__ void collide_f_pair(const StepArgs<PREC>& a, typename Store<PREC>::C fI,
+                                               typename Store<PREC>::C fO, const PairK<typename Store<PREC>::C>& K,
+                                               typename Store<PREC>::C ux, typename Store<PREC>::C uy,
+                                               typename Store<PREC>::C Fx, typename Store<PREC>::C Fy,
+                                               typename Store<PREC>::C drx, typename Store<PREC>::C dry, int k)
 {
     using T = Store<PREC>;
     using C = typename T::C;
+    static_assert(cx(O) == -cx(I) && cy(O) == -cy(I), "opposite pair");
     const C w = wgt<C>(I);
     const C cu = C(cx(I)) * ux + C(cy(I)) * uy;
     const C cF = C(cx(I)) * Fx + C(cy(I)) * Fy;
     const C cdr = C(cx(I)) * drx + C(cy(I)) * dry;
-    const C feq = w * (C(3) * p + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
-    const C Fi = force_pre * w * C(3) * (cF + cu * cdr);
-    a.out.f[I * a.plane + k] = T::template st<I>(f_i + omega_f * (feq - f_i) + Fi);
+    const C S = w * (K.base + cu * (K.c45 * cu + K.pre3 * cdr));
+    const C A = w * (K.c3 * cu + K.pre3 * cF);
+    a.out.f[I * a.plane + k] = T::template st<I>(K.omf * fI + (S + A));
+    a.out.f[O * a.plane + k] = T::template st<O>(K.omf * fO + (S - A));
 }
 
 // g_i (i != 0) collision and store; returns the storage rounding residual
@@ -327,14 +339,14 @@ __device__ __forceinline__ void collide_f_dir(const StepArgs<PREC>& a, typename 
 template <int PREC, int I>
 __device__ __forceinline__ typename Store<PREC>::C collide_g_dir(const StepArgs<PREC>& a,
                                                                  typename Store<PREC>::C g_i,
-                                                                 typename Store<PREC>::C am,
-                                                                 typename Store<PREC>::C src, int k)
+                                                                 typename Store<PREC>::C omg,
+                                                                 typename Store<PREC>::C gadd, int k)
 {
     using T = Store<PREC>;
     using C = typename T::C;
-    const C w = wgt<C>(I);
-    const C h = (I <= 4) ? C(-0.5) : C(1);
-    const C v = g_i + a.omega_g * (w * am - g_i) + w * h * src;
+    // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu + h_i src): gadd is the
+    // second term, the same for the four axes and for the four diagonals
+    const C v = omg * g_i + gadd;
     const typename T::S s = T::template st<I>(v);
     a.out.g[I * a.plane + k] = s;
     if (T::kAbsorb) return v - T::template ld<I>(s);
@@ -423,27 +435,33 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
         const C feq0 = C(-5) / C(3) * p - rho * (wgt<C>(0) * C(1.5)) * uu;
         a.out.f[k] = T::template st<0>(f[0] + omega_f * (feq0 - f[0]));
     }
-    collide_f_dir<PREC, 1>(a, f[1], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
-    collide_f_dir<PREC, 2>(a, f[2], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
-    collide_f_dir<PREC, 3>(a, f[3], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
-    collide_f_dir<PREC, 4>(a, f[4], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
-    collide_f_dir<PREC, 5>(a, f[5], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
-    collide_f_dir<PREC, 6>(a, f[6], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
-    collide_f_dir<PREC, 7>(a, f[7], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
-    collide_f_dir<PREC, 8>(a, f[8], p, rho, ux, uy, uu, Fx, Fy, drx, dry, omega_f, force_pre, k);
+    {
+        PairK<C> K;
+        K.base = omega_f * (C(3) * p - C(1.5) * rho * uu);
+        K.c45 = omega_f * C(4.5) * rho;
+        K.c3 = omega_f * C(3) * rho;
+        K.pre3 = C(3) * force_pre;
+        K.omf = C(1) - omega_f;
+        collide_f_pair<PREC, 1, 3>(a, f[1], f[3], K, ux, uy, Fx, Fy, drx, dry, k);
+        collide_f_pair<PREC, 2, 4>(a, f[2], f[4], K, ux, uy, Fx, Fy, drx, dry, k);
+        collide_f_pair<PREC, 5, 7>(a, f[5], f[7], K, ux, uy, Fx, Fy, drx, dry, k);
+        collide_f_pair<PREC, 6, 8>(a, f[6], f[8], K, ux, uy, Fx, Fy, drx, dry, k);
+    }
 
     // ---- g collision: g* = g + (g^eq - g)/tau_g + (3/2) G_i(t) - (1/2) G_i(t-1) ----
     const C s_now = ux * gpx + uy * gpy;
     const C src = a.dgdt ? s_now : C(1.5) * s_now - C(0.5) * (C)a.sprev[k];
     const C am = a.alpha * mu;
-    C resid = collide_g_dir<PREC, 1>(a, g[1], am, src, k);
-    resid += collide_g_dir<PREC, 2>(a, g[2], am, src, k);
-    resid += collide_g_dir<PREC, 3>(a, g[3], am, src, k);
-    resid += collide_g_dir<PREC, 4>(a, g[4], am, src, k);
-    resid += collide_g_dir<PREC, 5>(a, g[5], am, src, k);
-    resid += collide_g_dir<PREC, 6>(a, g[6], am, src, k);
-    resid += collide_g_dir<PREC, 7>(a, g[7], am, src, k);
-    resid += collide_g_dir<PREC, 8>(a, g[8], am, src, k);
+    const C omg = C(1) - a.omega_g, oam = a.omega_g * am;
+    const C g_ax = wgt<C>(1) * (oam - C(0.5) * src), g_dg = wgt<C>(5) * (oam + src);   // h = -1/2, 1
+    C resid = collide_g_dir<PREC, 1>(a, g[1], omg, g_ax, k);
+    resid += collide_g_dir<PREC, 2>(a, g[2], omg, g_ax, k);
+    resid += collide_g_dir<PREC, 3>(a, g[3], omg, g_ax, k);
+    resid += collide_g_dir<PREC, 4>(a, g[4], omg, g_ax, k);
+    resid += collide_g_dir<PREC, 5>(a, g[5], omg, g_dg, k);
+    resid += collide_g_dir<PREC, 6>(a, g[6], omg, g_dg, k);
+    resid += collide_g_dir<PREC, 7>(a, g[7], omg, g_dg, k);
+    resid += collide_g_dir<PREC, 8>(a, g[8], omg, g_dg, k);
     {
         // g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu (Eq. H_i); in the
         // 16-bit formats g_0 also takes back what rounding removed from g_1..g_8
