@@ -36,6 +36,35 @@ enum : uint8_t {
 };
 __host__ __device__ inline bool zeta_of(uint8_t c) { return c != CLS_OUT && (c & CLS_MASK) <= CLS_BOUNDARY; }
 
+// Multiply-add with one rounding. The library is compiled without implicit
+// contraction (-fmad=false): every fused multiply-add in it is written as one
+// of these, so a formula rounds the same way in every kernel that inlines it
+// (single-lattice, batched, fused and three-pass steps agree bit for bit).
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+
+// c . v for a lattice velocity c with components in {-1, 0, 1}, without
+// multiplications (x * 0 cannot be folded under IEEE rules).
+template <int X, int Y, typename C>
+__device__ __forceinline__ C cdot(C vx, C vy)
+{
+    static_assert(X >= -1 && X <= 1 && Y >= -1 && Y <= 1 && (X || Y), "lattice velocity");
+    if constexpr (X == 0) return Y > 0 ? vy : -vy;
+    else if constexpr (Y == 0) return X > 0 ? vx : -vx;
+    else if constexpr (X > 0) return Y > 0 ? vx + vy : vx - vy;
+    else return Y > 0 ? vy - vx : -(vx + vy);
+}
+template <int X, int Y, int Z, typename C>
+__device__ __forceinline__ C cdot(C vx, C vy, C vz)
+{
+    static_assert(X >= -1 && X <= 1 && Y >= -1 && Y <= 1 && Z >= -1 && Z <= 1 && (X || Y || Z), "lattice velocity");
+    static_assert(!(X && Y && Z), "D3Q19 velocity");
+    if constexpr (Z == 0) return cdot<X, Y>(vx, vy);
+    else if constexpr (X == 0 && Y == 0) return Z > 0 ? vz : -vz;
+    else if constexpr (X == 0) return cdot<Y, Z>(vy, vz);
+    else return cdot<X, Z>(vx, vz);
+}
+
 // Tile of the fused step: TX x TY nodes per CTA, one node per thread.
 constexpr int TX = 32;
 constexpr int TY = 8;

@@ -25,6 +25,13 @@
 // no O(1) term.
 #include "storage.cuh"
 
+#ifndef PFLBM_PREFETCH_F
+#define PFLBM_PREFETCH_F 0   // fluid tiles: pull f before the phi-tile barrier
+#endif
+#ifndef PFLBM_STEP_MINB
+#define PFLBM_STEP_MINB 6    // resident 256-thread CTAs per SM asked of k_step (FP32, 16-bit)
+#endif
+
 namespace pfk {
 namespace {
 
@@ -136,7 +143,8 @@ template <int PREC>
 __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
                                                     typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0,
                                                     typename Store<PREC>::C gown[9],
-                                                    typename Store<PREC>::G0T& raw0)
+                                                    typename Store<PREC>::G0T& raw0,
+                                                    typename Store<PREC>::C fown[9])
 {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
@@ -144,6 +152,8 @@ __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
     {
         const int gx = wrap1(x0 + tx, nx), gy = y0 + ty;
         pull_g<PREC, false>(gown, raw0, a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
+        // the f pulls do not depend on phi: issue them before the barrier
+        if (PFLBM_PREFETCH_F) pull_f<PREC, false>(fown, a.in.f, nullptr, 0, 0, gx, gy, nx, pitch, plane);
         s_phi[ty + 2][tx + 2] = phi_of(gown);
     }
     // ring: top row, bottom row (TX + 2 each), left and right columns (TY each)
@@ -297,9 +307,9 @@ __device__ __forceinline__ void stencils(C (*s_phi)[TX + 4], int py, int px, C& 
     C c = s_phi[py][px];
     C E = s_phi[py][px + 1], W = s_phi[py][px - 1], N = s_phi[py + 1][px], Sx = s_phi[py - 1][px];
     C NE = s_phi[py + 1][px + 1], NW = s_phi[py + 1][px - 1], SW = s_phi[py - 1][px - 1], SE = s_phi[py - 1][px + 1];
-    gx = (E - W) * (C(1) / C(3)) + ((NE + SE) - (NW + SW)) * (C(1) / C(12));
-    gy = (N - Sx) * (C(1) / C(3)) + ((NE + NW) - (SE + SW)) * (C(1) / C(12));
-    lap = ((E + W) + (N + Sx)) * (C(2) / C(3)) + ((NE + NW) + (SE + SW)) * (C(1) / C(6)) - c * (C(10) / C(3));
+    gx = fmadd(E - W, C(1) / C(3), ((NE + SE) - (NW + SW)) * (C(1) / C(12)));
+    gy = fmadd(N - Sx, C(1) / C(3), ((NE + NW) - (SE + SW)) * (C(1) / C(12)));
+    lap = fmadd((E + W) + (N + Sx), C(2) / C(3), fmadd((NE + NW) + (SE + SW), C(1) / C(6), c * (C(-10) / C(3))));
 }
 
 // Collision of the opposite pair (I, O) of D2Q9. With c = c_I, f^eq (Eqs.
@@ -325,13 +335,13 @@ __device__ __forceinline__ void collide_f_pair(const StepArgs<PREC>& a, typename
     using C = typename T::C;
     static_assert(cx(O) == -cx(I) && cy(O) == -cy(I), "opposite pair");
     const C w = wgt<C>(I);
-    const C cu = C(cx(I)) * ux + C(cy(I)) * uy;
-    const C cF = C(cx(I)) * Fx + C(cy(I)) * Fy;
-    const C cdr = C(cx(I)) * drx + C(cy(I)) * dry;
-    const C S = w * (K.base + cu * (K.c45 * cu + K.pre3 * cdr));
-    const C A = w * (K.c3 * cu + K.pre3 * cF);
-    a.out.f[I * a.plane + k] = T::template st<I>(K.omf * fI + (S + A));
-    a.out.f[O * a.plane + k] = T::template st<O>(K.omf * fO + (S - A));
+    const C cu = cdot<cx(I), cy(I)>(ux, uy);
+    const C cF = cdot<cx(I), cy(I)>(Fx, Fy);
+    const C cdr = cdot<cx(I), cy(I)>(drx, dry);
+    const C S = w * fmadd(cu, fmadd(K.c45, cu, K.pre3 * cdr), K.base);
+    const C A = w * fmadd(K.c3, cu, K.pre3 * cF);
+    a.out.f[I * a.plane + k] = T::template st<I>(fmadd(K.omf, fI, S + A));
+    a.out.f[O * a.plane + k] = T::template st<O>(fmadd(K.omf, fO, S - A));
 }
 
 // g_i (i != 0) collision and store; returns the storage rounding residual
@@ -346,10 +356,10 @@ __device__ __forceinline__ typename Store<PREC>::C collide_g_dir(const StepArgs<
     using C = typename T::C;
     // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu + h_i src): gadd is the
     // second term, the same for the four axes and for the four diagonals
-    const C v = omg * g_i + gadd;
+    const C v = fmadd(omg, g_i, gadd);
     const typename T::S s = T::template st<I>(v);
     a.out.g[I * a.plane + k] = s;
-    if (T::kAbsorb) return v - T::template ld<I>(s);
+    if (T::kAbsorb) return v - T::template ld<I>(s);   // ld is a single product
     return C(0);
 }
 
@@ -363,11 +373,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     using T = Store<PREC>;
     using C = typename T::C;
     const int x0 = bx * TX, y0 = by * TY;
-    C g[9];
+    C g[9], f[9];
     typename T::G0T g0raw;
     const bool fluid_tile = a.tiles[by * ntx + bx] != 0;
     if (fluid_tile)
-        tile_prologue_fluid<PREC>(a, s_phi, x0, y0, g, g0raw);
+        tile_prologue_fluid<PREC>(a, s_phi, x0, y0, g, g0raw, f);
     else
         tile_prologue<PREC>(a, s_cls, s_phi, x0, y0, g, g0raw);
 
@@ -391,28 +401,27 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     stencils<C>(s_phi, ty + 2, tx + 2, gpx, gpy, lap);
     const C ph = s_phi[ty + 2][tx + 2];
     const C wet = (code & F_WET) ? a.wet[k] : C(0);
-    const C mu = a.beta4 * ph * (ph - C(1)) * (ph - C(0.5)) - a.kappa * lap - wet * (ph - ph * ph);
+    const C mu = fmadd(-wet, fmadd(-ph, ph, ph), fmadd(-a.kappa, lap, a.beta4 * ph * (ph - C(1)) * (ph - C(0.5))));
 
     // ---- coupling fields (Sec. 2.1.1): F = F_s + F_b, F_s = mu grad(phi), F_b = rho g ----
-    const C rho = a.rho_g + a.drho * ph;
+    const C rho = fmadd(a.drho, ph, a.rho_g);
     const C drx = a.drho * gpx, dry = a.drho * gpy;
-    const C Fx = mu * gpx + rho * a.gx, Fy = mu * gpy + rho * a.gy;
+    const C Fx = fmadd(mu, gpx, rho * a.gx), Fy = fmadd(mu, gpy, rho * a.gy);
 
     // ---- hydrodynamic moments (Sec. 2.1.2) ----
-    C f[9];
     if (code & F_LINK)
         pull_f<PREC, true>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
-    else
+    else if (!(PFLBM_PREFETCH_F && fluid_tile))
         pull_f<PREC, false>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
     const C mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const C my = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
     const C inv_rho = C(1) / rho;
-    const C ux = (mx + C(0.5) * Fx) * inv_rho;
-    const C uy = (my + C(0.5) * Fy) * inv_rho;
-    const C uu = ux * ux + uy * uy;
+    const C ux = fmadd(C(0.5), Fx, mx) * inv_rho;
+    const C uy = fmadd(C(0.5), Fy, my) * inv_rho;
+    const C uu = fmadd(ux, ux, uy * uy);
     const C fsum = sum_moving(f);
     // p = c_s^2/(1 - w_0) [sum_{i!=0} f_i + u.grad(rho)/2 + rho s_0(u)], s_0 = -w_0 (3/2) u^2
-    const C p = C(0.6) * (fsum + C(0.5) * (ux * drx + uy * dry) - rho * (C(2) / C(3)) * uu);
+    const C p = C(0.6) * fmadd(-(rho * (C(2) / C(3))), uu, fmadd(C(0.5), fmadd(ux, drx, uy * dry), fsum));
 
     if (!COLLIDE) {
         size_t o = (size_t)gy * a.nx + gx;
@@ -426,18 +435,18 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     // nu(phi) = phi (nu_l - nu_g) + nu_g (Secs. 2.1.1, 2.1.2)
     C omega_f = a.omega_f, force_pre = a.force_pre;
     if (VV == 1 || (VV == 2 && a.varvisc)) {
-        omega_f = C(1) / (a.tau_g3h + a.dtau3 * ph);
-        force_pre = C(1) - C(0.5) * omega_f;
+        omega_f = C(1) / fmadd(a.dtau3, ph, a.tau_g3h);
+        force_pre = fmadd(C(-0.5), omega_f, C(1));
     }
 
     // ---- f collision: f* = f + (f^eq - f)/tau_f + F_i ----
     {
-        const C feq0 = C(-5) / C(3) * p - rho * (wgt<C>(0) * C(1.5)) * uu;
-        a.out.f[k] = T::template st<0>(f[0] + omega_f * (feq0 - f[0]));
+        const C feq0 = fmadd(-(rho * (wgt<C>(0) * C(1.5))), uu, (C(-5) / C(3)) * p);
+        a.out.f[k] = T::template st<0>(fmadd(omega_f, feq0 - f[0], f[0]));
     }
     {
         PairK<C> K;
-        K.base = omega_f * (C(3) * p - C(1.5) * rho * uu);
+        K.base = omega_f * fmadd(-(C(1.5) * rho), uu, C(3) * p);
         K.c45 = omega_f * C(4.5) * rho;
         K.c3 = omega_f * C(3) * rho;
         K.pre3 = C(3) * force_pre;
@@ -449,11 +458,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     }
 
     // ---- g collision: g* = g + (g^eq - g)/tau_g + (3/2) G_i(t) - (1/2) G_i(t-1) ----
-    const C s_now = ux * gpx + uy * gpy;
-    const C src = a.dgdt ? s_now : C(1.5) * s_now - C(0.5) * (C)a.sprev[k];
+    const C s_now = fmadd(ux, gpx, uy * gpy);
+    const C src = a.dgdt ? s_now : fmadd(C(1.5), s_now, C(-0.5) * (C)a.sprev[k]);
     const C am = a.alpha * mu;
     const C omg = C(1) - a.omega_g, oam = a.omega_g * am;
-    const C g_ax = wgt<C>(1) * (oam - C(0.5) * src), g_dg = wgt<C>(5) * (oam + src);   // h = -1/2, 1
+    const C g_ax = wgt<C>(1) * fmadd(C(-0.5), src, oam), g_dg = wgt<C>(5) * (oam + src);   // h = -1/2, 1
     C resid = collide_g_dir<PREC, 1>(a, g[1], omg, g_ax, k);
     resid += collide_g_dir<PREC, 2>(a, g[2], omg, g_ax, k);
     resid += collide_g_dir<PREC, 3>(a, g[3], omg, g_ax, k);
@@ -465,14 +474,14 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     {
         // g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu (Eq. H_i); in the
         // 16-bit formats g_0 also takes back what rounding removed from g_1..g_8
-        const C d0 = a.omega_g * (sum_moving(g) - (C(1) - wgt<C>(0)) * am) + wgt<C>(0) * C(-2) * src;
+        const C d0 = fmadd(a.omega_g, fmadd(-(C(1) - wgt<C>(0)), am, sum_moving(g)), (wgt<C>(0) * C(-2)) * src);
         a.out.g0[k] = T::g0_add(g0raw, T::kAbsorb ? d0 + resid : d0, a.status);
     }
     if (!a.dgdt) a.sprev[k] = s_now;
 }
 
 template <int PREC, bool COLLIDE, int VV>
-__global__ void __launch_bounds__(TX * TY) k_step(StepArgs<PREC> a)
+__global__ void __launch_bounds__(TX * TY, PREC == PFLBM_FP64 ? 1 : PFLBM_STEP_MINB) k_step(StepArgs<PREC> a)
 {
     __shared__ uint8_t s_cls[TY + 6][TX + 6];
     __shared__ typename Store<PREC>::C s_phi[TY + 4][TX + 4];

@@ -182,13 +182,13 @@ __device__ __forceinline__ void collide_pair(const Args3<PREC>& a, typename Stor
     using C = typename Store<PREC>::C;
     constexpr int X = q19x(I), Y = q19y(I), Z = q19z(I);
     const C w = q19w<C>(I);
-    const C cu = C(X) * u[0] + C(Y) * u[1] + C(Z) * u[2];
-    const C cF = C(X) * F[0] + C(Y) * F[1] + C(Z) * F[2];
-    const C cd = C(X) * dr[0] + C(Y) * dr[1] + C(Z) * dr[2];
-    const C S = w * (K.base + cu * (K.c45 * cu + K.pre3 * cd));
-    const C A = w * (K.c3 * cu + K.pre3 * cF);
-    a.f_out[I * a.plane + k] = Store<PREC>::template st<I>(K.omf * fI + (S + A));
-    a.f_out[(I + 1) * a.plane + k] = Store<PREC>::template st<I + 1>(K.omf * fO + (S - A));
+    const C cu = cdot<X, Y, Z>(u[0], u[1], u[2]);
+    const C cF = cdot<X, Y, Z>(F[0], F[1], F[2]);
+    const C cd = cdot<X, Y, Z>(dr[0], dr[1], dr[2]);
+    const C S = w * fmadd(cu, fmadd(K.c45, cu, K.pre3 * cd), K.base);
+    const C A = w * fmadd(K.c3, cu, K.pre3 * cF);
+    a.f_out[I * a.plane + k] = Store<PREC>::template st<I>(fmadd(K.omf, fI, S + A));
+    a.f_out[(I + 1) * a.plane + k] = Store<PREC>::template st<I + 1>(fmadd(K.omf, fO, S - A));
 }
 
 // (3) the fused collide-and-store (COLLIDE) or the macroscopic read-back of
@@ -213,14 +213,14 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
         const C vp = phi_at(i), vm = phi_at(i + 1);
         const C w3 = C(3) * q19w<C>(i);
         const C d = w3 * (vp - vm);
-        if (q19x(i)) gp[0] += C(q19x(i)) * d;
-        if (q19y(i)) gp[1] += C(q19y(i)) * d;
-        if (q19z(i)) gp[2] += C(q19z(i)) * d;
-        lap += C(2) * w3 * ((vp + vm) - C(2) * ph);
+        if (q19x(i)) gp[0] = q19x(i) > 0 ? gp[0] + d : gp[0] - d;
+        if (q19y(i)) gp[1] = q19y(i) > 0 ? gp[1] + d : gp[1] - d;
+        if (q19z(i)) gp[2] = q19z(i) > 0 ? gp[2] + d : gp[2] - d;
+        lap = fmadd(C(2) * w3, fmadd(C(-2), ph, vp + vm), lap);
     }
     const C wet = (code & F_WET) ? a.wet[k] : C(0);
-    const C mu = a.beta4 * ph * (ph - C(1)) * (ph - C(0.5)) - a.kappa * lap - wet * (ph - ph * ph);
-    const C rho = a.rho_g + a.drho * ph;
+    const C mu = fmadd(-wet, fmadd(-ph, ph, ph), fmadd(-a.kappa, lap, a.beta4 * ph * (ph - C(1)) * (ph - C(0.5))));
+    const C rho = fmadd(a.drho, ph, a.rho_g);
     const C dr[3] = {a.drho * gp[0], a.drho * gp[1], a.drho * gp[2]};
     const C F[3] = {mu * gp[0], mu * gp[1], mu * gp[2]};
     // ---- hydrodynamics ----
@@ -248,16 +248,17 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
 #pragma unroll
     for (int i = 1; i < 19; i += 2) {
         const C d = f[i] - f[i + 1];
-        if (q19x(i)) m[0] += C(q19x(i)) * d;
-        if (q19y(i)) m[1] += C(q19y(i)) * d;
-        if (q19z(i)) m[2] += C(q19z(i)) * d;
+        if (q19x(i)) m[0] = q19x(i) > 0 ? m[0] + d : m[0] - d;
+        if (q19y(i)) m[1] = q19y(i) > 0 ? m[1] + d : m[1] - d;
+        if (q19z(i)) m[2] = q19z(i) > 0 ? m[2] + d : m[2] - d;
         fsum += f[i] + f[i + 1];
     }
     const C ir = C(1) / rho;
-    const C u[3] = {(m[0] + C(0.5) * F[0]) * ir, (m[1] + C(0.5) * F[1]) * ir, (m[2] + C(0.5) * F[2]) * ir};
-    const C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const C u[3] = {fmadd(C(0.5), F[0], m[0]) * ir, fmadd(C(0.5), F[1], m[1]) * ir, fmadd(C(0.5), F[2], m[2]) * ir};
+    const C uu = fmadd(u[2], u[2], fmadd(u[1], u[1], u[0] * u[0]));
     // p = c_s^2/(1 - w_0) [...] = (1/2) [sum_{i!=0} f_i + u.grad(rho)/2 + rho s_0], s_0 = -uu/2
-    const C p = C(0.5) * (fsum + C(0.5) * (u[0] * dr[0] + u[1] * dr[1] + u[2] * dr[2]) - C(0.5) * rho * uu);
+    const C udr = fmadd(u[2], dr[2], fmadd(u[1], dr[1], u[0] * dr[0]));
+    const C p = C(0.5) * fmadd(-(C(0.5) * rho), uu, fmadd(C(0.5), udr, fsum));
     if (!COLLIDE) {
         const size_t o = ((size_t)z * a.ny + y) * a.nx + x;
         if (a.o_phi) a.o_phi[o] = (double)ph;
@@ -266,9 +267,9 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
         return;
     }
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
-    a.f_out[k] = T::template st<0>(f[0] + a.omega_f * ((C(-2) * p - C(0.5) * rho * uu) - f[0]));
+    a.f_out[k] = T::template st<0>(fmadd(a.omega_f, fmadd(-(C(0.5) * rho), uu, C(-2) * p) - f[0], f[0]));
     PairK<C> K;
-    K.base = a.omega_f * (C(3) * p - C(1.5) * rho * uu);
+    K.base = a.omega_f * fmadd(-(C(1.5) * rho), uu, C(3) * p);
     K.c45 = a.omega_f * C(4.5) * rho;
     K.c3 = a.omega_f * C(3) * rho;
     K.pre3 = C(3) * a.force_pre;
@@ -286,14 +287,14 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     C g[7];
     typename T::G0T raw0;
     load_g(g, raw0);
-    const C s_now = u[0] * gp[0] + u[1] * gp[1] + u[2] * gp[2];
-    const C src = C(1.5) * s_now - C(0.5) * a.sprev[k];
+    const C s_now = fmadd(u[2], gp[2], fmadd(u[1], gp[1], u[0] * gp[0]));
+    const C src = fmadd(C(1.5), s_now, C(-0.5) * a.sprev[k]);
     const C am = a.alpha * mu;
     // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu - src / 2), the same for i = 1..6
-    const C gm = q7w<C>(1) * (a.omega_g * am - C(0.5) * src), omg = C(1) - a.omega_g;
+    const C gm = q7w<C>(1) * fmadd(C(-0.5), src, a.omega_g * am), omg = C(1) - a.omega_g;
 #pragma unroll
-    for (int i = 1; i < 7; ++i) a.g_out[i * a.plane + k] = T::template st<1>(omg * g[i] + gm);
-    const C d0 = a.omega_g * (sum6(g) - C(0.75) * am) + q7w<C>(0) * C(-2.5) * src;
+    for (int i = 1; i < 7; ++i) a.g_out[i * a.plane + k] = T::template st<1>(fmadd(omg, g[i], gm));
+    const C d0 = fmadd(a.omega_g, fmadd(C(-0.75), am, sum6(g)), (q7w<C>(0) * C(-2.5)) * src);
     a.g0_out[k] = T::g0_add(raw0, d0, a.status);
     a.sprev[k] = s_now;
 }

@@ -82,25 +82,18 @@ def test_parity_3d(name, precision, path):
     assert np.max(np.abs(r["u"])) > 1e-6
 
 
-ULP_BOUND = {"fp64": dict(phi=2e-15, u=1e-16, p=1e-16), "fp32": dict(phi=1e-6, u=1e-8, p=1e-8)}
-
-
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name,zc", [("flat3d", 1), ("flat3d", 0), ("flat3d", 100), ("sphere3d", 3),
                                      ("tiny3d", 2)])
 def test_fused_equals_three_pass(name, zc, precision):
-    # The two step paths inline the same arithmetic, so a difference can only
-    # come from the compiler pairing multiply-adds differently: phi is equal
-    # after one step and within a few ulps after 40, whatever the number of
-    # planes each CTA of the fused path marches.
-    a = gpu_run(name, precision, "three_pass", steps=1)
-    b = gpu_run(name, precision, "fused", zc=zc, steps=1)
-    assert np.array_equal(a["phi"], b["phi"])
+    # The two step paths inline the same arithmetic, with every multiply-add
+    # explicit: they agree bit for bit, whatever the number of planes each
+    # CTA of the fused path marches.
     a = gpu_run(name, precision, "three_pass", steps=40)
     b = gpu_run(name, precision, "fused", zc=zc, steps=40)
-    for key, bound in ULP_BOUND[precision].items():
-        assert np.max(np.abs(a[key] - b[key])) <= bound, key
-    assert abs(a["mass"] - b["mass"]) <= 1e3 * bound * abs(a["mass"]) * 1e-3 + ULP_BOUND[precision]["phi"] * a["phi"].size
+    for key in ("phi", "u", "p"):
+        assert np.array_equal(a[key], b[key]), key
+    assert a["mass"] == b["mass"]
 
 
 def test_rejects_bad_mask_3d():
