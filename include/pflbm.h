@@ -274,7 +274,7 @@ typedef struct {
     int precision;               /* PFLBM_FP64 or PFLBM_FP32 */
     int device;                  /* CUDA device; < 0: current */
     void* stream;                /* cudaStream_t; NULL: a stream of its own */
-    int step_path;               /* enum pflbm3d_step_path; the results agree to a few ulps */
+    int step_path;               /* enum pflbm3d_step_path; the results are identical */
     int fused_zc;                /* planes per CTA of the fused step; <= 0: chosen by the library */
 } pflbm3d_params_t;
 
