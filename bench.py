@@ -37,6 +37,24 @@ BYTES_PER_LU = {"fp64": 2 * 9 * 2 * 8 + 2 * 8 + 1, "fp32": 2 * 9 * 2 * 4 + 2 * 4
                 "bf16": 2 * (17 * 2 + 4) + 2 * 4 + 1, "fp16": 2 * (17 * 2 + 4) + 2 * 4 + 1}
 
 
+def max_over_ranks(x, device, world):
+    """The largest value of x over all ranks (x itself when world == 1).
+    Every rank calls it; the barrier makes the slowest rank decide."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, nodes, steps, seconds):
+    """Lattice updates of all replicas (world x nodes x steps) per second, in millions."""
+    return world * nodes * steps / seconds / 1e6
+
+
 def step_source_sha256(files=("step.cu", "storage.cuh", "pflbm_internal.cuh")):
     import hashlib
     h = hashlib.sha256()
@@ -408,13 +426,9 @@ def run_3d(args, torch, rank, world, local):
         ms = e0.elapsed_time(e1)
         s.check()
         s.close()
-    ms_t = torch.tensor([ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.barrier()
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, f"cuda:{local}", world)
     ms_per_step = ms / args.steps
-    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, N, args.steps, ms * 1e-3)
     peak, peak_kind = load_peaks()
     bpl = BYTES_PER_LU_3D[prec]
     achieved = bpl * N / (ms_per_step * 1e-3) / 1e9
@@ -442,10 +456,7 @@ def run_3d(args, torch, rank, world, local):
         s2.close()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
+    e2e_s = max_over_ranks(e2e_s, f"cuda:{local}", world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc = oracle_sample_3d()
@@ -466,7 +477,7 @@ def run_3d(args, torch, rank, world, local):
                          "kernel": "whole step (k3_fused, 1 launch)" if args.path3d == "fused"
                          else "whole step (k3_phi, k3_ghost, k3_step: 3 launches)"},
             "hbm_roofline_mlups": peak * 1e9 / bpl / 1e6,
-            "e2e": {"value": world * N * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+            "e2e": {"value": whole_job_mlups(world, N, e2e_steps, e2e_s), "unit": "MLUPS",
                     "h2d_bytes_per_step": case.solid.nbytes / e2e_steps,
                     "d2h_bytes_per_step": (phi.nbytes + u.nbytes + p.nbytes) / e2e_steps,
                     "steps_per_solve": e2e_steps,
@@ -548,13 +559,9 @@ def main():
         clocks = sampler.stop()
         ms = e0.elapsed_time(e1)
         s.check()
-    ms_t = torch.tensor([ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.barrier()
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, f"cuda:{local}", world)
     ms_per_step = ms / args.steps
-    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, N, args.steps, ms * 1e-3)
 
     peak, peak_kind = load_peaks()
     bpl = BYTES_PER_LU[args.precision]
@@ -588,10 +595,7 @@ def main():
         s2.close()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
+    e2e_s = max_over_ranks(e2e_s, f"cuda:{local}", world)
     h2d = case.solid.nbytes + (case.theta_field.nbytes if case.theta_field is not None else 0)
     d2h = phi.nbytes + u.nbytes + p.nbytes
 
@@ -616,7 +620,7 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "bytes_per_lu": bpl},
             "hbm_roofline_mlups": peak * 1e9 / bpl / 1e6,
-            "e2e": {"value": world * N * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+            "e2e": {"value": whole_job_mlups(world, N, e2e_steps, e2e_s), "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
                     "steps_per_solve": e2e_steps,
                     "includes": "create (mask upload, geometry), droplet init, steps, get"},
