@@ -287,6 +287,10 @@ def _lib3d():
         L.or3_mass.restype = ctypes.c_double
         L.or3_mass.argtypes = [vp]
         L.or3_budget.argtypes = [vp, _dp]
+        L.or3_set_dgdt.restype = None
+        L.or3_set_dgdt.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or3_contact_angle.restype = ctypes.c_int
+        L.or3_contact_angle.argtypes = [_dp, _u8p] + [ctypes.c_int] * 3 + [ctypes.POINTER(Wall3), _dp, _dp]
         L.or3_contact_angle_flat.restype = ctypes.c_int
         L.or3_contact_angle_flat.argtypes = [_dp, _u8p] + [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_dp, _dp]
         _3d_ready = True
@@ -344,6 +348,40 @@ def stencil3(v):
     return g, lap.value
 
 
+class Wall3(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("p", ctypes.c_double * 3), ("n", ctypes.c_double * 3),
+                ("r", ctypes.c_double), ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
+                ("y_lo", ctypes.c_double), ("y_hi", ctypes.c_double), ("exclude", ctypes.c_double)]
+
+
+def wall3(wall: dict) -> Wall3:
+    w = Wall3()
+    w.type = int(wall.get("type", 0))
+    for i, v in enumerate(wall.get("p", (0.0, 0.0, 0.0))):
+        w.p[i] = float(v)
+    for i, v in enumerate(wall.get("n", (0.0, 0.0, 1.0))):
+        w.n[i] = float(v)
+    w.r = float(wall.get("r", 0.0))
+    w.x_lo, w.x_hi = float(wall.get("x_lo", -1e300)), float(wall.get("x_hi", 1e300))
+    w.y_lo, w.y_hi = float(wall.get("y_lo", -1e300)), float(wall.get("y_hi", 1e300))
+    w.exclude = float(wall.get("exclude", 0.0))
+    return w
+
+
+def contact_angle3(phi, cls, wall: dict):
+    """Sphere fit of the phi = 1/2 crossings and the contact angle against a
+    plane or a solid sphere (see or3_contact_angle). Returns (theta_deg,
+    [cx, cy, cz, R], n_points)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    cls = np.ascontiguousarray(cls, dtype=np.uint8)
+    nz, ny, nx = phi.shape
+    th = ctypes.c_double()
+    sph = np.zeros(4)
+    w = wall3(wall)
+    n = _lib3d().or3_contact_angle(_p(phi), _p(cls, _u8p), nx, ny, nz, ctypes.byref(w), ctypes.byref(th), _p(sph))
+    return th.value, sph, n
+
+
 def contact_angle_flat3(phi, cls, zw, exclude):
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     cls = np.ascontiguousarray(cls, dtype=np.uint8)
@@ -392,6 +430,9 @@ class Oracle3D:
 
     def init_phi(self, phi):
         _lib3d().or3_init_phi(self._h, _p(np.ascontiguousarray(phi, dtype=np.float64)))
+
+    def set_dgdt(self, mode):
+        _lib3d().or3_set_dgdt(self._h, int(mode))
 
     def step(self, n=1):
         _lib3d().or3_step(self._h, int(n))

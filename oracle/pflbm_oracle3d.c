@@ -142,6 +142,7 @@ struct or3_solver {
     double *f, *g, *fpost, *gpost, *s_prev;
     double *phi, *mu, *gp, *ux, *p;   /* gp: [N][3], ux: [N][3] */
     int history, replace_phi;
+    int dgdt;                         /* 1: the (1/2) dG/dt term omitted */
     double budget[4];
 };
 
@@ -429,7 +430,7 @@ static void step3(or3_solver* s)
             s->fpost[(long)i * N + k] = fi - (fi - feq[i]) / s->tau_f + Fi[i];
         }
         double s_now = u[0] * gp[0] + u[1] * gp[1] + u[2] * gp[2];
-        double s_old = s->history ? s->s_prev[k] : s_now;
+        double s_old = (s->history && !s->dgdt) ? s->s_prev[k] : s_now;
         double geq[Q7], Gn[Q7], Go[Q7];
         or3_geq(ph, mu, s->alpha, geq);
         or3_source(s_now, Gn);
@@ -490,6 +491,8 @@ static void step3(or3_solver* s)
     s->history = 1;
     s->replace_phi = 1;
 }
+
+void or3_set_dgdt(or3_solver* s, int mode) { s->dgdt = mode ? 1 : 0; }
 
 void or3_step(or3_solver* s, long n)
 {
@@ -553,8 +556,16 @@ static int solve4(double A[4][4], double b[4], double x[4])
     return 0;
 }
 
-int or3_contact_angle_flat(const double* phi, const uint8_t* cls, int nx, int ny, int nz, double zw,
-                           double exclude, double* theta_deg, double sphere[4])
+static double wall_distance3(const or3_wall_t* w, const double q[3])
+{
+    if (w->type == 0)
+        return (q[0] - w->p[0]) * w->n[0] + (q[1] - w->p[1]) * w->n[1] + (q[2] - w->p[2]) * w->n[2];
+    double d[3] = {q[0] - w->p[0], q[1] - w->p[1], q[2] - w->p[2]};
+    return sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - w->r;
+}
+
+int or3_contact_angle(const double* phi, const uint8_t* cls, int nx, int ny, int nz, const or3_wall_t* wall,
+                      double* theta_deg, double sphere[4])
 {
     long N = (long)nx * ny * nz, cap = 3 * N;
     double* P = (double*)calloc((size_t)(3 * cap), sizeof(double));
@@ -573,7 +584,8 @@ int or3_contact_angle_flat(const double* phi, const uint8_t* cls, int nx, int ny
                     if ((a >= 0.5) == (b >= 0.5)) continue;
                     double t = (0.5 - a) / (b - a);
                     double q[3] = {x + (d == 0 ? t : 0.0), y + (d == 1 ? t : 0.0), z + (d == 2 ? t : 0.0)};
-                    if (q[2] - zw <= exclude) continue;
+                    if (q[0] < wall->x_lo || q[0] >= wall->x_hi || q[1] < wall->y_lo || q[1] >= wall->y_hi) continue;
+                    if (wall_distance3(wall, q) <= wall->exclude) continue;
                     P[3 * n] = q[0];
                     P[3 * n + 1] = q[1];
                     P[3 * n + 2] = q[2];
@@ -624,9 +636,30 @@ int or3_contact_angle_flat(const double* phi, const uint8_t* cls, int nx, int ny
     }
     for (int d = 0; d < 3; ++d) sphere[d] = c[d] + mc[d];
     sphere[3] = R;
-    double ct = -(sphere[2] - zw) / R;
+    double ct;
+    if (wall->type == 0) {
+        ct = -((sphere[0] - wall->p[0]) * wall->n[0] + (sphere[1] - wall->p[1]) * wall->n[1] +
+               (sphere[2] - wall->p[2]) * wall->n[2]) / R;
+    } else {
+        double d[3] = {sphere[0] - wall->p[0], sphere[1] - wall->p[1], sphere[2] - wall->p[2]};
+        ct = (R * R + wall->r * wall->r - (d[0] * d[0] + d[1] * d[1] + d[2] * d[2])) / (2.0 * R * wall->r);
+    }
     ct = ct > 1 ? 1 : (ct < -1 ? -1 : ct);
     *theta_deg = acos(ct) * 180.0 / M_PI;
     free(P);
     return n;
+}
+
+int or3_contact_angle_flat(const double* phi, const uint8_t* cls, int nx, int ny, int nz, double zw,
+                           double exclude, double* theta_deg, double sphere[4])
+{
+    or3_wall_t w;
+    memset(&w, 0, sizeof(w));
+    w.type = 0;
+    w.p[2] = zw;
+    w.n[2] = 1.0;
+    w.x_lo = w.y_lo = -1e300;
+    w.x_hi = w.y_hi = 1e300;
+    w.exclude = exclude;
+    return or3_contact_angle(phi, cls, nx, ny, nz, &w, theta_deg, sphere);
 }

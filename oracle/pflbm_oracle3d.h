@@ -47,15 +47,34 @@ void or3_params(const or3_solver* s, double out[4]);  /* beta, kappa, tau_g, alp
 void or3_geometry(const or3_solver* s, uint8_t* cls, double* av);
 void or3_init_droplet(or3_solver* s, double x0, double y0, double z0, double R);
 void or3_init_phi(or3_solver* s, const double* phi);
+/* The (1/2) dG_i/dt term of the phase equation, as in 2D: 0 = backward
+ * difference (1/2)[G_i(t) - G_i(t-1)] (default), 1 = omitted. */
+void or3_set_dgdt(or3_solver* s, int mode);
 void or3_step(or3_solver* s, long n);
 /* phi [N], u [N][3], p [N]; any may be NULL */
 void or3_get(or3_solver* s, double* phi, double* u, double* p);
 double or3_mass(const or3_solver* s);
 void or3_budget(const or3_solver* s, double out[4]);
 
-/* Sphere fit of the phi = 1/2 crossings between fluid neighbours farther
- * than `exclude` above the flat wall z = zw (normal +z), and the contact
- * angle cos(theta) = -(z_c - zw)/R. Returns the number of points. */
+/* Wall for the contact-angle fit. type 0: the plane through p with unit
+ * normal n pointing into the fluid; type 1: a solid sphere of centre p and
+ * radius r. Only crossings with x_lo <= x < x_hi, y_lo <= y < y_hi and farther
+ * than `exclude` from the wall are fitted. */
+typedef struct {
+    int type;
+    double p[3], n[3], r;
+    double x_lo, x_hi, y_lo, y_hi;
+    double exclude;
+} or3_wall_t;
+
+/* Sphere fit (algebraic start, Gauss-Newton on the geometric distance) of the
+ * phi = 1/2 crossings between fluid neighbours, and the contact angle: plane
+ * cos(theta) = -n.(c - p)/R; sphere cos(theta) = (R^2 + r^2 - D^2)/(2 R r),
+ * D = |c - p| (the angle between the two spherical surfaces, measured through
+ * the liquid). Returns the number of points; theta is NaN below 4. */
+int or3_contact_angle(const double* phi, const uint8_t* cls, int nx, int ny, int nz, const or3_wall_t* wall,
+                      double* theta_deg, double sphere[4]);
+/* The flat wall z = zw with normal +z. */
 int or3_contact_angle_flat(const double* phi, const uint8_t* cls, int nx, int ny, int nz, double zw,
                            double exclude, double* theta_deg, double sphere[4]);
 

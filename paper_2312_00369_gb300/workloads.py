@@ -230,7 +230,7 @@ class Case3D:
     name: str
     solid: np.ndarray                      # uint8 [nz, ny, nx]
     droplets: list                         # [(x0, y0, z0, R), ...]
-    zw: float                              # effective flat wall (sphere fit)
+    zw: float                              # effective bottom wall plane z = zw
     theta_deg: float = 90.0
     sigma: float = 0.01
     W: float = 4.0
@@ -240,6 +240,9 @@ class Case3D:
     rho_g: float = 0.1
     steps: int = 1000
     meta: dict = field(default_factory=dict)
+    # effective wall for the sphere fit: type 0 plane through p with unit
+    # normal n into the fluid, type 1 solid sphere of centre p, radius r
+    wall: dict = field(default_factory=dict)
 
     @property
     def shape(self):
@@ -264,7 +267,32 @@ def droplet_on_flat_wall_3d(nx=64, ny=64, nz=40, R=16.0, theta=60.0, steps=5000,
     s, zw = box3d(nx, ny, nz)
     kw = dict(sigma=0.01, W=4.0, M=0.1, tau_f=0.8, rho_l=1.0, rho_g=0.1)
     kw.update(phys)
-    return Case3D("flat3d", s, [(nx / 2.0, ny / 2.0, zw, R)], zw, theta_deg=theta, steps=steps, **kw)
+    return Case3D("flat3d", s, [(nx / 2.0, ny / 2.0, zw, R)], zw, theta_deg=theta, steps=steps,
+                  wall=dict(type=0, p=(0.0, 0.0, zw), n=(0.0, 0.0, 1.0)), **kw)
+
+
+def inclined3d(nx: int, ny: int, nz: int, gamma_deg: float, z0: float = 2.0):
+    """Solid below the plane z = tan(gamma) x + z0 (a staircase in x, uniform
+    in y) plus the frame planes. Returns (solid, wall): the effective wall is
+    the plane moved one lattice spacing into the solid along its normal."""
+    t = math.tan(math.radians(gamma_deg))
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx]
+    s, _ = box3d(nx, ny, nz)
+    s |= (z < t * x + z0).astype(np.uint8)
+    c, sn = math.cos(math.radians(gamma_deg)), math.sin(math.radians(gamma_deg))
+    n = (-sn, 0.0, c)
+    wall = dict(type=0, p=(-n[0], 0.0, z0 - n[2]), n=n)
+    return s, wall
+
+
+def droplet_on_incline_3d(nx=40, ny=20, nz=40, gamma=30.0, R=7.0, theta=90.0, steps=1000, **phys) -> Case3D:
+    """Droplet centred on the staircase plane z = tan(gamma) x + 2 at x = nx/2."""
+    s, wall = inclined3d(nx, ny, nz, gamma)
+    x0 = nx / 2.0
+    kw = dict(sigma=0.01, W=4.0, M=0.1, tau_f=0.8, rho_l=1.0, rho_g=0.1)
+    kw.update(phys)
+    return Case3D("incline3d", s, [(x0, ny / 2.0, math.tan(math.radians(gamma)) * x0 + 2.0, R)], 1.5,
+                  theta_deg=theta, steps=steps, wall=wall, meta=dict(gamma=gamma), **kw)
 
 
 def droplet_on_sphere_3d(n=32, Rs=6.0, R=7.0, theta=90.0, steps=1000, **phys) -> Case3D:
@@ -277,7 +305,7 @@ def droplet_on_sphere_3d(n=32, Rs=6.0, R=7.0, theta=90.0, steps=1000, **phys) ->
     kw = dict(sigma=0.01, W=4.0, M=0.1, tau_f=0.8, rho_l=1.0, rho_g=0.1)
     kw.update(phys)
     return Case3D("sphere3d", s, [(c, c, c + Rs, R)], zw, theta_deg=theta, steps=steps,
-                  meta=dict(Rs=Rs), **kw)
+                  meta=dict(Rs=Rs), wall=dict(type=1, p=(c, c, c), r=Rs - 1.0), **kw)
 
 
 def many_droplets_3d(nx=512, ny=512, nz=128, n_drops=64, seed=2312, r_lo=12.0, r_hi=24.0,
@@ -288,4 +316,5 @@ def many_droplets_3d(nx=512, ny=512, nz=128, n_drops=64, seed=2312, r_lo=12.0, r
     s, zw = box3d(nx, ny, nz)
     d = [(float(rng.uniform(0, nx)), float(rng.uniform(0, ny)), zw, float(rng.uniform(r_lo, r_hi)))
          for _ in range(n_drops)]
-    return Case3D("many_flat3d", s, d, zw, theta_deg=theta, steps=steps, meta=dict(seed=seed))
+    return Case3D("many_flat3d", s, d, zw, theta_deg=theta, steps=steps, meta=dict(seed=seed),
+                  wall=dict(type=0, p=(0.0, 0.0, zw), n=(0.0, 0.0, 1.0)))

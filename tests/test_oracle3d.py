@@ -141,3 +141,52 @@ def test_laplace_law_3d():
     r = np.sqrt((x - 12) ** 2 + (y - 12) ** 2 + (z - 12) ** 2)
     dp = p[r < R - 3].mean() - p[r > R + 4].mean()
     assert abs(dp / (2 * sigma / Re) - 1) < 0.12
+
+
+def _cap_field(shape, c, R, W=4.0):
+    z, y, x = np.mgrid[0:shape[0], 0:shape[1], 0:shape[2]]
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    return 0.5 + 0.5 * np.tanh(2 * (R - r) / W)
+
+
+@pytest.mark.parametrize("theta", [40.0, 90.0, 130.0])
+def test_contact_angle_fit_exact_caps(theta):
+    # tanh spheres placed where a cap of angle theta meets (a) a plane tilted
+    # by 20 deg and (b) a solid sphere: the fit returns theta (closed-form
+    # geometry: centre at -R cos(theta) n from the plane; at distance
+    # sqrt(R^2 + r^2 - 2 R r cos(theta)) from the sphere's centre)
+    shape, R = (48, 64, 64), 14.0
+    cls = np.zeros(shape, np.uint8)
+    n = np.array([-math.sin(math.radians(20)), 0.0, math.cos(math.radians(20))])
+    p0 = np.array([32.0, 32.0, 16.0])
+    c = p0 - R * math.cos(math.radians(theta)) * n
+    th, sph, npts = oracle.contact_angle3(_cap_field(shape, c, R), cls, dict(type=0, p=p0, n=n, exclude=1.0))
+    assert npts > 200 and abs(th - theta) < 0.1 and abs(sph[3] - R) < 0.02
+    rs, cs = 10.0, np.array([32.0, 32.0, 14.0])
+    D = math.sqrt(R * R + rs * rs - 2 * R * rs * math.cos(math.radians(theta)))
+    c2 = cs + np.array([0.0, 0.0, D])
+    th, sph, npts = oracle.contact_angle3(_cap_field(shape, c2, R), cls, dict(type=1, p=cs, r=rs, exclude=1.0))
+    assert npts > 1000 and abs(th - theta) < 0.1
+    # the flat-wall form is the plane form with n = +z
+    field = _cap_field(shape, (30.0, 31.0, 10.0 - R * math.cos(math.radians(theta))), R)
+    th1, _, n1 = oracle.contact_angle_flat3(field, cls, 10.0, 1.0)
+    th2, _, n2 = oracle.contact_angle3(field, cls, dict(type=0, p=(0, 0, 10.0), n=(0, 0, 1), exclude=1.0))
+    assert n1 == n2 and th1 == th2 and abs(th1 - theta) < 0.1
+
+
+def test_dgdt_omitted_changes_only_the_source():
+    # with the (1/2) dG/dt term omitted the first step is unchanged (the
+    # backward difference starts from a zero derivative) and later steps differ
+    s = box(12, 10, 12)
+    a = oracle.Oracle3D(s, theta_deg=70.0)
+    b = oracle.Oracle3D(s, theta_deg=70.0)
+    b.set_dgdt(1)
+    for o in (a, b):
+        o.init_droplet(6, 5, 1.5, 5.0)
+        o.step(1)
+    assert np.array_equal(a.get()[0], b.get()[0])
+    a.step(5)
+    b.step(5)
+    assert np.max(np.abs(a.get()[0] - b.get()[0])) > 0
+    m0, src, lost, bb = b.budget()
+    assert abs(b.mass() - (m0 + src - lost + bb)) < 1e-12 * m0
