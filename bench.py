@@ -10,7 +10,7 @@ than L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--precision fp32|fp64] [--workload many_flat|flat|incline|cylinder|
-                     batched|serving|wsweep|many_flat3d]
+                     batched|serving|wsweep|many_flat3d|angles3d]
 
 Prints one JSON line (rank 0). Under torchrun each rank runs an independent
 replica of the workload (the solver does not shard: replicas only).
@@ -367,6 +367,58 @@ def run_wsweep(args, torch, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def angle_cases_3d():
+    """The 3D contact-angle table: flat wall (96 x 96 x 56, R = 20), 30 deg
+    staircase plane (128 x 64 x 112, R = 20) and solid sphere of radius 24
+    (128^3, R = 16)."""
+    from paper_2312_00369_gb300 import workloads as wl
+    out = [("flat", th, wl.droplet_on_flat_wall_3d(nx=96, ny=96, nz=56, R=20.0, theta=th))
+           for th in (30.0, 60.0, 90.0, 120.0, 150.0)]
+    out += [("incline30", th, wl.droplet_on_incline_3d(nx=128, ny=64, nz=112, gamma=30.0, R=20.0, theta=th))
+            for th in (60.0, 90.0, 120.0)]
+    out += [("sphere", th, wl.droplet_on_sphere_3d(n=128, Rs=24.0, R=16.0, theta=th)) for th in (60.0, 90.0, 120.0)]
+    return out
+
+
+def run_angles3d(args, torch, rank, world, local):
+    """Equilibrium contact angles in 3D (the 3D column of the paper's angle
+    comparison, Secs. 3.1-3.3): every case of angle_cases_3d() run for
+    `steps` (default 20000) with the (1/2) dG/dt term as --dgdt (default for
+    this workload: omitted), FP32; the fitted angle and its error per case."""
+    from paper_2312_00369_gb300.pflbm import PflbmError, Solver3D
+    steps = args.steps if args.steps > 1000 else 20000
+    stream = torch.cuda.Stream(device=local)
+    table, lu, busy = {}, 0, 0.0
+    for kind, th, c in angle_cases_3d():
+        with torch.cuda.stream(stream):
+            sv = Solver3D(c.solid, theta_deg=th, precision="fp32", device=local, stream=stream,
+                          dgdt_mode=args.dgdt, **c.physical())
+            for d in c.droplets:
+                sv.init_droplet(*d)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sv.step(steps)
+            torch.cuda.synchronize()
+            busy += time.perf_counter() - t0
+            lu += int(np.prod(c.shape)) * steps
+            try:
+                sv.check()
+                fit, sph, n = sv.contact_angle(dict(dict(exclude=1.5 * c.W), **c.wall))
+                row = {"measured": fit, "error": fit - th, "points": n}
+            except PflbmError as e:
+                row = {"failed": str(e)}
+            sv.close()
+        table.setdefault(kind, {})[f"theta={th:g}"] = row
+    line = {"metric": "MLUPS", "value": lu / busy / 1e6, "unit": "MLUPS", "n_gpus": world, "steps": steps,
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+            "data": "synthetic",
+            "config": {"workload": "angles3d", "dgdt_mode": args.dgdt,
+                       "cases": "flat 96x96x56 R=20; incline30 128x64x112 R=20; sphere Rs=24 128^3 R=16"},
+            "contact_angle": table}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # three dimensions (D3Q19 f, D3Q7 g): every f_i and g_i read and written
 # once, the history read and written once, one node byte
 BYTES_PER_LU_3D = {"fp64": 2 * (19 + 7) * 8 + 2 * 8 + 1, "fp32": 2 * (19 + 7) * 4 + 2 * 4 + 1}
@@ -524,9 +576,11 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    if args.workload in ("batched", "serving", "wsweep", "many_flat3d"):
+    if args.workload in ("batched", "serving", "wsweep", "many_flat3d", "angles3d"):
+        if args.workload == "angles3d" and "--dgdt" not in sys.argv:
+            args.dgdt = 1          # long 3D runs: the (1/2) dG/dt term omitted unless asked for
         {"batched": run_batched, "serving": run_serving, "wsweep": run_wsweep,
-         "many_flat3d": run_3d}[args.workload](
+         "many_flat3d": run_3d, "angles3d": run_angles3d}[args.workload](
             args, torch, rank, world, local)
         if world > 1:
             dist.destroy_process_group()

@@ -276,6 +276,7 @@ typedef struct {
     void* stream;                /* cudaStream_t; NULL: a stream of its own */
     int step_path;               /* enum pflbm3d_step_path; the results are identical */
     int fused_zc;                /* planes per CTA of the fused step; <= 0: chosen by the library */
+    int dgdt_mode;               /* as pflbm_params_t.dgdt_mode: 0 backward difference, 1 omitted */
 } pflbm3d_params_t;
 
 /* How a 3D step runs. PFLBM3D_FUSED: one launch; each CTA marches a 32 x 8
@@ -307,6 +308,29 @@ int pflbm3d_mass(pflbm3d_t* h, double* out);
 int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av);
 /* Waits for the stream; PFLBM_ENUMERIC if a NaN or |u| >= 0.3 was seen. */
 int pflbm3d_check(pflbm3d_t* h);
+
+/* Wall for the 3D contact-angle fit. type 0: the plane through (px, py, pz)
+ * with unit normal (nx, ny, nz) pointing into the fluid; type 1: a solid
+ * sphere of centre (px, py, pz) and radius r. Only the crossings with
+ * x_lo <= x < x_hi, y_lo <= y < y_hi and farther than `exclude` from the wall
+ * are fitted (the window separates droplets of a many-droplet lattice). */
+typedef struct {
+    int type;
+    double px, py, pz, nx, ny, nz, r;
+    double x_lo, x_hi, y_lo, y_hi;
+    double exclude;
+} pflbm3d_wall_t;
+
+/* Contact angle of one droplet (the 3D form of the fits of Secs. 3.1-3.3),
+ * in FP64 on the device: the phi = 1/2 crossings between fluid neighbours, a
+ * sphere fit, and theta from cos(theta) = -n.(c - p)/R (plane) or
+ * (R^2 + r^2 - |c - p|^2)/(2 R r) (sphere). theta is NaN when fewer than 4
+ * points remain. sphere (optional, 4 doubles) receives the fitted centre and
+ * radius, npoints (optional) the point count. The first call allocates a
+ * point buffer of min(3 N, 2^22) points. Synchronous. Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+int pflbm3d_contact_angle(pflbm3d_t* h, const pflbm3d_wall_t* wall, double* theta_deg, double* sphere,
+                          int* npoints);
 
 #ifdef __cplusplus
 }

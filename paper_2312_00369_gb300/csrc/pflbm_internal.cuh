@@ -69,6 +69,16 @@ __device__ __forceinline__ C cdot(C vx, C vy, C vz)
 constexpr int TX = 32;
 constexpr int TY = 8;
 
+// Wall of the 3D contact-angle fit (pflbm3d_wall_t on the device).
+struct Wall3 {
+    int type;             // 0 plane through p with unit normal n into the fluid; 1 solid sphere (p, r)
+    double p[3], n[3], r;
+    double x_lo, x_hi, y_lo, y_hi, exclude;
+};
+cudaError_t launch_contact_angle3d(const uint8_t* cls, const double* d_phi, int nx, int ny, int nz, int pitch,
+                                   const Wall3& w, double* pts, int cap, int* d_count, double* d_out,
+                                   cudaStream_t stream);
+
 struct Params {           // derived parameters (Sec. 2.1-2.2), in FP64
     double beta, kappa, alpha, tau_f, tau_g, rho_l, rho_g, W, sigma, M;
     double nu_l, nu_g;    // both > 0: variable viscosity

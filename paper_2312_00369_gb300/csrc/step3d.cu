@@ -9,6 +9,7 @@
 // collide-and-store of f and g (pull scheme and modified bounce-back as in
 // 2D, see step.cu), which reads phi of the 18 neighbours for the stencils.
 // Nodes are stored [nz][ny][pitch]; x and y are periodic, z has walls.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -76,6 +77,7 @@ struct Args3 {
     int nx, ny, nz, pitch;
     int plane;        // nz * ny * pitch, 26 planes fit in int
     C beta4, kappa, rho_g, drho, omega_f, omega_g, force_pre, alpha;
+    int dgdt;             // 1: the (1/2) dG/dt term omitted (no history read or written)
     int* status;
     double* o_phi;
     double* o_u;
@@ -288,7 +290,7 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     typename T::G0T raw0;
     load_g(g, raw0);
     const C s_now = fmadd(u[2], gp[2], fmadd(u[1], gp[1], u[0] * gp[0]));
-    const C src = fmadd(C(1.5), s_now, C(-0.5) * a.sprev[k]);
+    const C src = a.dgdt ? s_now : fmadd(C(1.5), s_now, C(-0.5) * a.sprev[k]);
     const C am = a.alpha * mu;
     // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu - src / 2), the same for i = 1..6
     const C gm = q7w<C>(1) * fmadd(C(-0.5), src, a.omega_g * am), omg = C(1) - a.omega_g;
@@ -296,7 +298,7 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     for (int i = 1; i < 7; ++i) a.g_out[i * a.plane + k] = T::template st<1>(fmadd(omg, g[i], gm));
     const C d0 = fmadd(a.omega_g, fmadd(C(-0.75), am, sum6(g)), (q7w<C>(0) * C(-2.5)) * src);
     a.g0_out[k] = T::g0_add(raw0, d0, a.status);
-    a.sprev[k] = s_now;
+    if (!a.dgdt) a.sprev[k] = s_now;
 }
 
 template <int PREC, bool COLLIDE>
@@ -765,6 +767,8 @@ struct pflbm3d {
     double* red = nullptr;
     double* out = nullptr;
     int* dstatus = nullptr;
+    double* pts = nullptr;      // contact-angle crossings (3 doubles each)
+    int pts_cap = 0;
     int* ghosts = nullptr;      // indices of the ghost nodes
     int n_ghosts = 0;
     bool fused = true;          // one-launch step (k3_fused) or three launches
@@ -814,6 +818,7 @@ Args3<PREC> make3(pflbm3d_t* h, int in)
     a.omega_g = (C)(1.0 / q.tau_g);
     a.force_pre = (C)(1.0 - 0.5 / q.tau_f);
     a.alpha = (C)q.alpha;
+    a.dgdt = q.dgdt_mode;
     a.status = h->dstatus;
     return a;
 }
@@ -895,7 +900,7 @@ void release3(pflbm3d_t* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* bufs[] = {h->cls, h->solid, h->av, h->wet, h->pop[0], h->pop[1], h->sprev, h->phi, h->phi0, h->mu0,
-                    h->red, h->out, h->dstatus, h->ghosts, h->gflag};
+                    h->red, h->out, h->dstatus, h->ghosts, h->gflag, h->pts};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -962,6 +967,7 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
     q.alpha = p->M / (0.25 * (q.tau_g - 0.5));   // Eq. mobility with the D3Q7 c_s^2 = 1/4
     q.rho_l = p->rho_l;
     q.rho_g = p->rho_g;
+    q.dgdt_mode = p->dgdt_mode ? 1 : 0;
     h->theta = p->theta_deg;
     if (p->stream) {
         h->stream = (cudaStream_t)p->stream;
@@ -974,7 +980,7 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
         {(void**)&h->cls, plane}, {(void**)&h->solid, plane}, {(void**)&h->av, plane * 8}, {&h->wet, plane * cs},
         {&h->pop[0], pop3_bytes(p->precision, plane)}, {&h->pop[1], pop3_bytes(p->precision, plane)},
         {&h->sprev, plane * cs}, {&h->phi, plane * cs}, {(void**)&h->phi0, plane * 8}, {(void**)&h->mu0, plane * 8},
-        {(void**)&h->red, kMassBlocks * 8 + 64}, {(void**)&h->dstatus, 16}};
+        {(void**)&h->red, (kMassBlocks + 32) * 8}, {(void**)&h->dstatus, 16}};
     for (auto& b : bufs) {
         if (cudaMalloc(b.ptr, b.bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -1167,6 +1173,44 @@ int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av)
         CK3(cudaMemcpy2DAsync(av, h->nx * 8, h->av, h->pitch * 8, h->nx * 8, (size_t)h->ny * h->nz,
                               cudaMemcpyDeviceToHost, h->stream));
     CK3(cudaStreamSynchronize(h->stream));
+    return PFLBM_OK;
+}
+
+int pflbm3d_contact_angle(pflbm3d_t* h, const pflbm3d_wall_t* wall, double* theta_deg, double* sphere, int* npoints)
+{
+    if (!h || !wall || !theta_deg) return fail3(PFLBM_EINVAL, "NULL argument");
+    if (wall->type != 0 && wall->type != 1) return fail3(PFLBM_EINVAL, "wall type must be 0 or 1");
+    if (int rc = materialize3(h)) return rc;
+    const size_t N = (size_t)h->nx * h->ny * h->nz;
+    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        h->out = nullptr;
+        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+    }
+    if (!h->pts) {
+        const long long cap = std::min<long long>(3LL * (long long)N, 1LL << 22);
+        if (cudaMalloc((void**)&h->pts, (size_t)cap * 3 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            h->pts = nullptr;
+            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+        }
+        h->pts_cap = (int)cap;
+    }
+    double* dphi = h->out;
+    CK3(P3(macro3_prec<PFLBM_FP64>(h, dphi, nullptr, nullptr), macro3_prec<PFLBM_FP32>(h, dphi, nullptr, nullptr)));
+    Wall3 w{wall->type, {wall->px, wall->py, wall->pz}, {wall->nx, wall->ny, wall->nz}, wall->r,
+            wall->x_lo, wall->x_hi, wall->y_lo, wall->y_hi, wall->exclude};
+    int* d_count = (int*)(h->red + kMassBlocks + 8);
+    double* d_res = h->red + kMassBlocks + 16;
+    CK3(launch_contact_angle3d(h->cls, dphi, h->nx, h->ny, h->nz, h->pitch, w, h->pts, h->pts_cap, d_count, d_res,
+                               h->stream));
+    double res[6];
+    CK3(cudaMemcpyAsync(res, d_res, sizeof(res), cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    *theta_deg = res[0];
+    if (sphere)
+        for (int i = 0; i < 4; ++i) sphere[i] = res[1 + i];
+    if (npoints) *npoints = (int)res[5];
     return PFLBM_OK;
 }
 

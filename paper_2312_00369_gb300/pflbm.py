@@ -55,7 +55,13 @@ class Params3D(ctypes.Structure):
                 ("M", ctypes.c_double), ("tau_f", ctypes.c_double), ("rho_l", ctypes.c_double),
                 ("rho_g", ctypes.c_double), ("tau_g", ctypes.c_double), ("precision", ctypes.c_int),
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("step_path", ctypes.c_int),
-                ("fused_zc", ctypes.c_int)]
+                ("fused_zc", ctypes.c_int), ("dgdt_mode", ctypes.c_int)]
+
+
+class Wall3D(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int)] + [(k, ctypes.c_double) for k in
+                                            ("px", "py", "pz", "nx", "ny", "nz", "r", "x_lo", "x_hi", "y_lo",
+                                             "y_hi", "exclude")]
 
 
 class Schedule(ctypes.Structure):
@@ -138,6 +144,7 @@ _SIGS = {
     "pflbm3d_mass": (ctypes.c_int, [_H, _dp]),
     "pflbm3d_geometry": (ctypes.c_int, [_H, _u8p, _dp]),
     "pflbm3d_check": (ctypes.c_int, [_H]),
+    "pflbm3d_contact_angle": (ctypes.c_int, [_H, ctypes.POINTER(Wall3D), _dp, _dp, _ip]),
 }
 
 
@@ -440,7 +447,7 @@ class Solver3D:
 
     def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
                  rho_l=1.0, rho_g=0.1, tau_g=0.0, precision="fp32", device=None, stream=None,
-                 step_path="auto", fused_zc=0):
+                 step_path="auto", fused_zc=0, dgdt_mode=0):
         import torch
         L = lib()
         solid = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -461,9 +468,11 @@ class Solver3D:
         p.stream = ctypes.c_void_p(stream.cuda_stream)
         p.step_path = {"auto": 0, "fused": 1, "three_pass": 2}[step_path]
         p.fused_zc = int(fused_zc)
+        p.dgdt_mode = int(dgdt_mode)
         h = _H()
         _check(L.pflbm3d_create(ctypes.byref(h), ctypes.byref(p)))
         self._h = h
+        self.W = W
         _LIVE_SOLVERS.add(self)
 
     def close(self):
@@ -508,3 +517,20 @@ class Solver3D:
 
     def check(self):
         _check(lib().pflbm3d_check(self._h))
+
+    def contact_angle(self, wall: dict, exclude=None):
+        """``wall``: dict(type=0, p=(x, y, z), n=(nx, ny, nz)) for a plane or
+        dict(type=1, p=centre, r=radius) for a solid sphere; optional x_lo,
+        x_hi, y_lo, y_hi window and ``exclude`` (default 1.5 W). Returns
+        (theta_deg, [cx, cy, cz, R], n_points)."""
+        p = wall.get("p", (0.0, 0.0, 0.0))
+        n = wall.get("n", (0.0, 0.0, 1.0))
+        w = Wall3D(type=int(wall.get("type", 0)), px=p[0], py=p[1], pz=p[2], nx=n[0], ny=n[1], nz=n[2],
+                   r=float(wall.get("r", 0.0)), x_lo=wall.get("x_lo", -1e300), x_hi=wall.get("x_hi", 1e300),
+                   y_lo=wall.get("y_lo", -1e300), y_hi=wall.get("y_hi", 1e300),
+                   exclude=wall.get("exclude", 1.5 * self.W if exclude is None else exclude))
+        th = ctypes.c_double()
+        sph = (ctypes.c_double * 4)()
+        npts = ctypes.c_int()
+        _check(lib().pflbm3d_contact_angle(self._h, ctypes.byref(w), ctypes.byref(th), sph, ctypes.byref(npts)))
+        return th.value, np.array(sph[:]), npts.value

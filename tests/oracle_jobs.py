@@ -134,13 +134,20 @@ def window_run(case_name_kwargs, x_centre, half, steps):
 def case3d_by_name(name):
     if name == "flat3d":          # ragged in x (40 = 32 + 8) and in y (20 = 8 + 8 + 4)
         s, zw = wl.box3d(40, 20, 20)
-        return wl.Case3D("flat3d", s, [(20.0, 10.0, zw, 7.0)], zw, theta_deg=60.0, steps=300)
+        return wl.Case3D("flat3d", s, [(20.0, 10.0, zw, 7.0)], zw, theta_deg=60.0, steps=300,
+                         wall=dict(type=0, p=(0.0, 0.0, zw), n=(0.0, 0.0, 1.0), exclude=1.0))
     if name == "flat3d_two":      # two overlapping droplets (pointwise maximum), theta > 90
         s, zw = wl.box3d(40, 20, 20)
         return wl.Case3D("flat3d_two", s, [(14.0, 10.0, zw, 6.0), (25.0, 9.0, zw, 5.0)], zw,
                          theta_deg=120.0, steps=200)
     if name == "sphere3d":
         return wl.droplet_on_sphere_3d(n=32, Rs=6.0, R=7.0, theta=75.0, steps=200)
+    if name == "incline3d":       # 30 deg staircase plane, theta > 90
+        return wl.droplet_on_incline_3d(nx=40, ny=20, nz=40, gamma=30.0, R=7.0, theta=110.0, steps=250)
+    if name == "flat3d_nodgdt":   # the (1/2) dG/dt term omitted
+        s, zw = wl.box3d(40, 20, 20)
+        return wl.Case3D("flat3d_nodgdt", s, [(20.0, 10.0, zw, 7.0)], zw, theta_deg=50.0, steps=300,
+                         meta=dict(dgdt=1), wall=dict(type=0, p=(0.0, 0.0, zw), n=(0.0, 0.0, 1.0)))
     if name == "tiny3d":          # smaller than one tile and its halo in x and y
         s, zw = wl.box3d(3, 4, 9)
         return wl.Case3D("tiny3d", s, [(1.0, 2.0, zw, 3.0)], zw, theta_deg=50.0, steps=60)
@@ -150,10 +157,15 @@ def case3d_by_name(name):
 def run3d_case(name, steps=None):
     c = case3d_by_name(name)
     o = oracle.Oracle3D(c.solid, theta_deg=c.theta_deg, **c.physical())
+    o.set_dgdt(c.meta.get("dgdt", 0))
     for d in c.droplets:
         o.init_droplet(*d)
     m0 = o.mass()
     o.step(c.steps if steps is None else steps)
     phi, u, p = o.get()
     g = o.geometry()
-    return dict(phi=phi, u=u, p=p, mass0=m0, mass=o.mass(), cls=g["cls"], av=g["av"])
+    out = dict(phi=phi, u=u, p=p, mass0=m0, mass=o.mass(), cls=g["cls"], av=g["av"])
+    if c.wall:
+        th, sph, n = oracle.contact_angle3(phi, g["cls"], dict(dict(exclude=1.5 * c.W), **c.wall))
+        out.update(theta=th, sphere=sph, npts=n)
+    return out
