@@ -321,10 +321,16 @@ class Solver:
     def step(self, n=1):
         _check(lib().pflbm_step(self._h, int(n)))
 
-    def get(self):
-        phi = np.empty((self.ny, self.nx))
-        u = np.empty((self.ny, self.nx, 2))
-        p = np.empty((self.ny, self.nx))
+    def get(self, out=None):
+        """(phi [ny, nx], u [ny, nx, 2], p [ny, nx]) as float64 host arrays.
+        ``out``: three C-contiguous float64 arrays of those shapes to fill
+        (for example views of pinned memory, which copy faster)."""
+        if out is None:
+            out = (np.empty((self.ny, self.nx)), np.empty((self.ny, self.nx, 2)), np.empty((self.ny, self.nx)))
+        phi, u, p = out
+        for a, shp in zip(out, ((self.ny, self.nx), (self.ny, self.nx, 2), (self.ny, self.nx))):
+            if a.shape != shp or a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError(f"output array must be C-contiguous float64 {shp}")
         _check(lib().pflbm_get(self._h, _p(phi), _p(u), _p(p)))
         return phi, u, p
 
@@ -498,9 +504,16 @@ class Solver3D:
     def step(self, n=1):
         _check(lib().pflbm3d_step(self._h, int(n)))
 
-    def get(self):
+    def get(self, out=None):
+        """(phi, u [..., 3], p) as float64 host arrays [nz, ny, nx]; ``out``
+        as for Solver.get."""
         shp = (self.nz, self.ny, self.nx)
-        phi, u, p = np.empty(shp), np.empty(shp + (3,)), np.empty(shp)
+        if out is None:
+            out = (np.empty(shp), np.empty(shp + (3,)), np.empty(shp))
+        phi, u, p = out
+        for a, sh in zip(out, (shp, shp + (3,), shp)):
+            if a.shape != sh or a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError(f"output array must be C-contiguous float64 {sh}")
         _check(lib().pflbm3d_get(self._h, _p(phi), _p(u), _p(p)))
         return phi, u, p
 
