@@ -72,12 +72,12 @@ __device__ __forceinline__ typename Store<PREC>::C pull(const typename Store<PRE
     using T = Store<PREC>;
     constexpr int X = cx(I), Y = cy(I), O = opp(I);
     if (!CHECK || zeta_of(s_cls[sy - Y][sx - X])) {
-        return T::template ld<I>(base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)]);
+        return T::template ldp<I>(base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)]);
     }
     if (zeta_of(s_cls[sy + Y][sx + X])) {
-        return T::template ld<O>(base[O * plane + (gy + Y) * pitch + wrap1(gx + X, nx)]);
+        return T::template ldp<O>(base[O * plane + (gy + Y) * pitch + wrap1(gx + X, nx)]);
     }
-    return T::template ld<O>(base[O * plane + gy * pitch + gx]);
+    return T::template ldp<O>(base[O * plane + gy * pitch + gx]);
 }
 
 template <int PREC, bool CHECK>
@@ -86,7 +86,7 @@ __device__ __forceinline__ void pull_f(typename Store<PREC>::C v[9], const typen
                                        int pitch, int plane)
 {
     using T = Store<PREC>;
-    v[0] = T::template ld<0>(f[gy * pitch + gx]);
+    v[0] = T::template ldp<0>(f[gy * pitch + gx]);
     v[1] = pull<1, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     v[2] = pull<2, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     v[3] = pull<3, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
@@ -122,9 +122,24 @@ __device__ __forceinline__ C sum_moving(const C v[9])
     return ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
 }
 
+// sum_{i != 0} v_i in population units (v in the step's work units).
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::C sum_pop(const typename Store<PREC>::C v[9])
+{
+    using T = Store<PREC>;
+    if constexpr (T::kNorm)
+        return fmadd(T::template unit<1>(), (v[1] + v[2]) + (v[3] + v[4]),
+                     T::template unit<5>() * ((v[5] + v[6]) + (v[7] + v[8])));
+    else
+        return sum_moving(v);
+}
+
 // phi = sum_i g_i (Eq. order-parameter), in one fixed order everywhere.
-template <typename C>
-__device__ __forceinline__ C phi_of(const C v[9]) { return v[0] + sum_moving(v); }
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::C phi_of(const typename Store<PREC>::C v[9])
+{
+    return v[0] + sum_pop<PREC>(v);
+}
 
 template <int PREC, bool CHECK>
 __device__ __forceinline__ typename Store<PREC>::C pulled_phi(const Planes<PREC>& P, const uint8_t (*s_cls)[TX + 6],
@@ -134,7 +149,7 @@ __device__ __forceinline__ typename Store<PREC>::C pulled_phi(const Planes<PREC>
     typename Store<PREC>::C v[9];
     typename Store<PREC>::G0T raw0;
     pull_g<PREC, CHECK>(v, raw0, P, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    return phi_of(v);
+    return phi_of<PREC>(v);
 }
 
 // Prologue of a tile whose nodes within two of it are all fluid: no class
@@ -154,7 +169,7 @@ __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
         pull_g<PREC, false>(gown, raw0, a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
         // the f pulls do not depend on phi: issue them before the barrier
         if (PFLBM_PREFETCH_F) pull_f<PREC, false>(fown, a.in.f, nullptr, 0, 0, gx, gy, nx, pitch, plane);
-        s_phi[ty + 2][tx + 2] = phi_of(gown);
+        s_phi[ty + 2][tx + 2] = phi_of<PREC>(gown);
     }
     // ring: top row, bottom row (TX + 2 each), left and right columns (TY each)
     constexpr int RT = TX + 2, NR = 2 * (TX + 2) + 2 * TY;
@@ -263,7 +278,7 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
                 pull_g<PREC, true>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
             else
                 pull_g<PREC, false>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
-            ph = phi_of(gown);
+            ph = phi_of<PREC>(gown);
         }
         s_phi[ty + 2][tx + 2] = ph;
     }
@@ -338,10 +353,16 @@ __device__ __forceinline__ void collide_f_pair(const StepArgs<PREC>& a, typename
     const C cu = cdot<cx(I), cy(I)>(ux, uy);
     const C cF = cdot<cx(I), cy(I)>(Fx, Fy);
     const C cdr = cdot<cx(I), cy(I)>(drx, dry);
-    const C S = w * fmadd(cu, fmadd(K.c45, cu, K.pre3 * cdr), K.base);
-    const C A = w * fmadd(K.c3, cu, K.pre3 * cF);
-    a.out.f[I * a.plane + k] = T::template st<I>(fmadd(K.omf, fI, S + A));
-    a.out.f[O * a.plane + k] = T::template st<O>(fmadd(K.omf, fO, S - A));
+    // 16-bit work units f~ = f scale / w: the factor w becomes scale, which
+    // the caller has folded into K
+    C S = fmadd(cu, fmadd(K.c45, cu, K.pre3 * cdr), K.base);
+    C A = fmadd(K.c3, cu, K.pre3 * cF);
+    if constexpr (!T::kNorm) {
+        S = w * S;
+        A = w * A;
+    }
+    a.out.f[I * a.plane + k] = T::template stp<I>(fmadd(K.omf, fI, S + A));
+    a.out.f[O * a.plane + k] = T::template stp<O>(fmadd(K.omf, fO, S - A));
 }
 
 // g_i (i != 0) collision and store; returns the storage rounding residual
@@ -357,9 +378,9 @@ __device__ __forceinline__ typename Store<PREC>::C collide_g_dir(const StepArgs<
     // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu + h_i src): gadd is the
     // second term, the same for the four axes and for the four diagonals
     const C v = fmadd(omg, g_i, gadd);
-    const typename T::S s = T::template st<I>(v);
+    const typename T::S s = T::template stp<I>(v);
     a.out.g[I * a.plane + k] = s;
-    if (T::kAbsorb) return v - T::template ld<I>(s);   // ld is a single product
+    if (T::kAbsorb) return v - T::template ldp<I>(s);   // in work units
     return C(0);
 }
 
@@ -413,13 +434,19 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
         pull_f<PREC, true>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
     else if (!(PFLBM_PREFETCH_F && fluid_tile))
         pull_f<PREC, false>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
-    const C mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const C my = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    C mx, my;
+    if constexpr (T::kNorm) {
+        mx = fmadd(T::template unit<1>(), f[1] - f[3], T::template unit<5>() * ((f[5] - f[6]) + (f[8] - f[7])));
+        my = fmadd(T::template unit<1>(), f[2] - f[4], T::template unit<5>() * ((f[5] + f[6]) - (f[7] + f[8])));
+    } else {
+        mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        my = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    }
     const C inv_rho = C(1) / rho;
     const C ux = fmadd(C(0.5), Fx, mx) * inv_rho;
     const C uy = fmadd(C(0.5), Fy, my) * inv_rho;
     const C uu = fmadd(ux, ux, uy * uy);
-    const C fsum = sum_moving(f);
+    const C fsum = sum_pop<PREC>(f);
     // p = c_s^2/(1 - w_0) [sum_{i!=0} f_i + u.grad(rho)/2 + rho s_0(u)], s_0 = -w_0 (3/2) u^2
     const C p = C(0.6) * fmadd(-(rho * (C(2) / C(3))), uu, fmadd(C(0.5), fmadd(ux, drx, uy * dry), fsum));
 
@@ -441,8 +468,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
 
     // ---- f collision: f* = f + (f^eq - f)/tau_f + F_i ----
     {
-        const C feq0 = fmadd(-(rho * (wgt<C>(0) * C(1.5))), uu, (C(-5) / C(3)) * p);
-        a.out.f[k] = T::template st<0>(fmadd(omega_f, feq0 - f[0], f[0]));
+        C feq0 = fmadd(-(rho * (wgt<C>(0) * C(1.5))), uu, (C(-5) / C(3)) * p);
+        if constexpr (T::kNorm) feq0 = feq0 * (C(1) / T::template unit<0>());
+        a.out.f[k] = T::template stp<0>(fmadd(omega_f, feq0 - f[0], f[0]));
     }
     {
         PairK<C> K;
@@ -451,6 +479,12 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
         K.c3 = omega_f * C(3) * rho;
         K.pre3 = C(3) * force_pre;
         K.omf = C(1) - omega_f;
+        if constexpr (T::kNorm) {          // scale is a power of two: exact
+            K.base = K.base * T::scale();
+            K.c45 = K.c45 * T::scale();
+            K.c3 = K.c3 * T::scale();
+            K.pre3 = K.pre3 * T::scale();
+        }
         collide_f_pair<PREC, 1, 3>(a, f[1], f[3], K, ux, uy, Fx, Fy, drx, dry, k);
         collide_f_pair<PREC, 2, 4>(a, f[2], f[4], K, ux, uy, Fx, Fy, drx, dry, k);
         collide_f_pair<PREC, 5, 7>(a, f[5], f[7], K, ux, uy, Fx, Fy, drx, dry, k);
@@ -462,19 +496,24 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     const C src = a.dgdt ? s_now : fmadd(C(1.5), s_now, C(-0.5) * (C)a.sprev[k]);
     const C am = a.alpha * mu;
     const C omg = C(1) - a.omega_g, oam = a.omega_g * am;
-    const C g_ax = wgt<C>(1) * fmadd(C(-0.5), src, oam), g_dg = wgt<C>(5) * (oam + src);   // h = -1/2, 1
-    C resid = collide_g_dir<PREC, 1>(a, g[1], omg, g_ax, k);
-    resid += collide_g_dir<PREC, 2>(a, g[2], omg, g_ax, k);
-    resid += collide_g_dir<PREC, 3>(a, g[3], omg, g_ax, k);
-    resid += collide_g_dir<PREC, 4>(a, g[4], omg, g_ax, k);
-    resid += collide_g_dir<PREC, 5>(a, g[5], omg, g_dg, k);
-    resid += collide_g_dir<PREC, 6>(a, g[6], omg, g_dg, k);
-    resid += collide_g_dir<PREC, 7>(a, g[7], omg, g_dg, k);
-    resid += collide_g_dir<PREC, 8>(a, g[8], omg, g_dg, k);
+    // h = -1/2 on the axes, 1 on the diagonals; in the 16-bit work units the
+    // factor w_i is scale for every direction
+    const C g_ax = (T::kNorm ? T::scale() : wgt<C>(1)) * fmadd(C(-0.5), src, oam);
+    const C g_dg = (T::kNorm ? T::scale() : wgt<C>(5)) * (oam + src);
+    C r_ax = collide_g_dir<PREC, 1>(a, g[1], omg, g_ax, k);
+    r_ax += collide_g_dir<PREC, 2>(a, g[2], omg, g_ax, k);
+    r_ax += collide_g_dir<PREC, 3>(a, g[3], omg, g_ax, k);
+    r_ax += collide_g_dir<PREC, 4>(a, g[4], omg, g_ax, k);
+    C r_dg = collide_g_dir<PREC, 5>(a, g[5], omg, g_dg, k);
+    r_dg += collide_g_dir<PREC, 6>(a, g[6], omg, g_dg, k);
+    r_dg += collide_g_dir<PREC, 7>(a, g[7], omg, g_dg, k);
+    r_dg += collide_g_dir<PREC, 8>(a, g[8], omg, g_dg, k);
+    // storage rounding residual in population units (0 for FP32 / FP64)
+    const C resid = T::kAbsorb ? fmadd(T::template unit<1>(), r_ax, T::template unit<5>() * r_dg) : C(0);
     {
         // g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu (Eq. H_i); in the
         // 16-bit formats g_0 also takes back what rounding removed from g_1..g_8
-        const C d0 = fmadd(a.omega_g, fmadd(-(C(1) - wgt<C>(0)), am, sum_moving(g)), (wgt<C>(0) * C(-2)) * src);
+        const C d0 = fmadd(a.omega_g, fmadd(-(C(1) - wgt<C>(0)), am, sum_pop<PREC>(g)), (wgt<C>(0) * C(-2)) * src);
         a.out.g0[k] = T::g0_add(g0raw, T::kAbsorb ? d0 + resid : d0, a.status);
     }
     if (!a.dgdt) a.sprev[k] = s_now;

@@ -12,6 +12,11 @@
 //               node, so the stored sum_i g_i is exact to 2^-30 at every node;
 //               arithmetic in FP32.
 //
+// Work units of the step (ldp / stp / unit): FP64 and FP32 work in population
+// units. The 16-bit formats work in the stored units f~ = f scale / w_i, so a
+// load or store is a bare conversion; unit<I>() = w_I / scale converts back to
+// population units where a sum over directions needs them (phi, moments).
+//
 // Layout of one copy of the state, planes of ny * pitch elements:
 //   FP64 / FP32: f_0..f_8, g_0..g_8 (the g_0 plane holds the g_0 storage);
 //   16-bit:      f_0..f_8, g_0..g_8 (16-bit, the g_0 plane unused), then one
@@ -34,6 +39,11 @@ template <> struct Store<PFLBM_FP64> {
     using C = double;
     using G0T = double;
     static constexpr bool kAbsorb = false;
+    static constexpr bool kNorm = false;
+    template <int I> __device__ static C ldp(S v) { return v; }
+    template <int I> __device__ static S stp(C v) { return v; }
+    template <int I> __device__ static constexpr C unit() { return C(1); }
+    __device__ static constexpr C scale() { return C(1); }
     template <int I> __device__ static C ld(S v) { return v; }
     template <int I> __device__ static S st(C v) { return v; }
     __device__ static C g0(G0T raw) { return raw; }
@@ -66,6 +76,11 @@ template <> struct Store<PFLBM_FP32> {
     using C = float;
     using G0T = int32_t;
     static constexpr bool kAbsorb = false;
+    static constexpr bool kNorm = false;
+    template <int I> __device__ static C ldp(S v) { return v; }
+    template <int I> __device__ static S stp(C v) { return v; }
+    template <int I> __device__ static constexpr C unit() { return C(1); }
+    __device__ static constexpr C scale() { return C(1); }
     template <int I> __device__ static C ld(S v) { return v; }
     template <int I> __device__ static S st(C v) { return v; }
     __device__ static C g0(G0T raw) { return Fixed30::value(raw); }
@@ -80,6 +95,11 @@ template <typename H, int SCALE_LOG2> struct Store16 {
     using C = float;
     using G0T = int32_t;
     static constexpr bool kAbsorb = true;
+    static constexpr bool kNorm = true;
+    template <int I> __device__ static C ldp(S v) { return to_float(v); }
+    template <int I> __device__ static S stp(C v) { return from_float(v); }
+    template <int I> __device__ static constexpr float unit() { return to_pop<I>(); }
+    __device__ static constexpr float scale() { return (float)(1 << SCALE_LOG2); }
     template <int I> __device__ static constexpr float to_pop()
     {
         return wgt<float>(I) / (float)(1 << SCALE_LOG2);
