@@ -169,3 +169,31 @@ def run3d_case(name, steps=None):
         th, sph, n = oracle.contact_angle3(phi, g["cls"], dict(dict(exclude=1.5 * c.W), **c.wall))
         out.update(theta=th, sphere=sph, npts=n)
     return out
+
+
+def window3d_run(full_kwargs, xc, yc, half, steps):
+    """Run the 3D oracle on a full-height window [xc - half, xc + half] x
+    [yc - half, yc + half] of a large many-droplet box, built from the same
+    generator, for `steps` steps. The initial field is Eq. initialphi with
+    the periods of the full box (pointwise maximum over droplets). Nodes
+    farther than 2 * steps + 1 from the window edges do not feel the wrong
+    periodic wrap of the window, so the centre column equals the full run."""
+    case = wl.many_droplets_3d(**full_kwargs)
+    nz, ny_full, nx_full = case.shape
+    xs = np.arange(xc - half, xc + half + 1) % nx_full
+    ys = np.arange(yc - half, yc + half + 1) % ny_full
+    solid = np.ascontiguousarray(case.solid[:, ys][:, :, xs])
+    z, yy, xx = np.meshgrid(np.arange(nz, dtype=float), ys.astype(float), xs.astype(float), indexing="ij")
+    phi0 = np.zeros(solid.shape)
+    for (x0, y0, z0, R) in case.droplets:
+        dx = np.abs(xx - x0) % nx_full
+        dx = np.where(dx > 0.5 * nx_full, nx_full - dx, dx)
+        dy = np.abs(yy - y0) % ny_full
+        dy = np.where(dy > 0.5 * ny_full, ny_full - dy, dy)
+        r = np.sqrt(dx * dx + dy * dy + (z - z0) ** 2)
+        phi0 = np.maximum(phi0, 0.5 + 0.5 * np.tanh(2.0 * (R - r) / case.W))
+    o = oracle.Oracle3D(solid, theta_deg=case.theta_deg, **case.physical())
+    o.init_phi(phi0)
+    o.step(steps)
+    phi, u, p = o.get()
+    return dict(phi=phi[:, half, half], u=u[:, half, half], p=p[:, half, half])

@@ -21,12 +21,26 @@ _pool = None
 _fut = {}
 
 
+# the benchmark box (512 x 512 x 128, 64 droplets) compared on columns with
+# oracle windows of the same input
+FULL3 = dict(nx=512, ny=512, nz=128)
+WIN3_STEPS, WIN3_HALF = 8, 18
+
+
+def _win_centres():
+    from paper_2312_00369_gb300 import workloads as wl
+    c = wl.many_droplets_3d(**FULL3)
+    return [(int(round(d[0] + 0.5 * d[3])) % 512, int(round(d[1])) % 512) for d in c.droplets[:4]]
+
+
 @pytest.fixture(scope="module", autouse=True)
 def oracle_pool():
     global _pool
-    _pool = mp.get_context("spawn").Pool(processes=len(CASES))
+    _pool = mp.get_context("spawn").Pool(processes=len(CASES) + 4)
     for name in CASES:
         _fut[name] = _pool.apply_async(oj.run3d_case, (name,))
+    for xc, yc in _win_centres():
+        _fut[("win3", xc, yc)] = _pool.apply_async(oj.window3d_run, (FULL3, xc, yc, WIN3_HALF, WIN3_STEPS))
     yield
     _pool.close()
     _pool.join()
@@ -111,6 +125,28 @@ def test_contact_angle_3d(name):
     # and against the oracle's own run: within 0.5 deg
     r = ref(name)
     assert abs(g["theta"] - r["theta"]) < 0.5
+
+
+@pytest.mark.parametrize("path", ["auto", "fused"])
+def test_full_size_box_sampled_columns(path):
+    # the benchmark's box and launch configuration (FP32), columns through
+    # the edge of four droplets compared with oracle windows of the same input
+    from paper_2312_00369_gb300 import pflbm
+    from paper_2312_00369_gb300 import workloads as wl
+    c = wl.many_droplets_3d(**FULL3)
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp32", step_path=path, **c.physical())
+    for d in c.droplets:
+        s.init_droplet(*d)
+    s.step(WIN3_STEPS)
+    s.check()
+    phi, u, p = s.get()
+    s.close()
+    for xc, yc in _win_centres():
+        r = _fut[("win3", xc, yc)].get(timeout=900)
+        assert r["phi"].max() > 0.9 and r["phi"].min() < 0.1    # the column crosses the interface
+        assert np.max(np.abs(phi[:, yc, xc] - r["phi"])) <= 1e-5
+        assert np.max(np.abs(u[:, yc, xc] - r["u"])) <= 1e-6
+        assert np.max(np.abs(p[:, yc, xc] - r["p"])) <= 1e-6
 
 
 def test_rejects_bad_mask_3d():
