@@ -47,3 +47,14 @@ def test_host_only_checks_3d():
     assert L.pflbm3d_create(ctypes.byref(h), ctypes.byref(P)) == pflbm.EINVAL
     assert L.pflbm3d_step(None, 1) == pflbm.EINVAL
     assert L.pflbm3d_mass(None, None) == pflbm.EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # no CPU fallback: without libpflbm.so every entry point raises
+    monkeypatch.setattr(pflbm, "_lib", None)
+    monkeypatch.setattr(pflbm, "LIB_PATH", str(tmp_path / "libpflbm.so"))
+    import pytest
+    with pytest.raises(RuntimeError, match="missing"):
+        pflbm.lib()
+    with pytest.raises(RuntimeError):
+        pflbm.pflbm_footprint_bytes(64, 32)
