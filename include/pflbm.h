@@ -116,8 +116,10 @@ void pflbm_params_default(pflbm_params_t* p);
 /* Create a solver from the problem statement of Sec. 3 (lattice, solid mask,
  * theta, sigma, W, M, tau_f, rho_l, rho_g), FP32 storage. Classifies the
  * nodes and computes a_v = |grad epsilon| (Eq. avvv) on the device.
- * Errors: EINVAL (sizes, parameters: W > 0, M > 0, tau_f > 1/2, densities
- * > 0, sigma >= 0), EBADMASK, ENOMEM, ECUDA. *out is NULL on failure. */
+ * Errors: EINVAL (sizes: nx >= 3, 5 <= ny <= 524280, 18 ny pitch < 2^31 with
+ * pitch = nx rounded up to 64; parameters: W > 0, M > 0, tau_f > 1/2,
+ * densities > 0, sigma >= 0), EBADMASK, ENOMEM, ECUDA. *out is NULL on
+ * failure. */
 int pflbm_create(pflbm_t** out, int nx, int ny, const uint8_t* solid_mask, double theta_deg,
                  double sigma, double W, double M, double tau_f, double rho_l, double rho_g);
 /* Same with every option (precision, tau_g, angle field, device, stream,
@@ -262,7 +264,9 @@ const char* pflbm_last_error(void);
  * Precision: PFLBM_FP64 or PFLBM_FP32 (g_0 in 32-bit fixed point as in 2D).
  * The library allocates its device memory with cudaMalloc; the state takes
  * 2 x 26 population planes of nz*ny*pitch elements (pitch = nx rounded up to
- * 64) plus 8 further planes. Error behaviour as for the 2D calls.
+ * 64) plus 8 further planes. Sizes: nx, ny >= 3, 5 <= nz <= 65535,
+ * ny <= 524280, 26 nz ny pitch < 2^31 (EINVAL otherwise). Error behaviour as
+ * for the 2D calls.
  * ------------------------------------------------------------------------ */
 typedef struct pflbm3d pflbm3d_t;
 

@@ -109,6 +109,10 @@ Sizes sizes_of(int nx, int ny, int precision)
 bool valid_params(const pflbm_params_t* p, std::string& why)
 {
     if (p->nx < 3 || p->ny < 5) { why = "nx must be >= 3 and ny >= 5"; return false; }
+    if ((p->ny + TY - 1) / TY > 65535) {
+        why = "ny too large (at most 524280 rows: one launch row of tiles per 8 rows)";
+        return false;
+    }
     if (18LL * p->ny * ((p->nx + 63) / 64 * 64) >= (1LL << 31)) {
         why = "lattice too large (18 * ny * padded nx must stay below 2^31)";
         return false;

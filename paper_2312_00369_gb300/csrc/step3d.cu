@@ -940,6 +940,8 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
     const int pitch = (p->nx + 63) / 64 * 64;
     const size_t plane = (size_t)p->nz * p->ny * pitch;
     if (26.0 * (double)plane >= 2147483647.0) return fail3(PFLBM_EINVAL, "lattice too large");
+    if (p->nz > 65535 || (p->ny + 7) / 8 > 65535)
+        return fail3(PFLBM_EINVAL, "nz must be <= 65535 and ny <= 524280 (launch grid limits)");
     const size_t pl = (size_t)p->nx * p->ny;
     for (size_t k = 0; k < pl; ++k)
         if (!p->solid_mask[k] || !p->solid_mask[pl + k] || !p->solid_mask[(p->nz - 2) * pl + k] ||

@@ -58,3 +58,26 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
         pflbm.lib()
     with pytest.raises(RuntimeError):
         pflbm.pflbm_footprint_bytes(64, 32)
+
+
+def test_sizes_beyond_the_launch_grid_are_refused():
+    # refused by the argument checks, before any CUDA call
+    import numpy as np
+    L = pflbm.lib()
+    ny = 524288 + 8
+    mask = np.ones((ny, 3), np.uint8)
+    P = pflbm.Params()
+    L.pflbm_params_default(ctypes.byref(P))
+    P.nx, P.ny = 3, ny
+    P.solid_mask = mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    h = pflbm._H()
+    assert L.pflbm_create_ex(ctypes.byref(h), ctypes.byref(P)) == pflbm.EINVAL
+    assert b"ny too large" in L.pflbm_last_error()
+    nz = 65536 + 2
+    mask3 = np.ones((nz, 3, 3), np.uint8)
+    P3 = pflbm.Params3D()
+    L.pflbm3d_params_default(ctypes.byref(P3))
+    P3.nx, P3.ny, P3.nz = 3, 3, nz
+    P3.solid_mask = mask3.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    assert L.pflbm3d_create(ctypes.byref(h), ctypes.byref(P3)) == pflbm.EINVAL
+    assert b"65535" in L.pflbm_last_error()
