@@ -35,7 +35,7 @@ def alone(req, precision):
     return th, n, m
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp32"])
 def test_served_results_equal_standalone(precision):
     from paper_2312_00369_gb300 import pflbm
     from paper_2312_00369_gb300.serve import Server
