@@ -1,13 +1,16 @@
-// step3d.cu -- the three-dimensional form of the scheme (the pflbm3d_* entry
-// points of pflbm.h): f on D3Q19 (Eq. 3ci, w = 1/3, 1/18, 1/36, c_s^2 = 1/3),
-// g on D3Q7 (the paper's matrix, w = 1/4, 1/8, c_s^2 = 1/4, Sec. 2.1.3),
-// gradients, Laplacian and a_v with the D3Q19 weights (Eqs. gradient,
-// Laplace, avvv), the 27-neighbour ghost average of Sec. 2.2.2 (b = 27).
+// step3d.cu -- kernels of the three-dimensional form of the scheme (behind
+// the pflbm3d_* entry points of capi3d.cu): f on D3Q19 (Eq. 3ci, w = 1/3,
+// 1/18, 1/36, c_s^2 = 1/3), g on D3Q7 (the paper's matrix, w = 1/4, 1/8,
+// c_s^2 = 1/4, Sec. 2.1.3), gradients, Laplacian and a_v with the D3Q19
+// weights (Eqs. gradient, Laplace, avvv), the 27-neighbour ghost average of
+// Sec. 2.2.2 (b = 27).
 //
-// A step is three kernels: (1) phi = sum of the pulled g on zeta = 1 nodes,
-// (2) ghost phi from the zeta-weighted 27-neighbour mean, (3) the fused
+// A step is either three kernels -- (1) phi = sum of the pulled g on zeta = 1
+// nodes, (2) ghost phi from the zeta-weighted 27-neighbour mean, (3) the
 // collide-and-store of f and g (pull scheme and modified bounce-back as in
-// 2D, see step.cu), which reads phi of the 18 neighbours for the stencils.
+// 2D, see step.cu), which reads phi of the 18 neighbours for the stencils --
+// or the single z-marching kernel k3_fused, which recomputes phi and the
+// ghost values in shared memory. Both call the same collide-and-store body.
 // Nodes are stored [nz][ny][pitch]; x and y are periodic, z has walls.
 #include <algorithm>
 #include <climits>
@@ -16,11 +19,9 @@
 #include <new>
 #include <string>
 
+#include "pflbm3d_internal.cuh"
 #include "storage.cuh"
 
-namespace pfk {
-int set_error(int code, const char* msg);
-}
 using namespace pfk;
 
 #ifndef PFLBM3D_STEP_MINB
@@ -741,50 +742,11 @@ __global__ void k3_sum(const double* partial, int n, double* out)
     }
 }
 
-constexpr int kMassBlocks = 1216;
 
 }  // namespace pfk3
 using namespace pfk3;
 
-// ---------------------------------------------------------------------------
-// the handle and the C ABI
-// ---------------------------------------------------------------------------
-struct pflbm3d {
-    int nx = 0, ny = 0, nz = 0, pitch = 0, precision = PFLBM_FP32, device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    Params prm{};
-    double theta = 90.0;
-    uint8_t* cls = nullptr;
-    uint8_t* solid = nullptr;
-    double* av = nullptr;
-    void* wet = nullptr;
-    void* pop[2] = {nullptr, nullptr};
-    void* sprev = nullptr;
-    void* phi = nullptr;
-    double* phi0 = nullptr;
-    double* mu0 = nullptr;
-    double* red = nullptr;
-    double* out = nullptr;
-    int* dstatus = nullptr;
-    double* pts = nullptr;      // contact-angle crossings (3 doubles each)
-    int pts_cap = 0;
-    int* ghosts = nullptr;      // indices of the ghost nodes
-    int n_ghosts = 0;
-    bool fused = true;          // one-launch step (k3_fused) or three launches
-    uint8_t* gflag = nullptr;   // [nz][tiles]: a ghost in the tile's 34 x 10 window
-    int fused_zc = 0;           // planes per CTA of the fused step
-    int cur = 0;
-    bool replace_phi = true, init_pending = false;
-    int64_t steps = 0;
-};
-
 namespace {
-
-size_t pop3_bytes(int prec, size_t plane)
-{
-    return prec == PFLBM_FP64 ? 26 * plane * 8 : 26 * plane * 4;  // g_0 plane holds its storage form
-}
 
 template <int PREC>
 Args3<PREC> make3(pflbm3d_t* h, int in)
@@ -876,353 +838,82 @@ cudaError_t mass3_prec(pflbm3d_t* h, double* d_out)
     return cudaGetLastError();
 }
 
-#define P3(call64, call32) (h->precision == PFLBM_FP64 ? (call64) : (call32))
-
-int fail3(int code, const std::string& m) { return set_error(code, m.c_str()); }
-
-#define CK3(call)                                                        \
-    do {                                                                 \
-        cudaError_t e_ = (call);                                         \
-        if (e_ != cudaSuccess) return fail3(PFLBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-int materialize3(pflbm3d_t* h)
-{
-    if (!h->init_pending) return PFLBM_OK;
-    CK3(P3(init3_prec<PFLBM_FP64>(h), init3_prec<PFLBM_FP32>(h)));
-    CK3(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
-    h->init_pending = false;
-    return PFLBM_OK;
-}
-
-void release3(pflbm3d_t* h)
-{
-    if (!h) return;
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    void* bufs[] = {h->cls, h->solid, h->av, h->wet, h->pop[0], h->pop[1], h->sprev, h->phi, h->phi0, h->mu0,
-                    h->red, h->out, h->dstatus, h->ghosts, h->gflag, h->pts};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
-    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
-    delete h;
-}
 
 }  // namespace
 
-extern "C" {
+namespace pfk3 {
 
-void pflbm3d_params_default(pflbm3d_params_t* p)
+cudaError_t launch_step(pflbm3d_t* h)
 {
-    if (!p) return;
-    std::memset(p, 0, sizeof(*p));
-    p->theta_deg = 90.0;
-    p->sigma = 0.01;
-    p->W = 4.0;
-    p->M = 0.1;
-    p->tau_f = 0.8;
-    p->rho_l = 1.0;
-    p->rho_g = 0.1;
-    p->tau_g = 1.0;
-    p->precision = PFLBM_FP32;
-    p->device = -1;
+    return h->precision == PFLBM_FP64 ? step3_prec<PFLBM_FP64>(h) : step3_prec<PFLBM_FP32>(h);
 }
 
-int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
+cudaError_t launch_macro(pflbm3d_t* h, double* phi, double* u, double* p)
 {
-    if (!out || !p) return fail3(PFLBM_EINVAL, "NULL argument");
-    *out = nullptr;
-    if (p->nx < 3 || p->ny < 3 || p->nz < 5 || !p->solid_mask) return fail3(PFLBM_EINVAL, "need nx, ny >= 3, nz >= 5 and a mask");
-    if (!(p->W > 0) || !(p->M > 0) || !(p->tau_f > 0.5) || !(p->rho_l > 0) || !(p->rho_g > 0) || !(p->sigma >= 0) ||
-        (p->tau_g > 0 && !(p->tau_g > 0.5)) || !std::isfinite(p->theta_deg))
-        return fail3(PFLBM_EINVAL, "invalid physical parameters");
-    if (p->precision != PFLBM_FP64 && p->precision != PFLBM_FP32)
-        return fail3(PFLBM_EINVAL, "3D supports PFLBM_FP64 and PFLBM_FP32");
-    const int pitch = (p->nx + 63) / 64 * 64;
-    const size_t plane = (size_t)p->nz * p->ny * pitch;
-    if (26.0 * (double)plane >= 2147483647.0) return fail3(PFLBM_EINVAL, "lattice too large");
-    if (p->nz > 65535 || (p->ny + 7) / 8 > 65535)
-        return fail3(PFLBM_EINVAL, "nz must be <= 65535 and ny <= 524280 (launch grid limits)");
-    const size_t pl = (size_t)p->nx * p->ny;
-    for (size_t k = 0; k < pl; ++k)
-        if (!p->solid_mask[k] || !p->solid_mask[pl + k] || !p->solid_mask[(p->nz - 2) * pl + k] ||
-            !p->solid_mask[(p->nz - 1) * pl + k])
-            return fail3(PFLBM_EBADMASK, "planes 0, 1, nz-2 and nz-1 of the solid mask must be solid");
-    pflbm3d_t* h = new (std::nothrow) pflbm3d();
-    if (!h) return fail3(PFLBM_ENOMEM, "host allocation failed");
-    h->nx = p->nx;
-    h->ny = p->ny;
-    h->nz = p->nz;
-    h->pitch = pitch;
-    h->precision = p->precision;
-    int dev = p->device;
-    if (dev < 0) cudaGetDevice(&dev);
-    h->device = dev;
-    cudaSetDevice(dev);
-    Params& q = h->prm;
-    q.sigma = p->sigma;
-    q.W = p->W;
-    q.M = p->M;
-    q.beta = 12.0 * p->sigma / p->W;
-    q.kappa = 1.5 * p->sigma * p->W;
-    q.tau_f = p->tau_f;
-    q.tau_g = p->tau_g > 0 ? p->tau_g : 1.0;
-    q.alpha = p->M / (0.25 * (q.tau_g - 0.5));   // Eq. mobility with the D3Q7 c_s^2 = 1/4
-    q.rho_l = p->rho_l;
-    q.rho_g = p->rho_g;
-    q.dgdt_mode = p->dgdt_mode ? 1 : 0;
-    h->theta = p->theta_deg;
-    if (p->stream) {
-        h->stream = (cudaStream_t)p->stream;
-    } else {
-        cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        h->own_stream = true;
-    }
-    const size_t cs = p->precision == PFLBM_FP64 ? 8 : 4;
-    struct B { void** ptr; size_t bytes; } bufs[] = {
-        {(void**)&h->cls, plane}, {(void**)&h->solid, plane}, {(void**)&h->av, plane * 8}, {&h->wet, plane * cs},
-        {&h->pop[0], pop3_bytes(p->precision, plane)}, {&h->pop[1], pop3_bytes(p->precision, plane)},
-        {&h->sprev, plane * cs}, {&h->phi, plane * cs}, {(void**)&h->phi0, plane * 8}, {(void**)&h->mu0, plane * 8},
-        {(void**)&h->red, (kMassBlocks + 32) * 8}, {(void**)&h->dstatus, 16}};
-    for (auto& b : bufs) {
-        if (cudaMalloc(b.ptr, b.bytes) != cudaSuccess) {
-            cudaGetLastError();
-            release3(h);
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-        }
-    }
-    cudaMemsetAsync(h->pop[0], 0, pop3_bytes(p->precision, plane), h->stream);
-    cudaMemsetAsync(h->pop[1], 0, pop3_bytes(p->precision, plane), h->stream);
-    cudaMemsetAsync(h->phi, 0, plane * cs, h->stream);
-    cudaMemsetAsync(h->phi0, 0, plane * 8, h->stream);
-    cudaMemsetAsync(h->dstatus, 0, 16, h->stream);
-    cudaMemsetAsync(h->solid, 1, plane, h->stream);
-    cudaMemcpy2DAsync(h->solid, pitch, p->solid_mask, p->nx, p->nx, (size_t)p->ny * p->nz, cudaMemcpyHostToDevice,
-                      h->stream);
+    return h->precision == PFLBM_FP64 ? macro3_prec<PFLBM_FP64>(h, phi, u, p) : macro3_prec<PFLBM_FP32>(h, phi, u, p);
+}
+
+cudaError_t launch_init(pflbm3d_t* h)
+{
+    return h->precision == PFLBM_FP64 ? init3_prec<PFLBM_FP64>(h) : init3_prec<PFLBM_FP32>(h);
+}
+
+cudaError_t launch_mass(pflbm3d_t* h, double* d_out)
+{
+    return h->precision == PFLBM_FP64 ? mass3_prec<PFLBM_FP64>(h, d_out) : mass3_prec<PFLBM_FP32>(h, d_out);
+}
+
+cudaError_t launch_geometry(pflbm3d_t* h, double wet_coef)
+{
     dim3 b(32, 8), g = grid3(h);
-    k3_cls1<<<g, b, 0, h->stream>>>(h->solid, h->cls, h->nx, h->ny, h->nz, pitch);
-    k3_cls2<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch);
-    k3_cls3<<<g, b, 0, h->stream>>>(h->cls, h->av, h->nx, h->ny, h->nz, pitch);
-    const double coef = sqrt(2.0 * q.kappa * q.beta) * cos(h->theta * 3.14159265358979323846 / 180.0);
+    k3_cls1<<<g, b, 0, h->stream>>>(h->solid, h->cls, h->nx, h->ny, h->nz, h->pitch);
+    k3_cls2<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, h->pitch);
+    k3_cls3<<<g, b, 0, h->stream>>>(h->cls, h->av, h->nx, h->ny, h->nz, h->pitch);
+    const size_t plane = (size_t)h->nz * h->ny * h->pitch;
     const unsigned nb = (unsigned)((plane + 255) / 256);
-    if (p->precision == PFLBM_FP64)
-        k3_wet<double><<<nb, 256, 0, h->stream>>>(h->av, (double*)h->wet, plane, coef);
+    if (h->precision == PFLBM_FP64)
+        k3_wet<double><<<nb, 256, 0, h->stream>>>(h->av, (double*)h->wet, plane, wet_coef);
     else
-        k3_wet<float><<<nb, 256, 0, h->stream>>>(h->av, (float*)h->wet, plane, coef);
-    // step path: the fused z-marching kernel unless asked otherwise
-    if (p->step_path != PFLBM3D_AUTO && p->step_path != PFLBM3D_FUSED && p->step_path != PFLBM3D_THREE_PASS) {
-        release3(h);
-        return fail3(PFLBM_EINVAL, "unknown step_path");
-    }
-    h->fused = p->step_path == PFLBM3D_FUSED;
-    if (h->fused) {
-        const size_t sb = p->precision == PFLBM_FP64 ? fused_smem_bytes<PFLBM_FP64>() : fused_smem_bytes<PFLBM_FP32>();
-        cudaError_t ea = p->precision == PFLBM_FP64
-            ? cudaFuncSetAttribute(k3_fused<PFLBM_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb)
-            : cudaFuncSetAttribute(k3_fused<PFLBM_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-        int per_sm = 0, sms = 0;
-        if (ea == cudaSuccess)
-            ea = p->precision == PFLBM_FP64
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fused<PFLBM_FP64>, 256, sb)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fused<PFLBM_FP32>, 256, sb);
-        if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (ea != cudaSuccess || per_sm < 1) {
-            cudaGetLastError();
-            release3(h);
-            return fail3(PFLBM_ECUDA, "fused 3D step kernel cannot be resident");
-        }
-        const long long tiles = (long long)((h->nx + TX - 1) / TX) * ((h->ny + TY - 1) / TY);
-        const int nzz = h->nz - 2;
-        int zc = p->fused_zc;
-        if (zc <= 0) {
-            // about six waves of resident CTAs, 8 to 64 planes per CTA
-            zc = (int)(((long long)nzz * tiles) / (6LL * sms * per_sm));
-            zc = zc < 8 ? 8 : (zc > 64 ? 64 : zc);
-        }
-        h->fused_zc = zc > nzz ? nzz : zc;
-        const int tiles_x = (h->nx + TX - 1) / TX;
-        if (cudaMalloc((void**)&h->gflag, (size_t)tiles * h->nz) != cudaSuccess) {
-            cudaGetLastError();
-            release3(h);
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-        }
-        k3_ghost_flags<<<dim3((unsigned)tiles, h->nz), 128, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch,
-                                                                             tiles_x, h->gflag);
-    }
-    int* cnt = h->dstatus + 1;
-    cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
-    k3_ghost_collect<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch, cnt, nullptr);
-    cudaMemcpyAsync(&h->n_ghosts, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e == cudaSuccess && h->n_ghosts > 0) {
-        if (cudaMalloc((void**)&h->ghosts, (size_t)h->n_ghosts * sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
-            release3(h);
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-        }
-        cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
-        k3_ghost_collect<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, pitch, cnt, h->ghosts);
-        cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
-        e = cudaStreamSynchronize(h->stream);
-    }
-    if (e != cudaSuccess) {
-        release3(h);
-        return fail3(PFLBM_ECUDA, cudaGetErrorString(e));
-    }
-    *out = h;
-    return PFLBM_OK;
+        k3_wet<float><<<nb, 256, 0, h->stream>>>(h->av, (float*)h->wet, plane, wet_coef);
+    return cudaGetLastError();
 }
 
-void pflbm3d_destroy(pflbm3d_t* h) { release3(h); }
-
-int pflbm3d_init_droplet(pflbm3d_t* h, double x0, double y0, double z0, double R)
+cudaError_t launch_ghost_collect(pflbm3d_t* h, int* count, int* list)
 {
-    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
-    if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(z0) || !std::isfinite(R))
-        return fail3(PFLBM_EINVAL, "non-finite droplet");
-    if (h->replace_phi) CK3(cudaMemsetAsync(h->phi0, 0, (size_t)h->nz * h->ny * h->pitch * 8, h->stream));
-    const double reach = fabs(R) + 10.0 * h->prm.W;
-    auto span = [&](double c, int n, int& lo, int& w) {
-        lo = 0;
-        w = n;
-        if (2.0 * reach + 2.0 < n && fabs(c) < 1e8) {
-            lo = (int)floor(c - reach);
-            w = (int)(ceil(c + reach) - floor(c - reach)) + 1;
-        }
-    };
-    int xlo, xw, ylo, yw;
-    span(x0, h->nx, xlo, xw);
-    span(y0, h->ny, ylo, yw);
-    const int zlo = (int)fmin((double)h->nz, fmax(0.0, floor(z0 - reach)));
-    const int zhi = (int)fmax(-1.0, fmin((double)h->nz - 1, ceil(z0 + reach)));
-    if (zlo <= zhi) {
-        dim3 b(32, 8), g((xw + 31) / 32, (yw + 7) / 8, zhi - zlo + 1);
-        k3_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yw, zlo, x0, y0,
-                                           z0, R, h->prm.W);
-        CK3(cudaGetLastError());
-    }
-    h->replace_phi = false;
-    h->init_pending = true;
-    h->steps = 0;
-    return PFLBM_OK;
+    dim3 b(32, 8), g = grid3(h);
+    k3_ghost_collect<<<g, b, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, h->pitch, count, list);
+    return cudaGetLastError();
 }
 
-int pflbm3d_init_phi(pflbm3d_t* h, const double* phi)
+cudaError_t launch_ghost_flags(pflbm3d_t* h)
 {
-    if (!h || !phi) return fail3(PFLBM_EINVAL, "NULL argument");
-    CK3(cudaMemcpy2DAsync(h->phi0, h->pitch * 8, phi, h->nx * 8, h->nx * 8, (size_t)h->ny * h->nz,
-                          cudaMemcpyHostToDevice, h->stream));
-    CK3(cudaStreamSynchronize(h->stream));
-    h->replace_phi = false;
-    h->init_pending = true;
-    h->steps = 0;
-    return PFLBM_OK;
+    const int tiles_x = (h->nx + TX - 1) / TX;
+    const long long tiles = (long long)tiles_x * ((h->ny + TY - 1) / TY);
+    k3_ghost_flags<<<dim3((unsigned)tiles, h->nz), 128, 0, h->stream>>>(h->cls, h->nx, h->ny, h->nz, h->pitch,
+                                                                         tiles_x, h->gflag);
+    return cudaGetLastError();
 }
 
-int pflbm3d_step(pflbm3d_t* h, int64_t n)
+cudaError_t launch_droplet(pflbm3d_t* h, int xlo, int xw, int ylo, int yw, int zlo, int zn, double x0, double y0,
+                           double z0, double R)
 {
-    if (!h || n < 0) return fail3(PFLBM_EINVAL, "invalid arguments");
-    if (int rc = materialize3(h)) return rc;
-    for (int64_t t = 0; t < n; ++t) {
-        CK3(P3(step3_prec<PFLBM_FP64>(h), step3_prec<PFLBM_FP32>(h)));
-        h->cur ^= 1;
-        h->steps += 1;
-    }
-    if (n > 0) h->replace_phi = true;
-    return PFLBM_OK;
+    dim3 b(32, 8), g((xw + 31) / 32, (yw + 7) / 8, zn);
+    k3_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yw, zlo, x0, y0, z0, R,
+                                       h->prm.W);
+    return cudaGetLastError();
 }
 
-int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p)
+cudaError_t fused_setup(int precision, size_t* smem_bytes, int* ctas_per_sm)
 {
-    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
-    if (int rc = materialize3(h)) return rc;
-    const size_t N = (size_t)h->nx * h->ny * h->nz;
-    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        h->out = nullptr;
-        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-    }
-    double *dphi = h->out, *du = h->out + N, *dp = h->out + 4 * N;
-    CK3(P3(macro3_prec<PFLBM_FP64>(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr),
-           macro3_prec<PFLBM_FP32>(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr)));
-    if (phi) CK3(cudaMemcpyAsync(phi, dphi, N * 8, cudaMemcpyDeviceToHost, h->stream));
-    if (u) CK3(cudaMemcpyAsync(u, du, 3 * N * 8, cudaMemcpyDeviceToHost, h->stream));
-    if (p) CK3(cudaMemcpyAsync(p, dp, N * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK3(cudaStreamSynchronize(h->stream));
-    return PFLBM_OK;
+    const size_t sb = precision == PFLBM_FP64 ? fused_smem_bytes<PFLBM_FP64>() : fused_smem_bytes<PFLBM_FP32>();
+    cudaError_t e = precision == PFLBM_FP64
+        ? cudaFuncSetAttribute(k3_fused<PFLBM_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb)
+        : cudaFuncSetAttribute(k3_fused<PFLBM_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    if (e != cudaSuccess) return e;
+    *smem_bytes = sb;
+    return precision == PFLBM_FP64
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k3_fused<PFLBM_FP64>, 256, sb)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k3_fused<PFLBM_FP32>, 256, sb);
 }
 
-int pflbm3d_mass(pflbm3d_t* h, double* out)
-{
-    if (!h || !out) return fail3(PFLBM_EINVAL, "NULL argument");
-    if (int rc = materialize3(h)) return rc;
-    double* d = h->red + kMassBlocks + 4;
-    CK3(P3(mass3_prec<PFLBM_FP64>(h, d), mass3_prec<PFLBM_FP32>(h, d)));
-    CK3(cudaMemcpyAsync(out, d, 8, cudaMemcpyDeviceToHost, h->stream));
-    CK3(cudaStreamSynchronize(h->stream));
-    return PFLBM_OK;
-}
-
-int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av)
-{
-    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
-    if (cls) {
-        CK3(cudaMemcpy2DAsync(cls, h->nx, h->cls, h->pitch, h->nx, (size_t)h->ny * h->nz, cudaMemcpyDeviceToHost,
-                              h->stream));
-        CK3(cudaStreamSynchronize(h->stream));
-        for (size_t k = 0; k < (size_t)h->nx * h->ny * h->nz; ++k) cls[k] &= CLS_MASK;
-    }
-    if (av)
-        CK3(cudaMemcpy2DAsync(av, h->nx * 8, h->av, h->pitch * 8, h->nx * 8, (size_t)h->ny * h->nz,
-                              cudaMemcpyDeviceToHost, h->stream));
-    CK3(cudaStreamSynchronize(h->stream));
-    return PFLBM_OK;
-}
-
-int pflbm3d_contact_angle(pflbm3d_t* h, const pflbm3d_wall_t* wall, double* theta_deg, double* sphere, int* npoints)
-{
-    if (!h || !wall || !theta_deg) return fail3(PFLBM_EINVAL, "NULL argument");
-    if (wall->type != 0 && wall->type != 1) return fail3(PFLBM_EINVAL, "wall type must be 0 or 1");
-    if (int rc = materialize3(h)) return rc;
-    const size_t N = (size_t)h->nx * h->ny * h->nz;
-    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        h->out = nullptr;
-        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-    }
-    if (!h->pts) {
-        const long long cap = std::min<long long>(3LL * (long long)N, 1LL << 22);
-        if (cudaMalloc((void**)&h->pts, (size_t)cap * 3 * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            h->pts = nullptr;
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-        }
-        h->pts_cap = (int)cap;
-    }
-    double* dphi = h->out;
-    CK3(P3(macro3_prec<PFLBM_FP64>(h, dphi, nullptr, nullptr), macro3_prec<PFLBM_FP32>(h, dphi, nullptr, nullptr)));
-    Wall3 w{wall->type, {wall->px, wall->py, wall->pz}, {wall->nx, wall->ny, wall->nz}, wall->r,
-            wall->x_lo, wall->x_hi, wall->y_lo, wall->y_hi, wall->exclude};
-    int* d_count = (int*)(h->red + kMassBlocks + 8);
-    double* d_res = h->red + kMassBlocks + 16;
-    CK3(launch_contact_angle3d(h->cls, dphi, h->nx, h->ny, h->nz, h->pitch, w, h->pts, h->pts_cap, d_count, d_res,
-                               h->stream));
-    double res[6];
-    CK3(cudaMemcpyAsync(res, d_res, sizeof(res), cudaMemcpyDeviceToHost, h->stream));
-    CK3(cudaStreamSynchronize(h->stream));
-    *theta_deg = res[0];
-    if (sphere)
-        for (int i = 0; i < 4; ++i) sphere[i] = res[1 + i];
-    if (npoints) *npoints = (int)res[5];
-    return PFLBM_OK;
-}
-
-int pflbm3d_check(pflbm3d_t* h)
-{
-    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
-    CK3(cudaStreamSynchronize(h->stream));
-    int st = 0;
-    CK3(cudaMemcpy(&st, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
-    return st ? fail3(PFLBM_ENUMERIC, "NaN or |u| >= 0.3 detected on the device") : PFLBM_OK;
-}
-
-}  // extern "C"
+}  // namespace pfk3
