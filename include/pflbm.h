@@ -312,6 +312,15 @@ int pflbm3d_mass(pflbm3d_t* h, double* out);
 int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av);
 /* Waits for the stream; PFLBM_ENUMERIC if a NaN or |u| >= 0.3 was seen. */
 int pflbm3d_check(pflbm3d_t* h);
+/* Steps taken since the last initialisation (-1 for a NULL handle). */
+int64_t pflbm3d_steps(const pflbm3d_t* h);
+/* Checkpoint of the state (populations, u.grad(phi) history, step count)
+ * into a caller buffer; buf == NULL returns the size in *len. pflbm3d_load
+ * restores it into a handle of the same size and precision, after which the
+ * steps continue bit for bit as if uninterrupted. Synchronous. Errors:
+ * EINVAL (buffer too small, not a checkpoint, size or precision differs). */
+int pflbm3d_save(pflbm3d_t* h, void* buf, size_t* len);
+int pflbm3d_load(pflbm3d_t* h, const void* buf, size_t len);
 
 /* Wall for the 3D contact-angle fit. type 0: the plane through (px, py, pz)
  * with unit normal (nx, ny, nz) pointing into the fluid; type 1: a solid

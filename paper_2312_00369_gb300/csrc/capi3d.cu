@@ -342,6 +342,74 @@ int pflbm3d_contact_angle(pflbm3d_t* h, const pflbm3d_wall_t* wall, double* thet
     return PFLBM_OK;
 }
 
+namespace {
+constexpr uint64_t kMagic3 = 0x33444d424c46504bULL;   // checkpoint tag of the 3D state
+struct Blob3 {
+    uint64_t magic;
+    int32_t version, nx, ny, nz, precision, replace_phi;
+    int64_t steps;
+    double params[10];
+};
+size_t sprev3_bytes(const pflbm3d_t* h)
+{
+    return (size_t)h->nz * h->ny * h->pitch * (h->precision == PFLBM_FP64 ? 8 : 4);
+}
+}  // namespace
+
+int pflbm3d_save(pflbm3d_t* h, void* buf, size_t* len)
+{
+    if (!h || !len) return fail3(PFLBM_EINVAL, "NULL argument");
+    const size_t plane = (size_t)h->nz * h->ny * h->pitch;
+    const size_t pop = pop3_bytes(h->precision, plane), sp = sprev3_bytes(h);
+    const size_t need = sizeof(Blob3) + pop + sp;
+    if (!buf) { *len = need; return PFLBM_OK; }
+    if (*len < need) { *len = need; return fail3(PFLBM_EINVAL, "buffer too small"); }
+    if (int rc = materialize3(h)) return rc;
+    Blob3 b{};
+    b.magic = kMagic3;
+    b.version = 1;
+    b.nx = h->nx;
+    b.ny = h->ny;
+    b.nz = h->nz;
+    b.precision = h->precision;
+    b.replace_phi = h->replace_phi;
+    b.steps = h->steps;
+    const Params& q = h->prm;
+    const double pv[10] = {q.beta, q.kappa, q.alpha, q.tau_f, q.tau_g, q.rho_l, q.rho_g, q.W, q.sigma, q.M};
+    std::memcpy(b.params, pv, sizeof(pv));
+    std::memcpy(buf, &b, sizeof(b));
+    char* dst = (char*)buf + sizeof(Blob3);
+    CK3(cudaMemcpyAsync(dst, h->pop[h->cur], pop, cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaMemcpyAsync(dst + pop, h->sprev, sp, cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    *len = need;
+    return PFLBM_OK;
+}
+
+int pflbm3d_load(pflbm3d_t* h, const void* buf, size_t len)
+{
+    if (!h || !buf || len < sizeof(Blob3)) return fail3(PFLBM_EINVAL, "blob too small");
+    Blob3 b;
+    std::memcpy(&b, buf, sizeof(b));
+    if (b.magic != kMagic3 || b.version != 1) return fail3(PFLBM_EINVAL, "not a pflbm3d checkpoint");
+    if (b.nx != h->nx || b.ny != h->ny || b.nz != h->nz || b.precision != h->precision)
+        return fail3(PFLBM_EINVAL, "checkpoint size or precision differs from the handle");
+    const size_t plane = (size_t)h->nz * h->ny * h->pitch;
+    const size_t pop = pop3_bytes(h->precision, plane), sp = sprev3_bytes(h);
+    if (len < sizeof(Blob3) + pop + sp) return fail3(PFLBM_EINVAL, "blob truncated");
+    const char* src = (const char*)buf + sizeof(Blob3);
+    CK3(cudaMemcpyAsync(h->pop[h->cur], src, pop, cudaMemcpyHostToDevice, h->stream));
+    CK3(cudaMemcpyAsync(h->sprev, src + pop, sp, cudaMemcpyHostToDevice, h->stream));
+    CK3(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    h->init_pending = false;
+    h->steps = b.steps;
+    h->replace_phi = b.replace_phi != 0;
+    return PFLBM_OK;
+}
+
+int64_t pflbm3d_steps(const pflbm3d_t* h) { return h ? h->steps : -1; }
+
 int pflbm3d_check(pflbm3d_t* h)
 {
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");

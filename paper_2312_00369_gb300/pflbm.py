@@ -145,6 +145,9 @@ _SIGS = {
     "pflbm3d_geometry": (ctypes.c_int, [_H, _u8p, _dp]),
     "pflbm3d_check": (ctypes.c_int, [_H]),
     "pflbm3d_contact_angle": (ctypes.c_int, [_H, ctypes.POINTER(Wall3D), _dp, _dp, _ip]),
+    "pflbm3d_steps": (ctypes.c_int64, [_H]),
+    "pflbm3d_save": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "pflbm3d_load": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
 }
 
 
@@ -530,6 +533,21 @@ class Solver3D:
 
     def check(self):
         _check(lib().pflbm3d_check(self._h))
+
+    @property
+    def steps(self):
+        return lib().pflbm3d_steps(self._h)
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t()
+        _check(lib().pflbm3d_save(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().pflbm3d_save(self._h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().pflbm3d_load(self._h, buf, len(blob)))
 
     def contact_angle(self, wall: dict, exclude=None):
         """``wall``: dict(type=0, p=(x, y, z), n=(nx, ny, nz)) for a plane or

@@ -149,6 +149,35 @@ def test_full_size_box_sampled_columns(path):
         assert np.max(np.abs(p[:, yc, xc] - r["p"])) <= 1e-6
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_3d(precision):
+    # save after 25 steps, run 30 more; a fresh handle loaded from the
+    # checkpoint runs the same 30 steps to the same state, bit for bit
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.case3d_by_name("sphere3d")
+    mk = lambda: pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision=precision, **c.physical())
+    a = mk()
+    for d in c.droplets:
+        a.init_droplet(*d)
+    a.step(25)
+    blob = a.save()
+    a.step(30)
+    b = mk()
+    b.load(blob)
+    assert b.steps == 25
+    b.step(30)
+    for x, y in zip(a.get(), b.get()):
+        assert np.array_equal(x, y)
+    assert a.mass() == b.mass() and b.steps == 55
+    # a checkpoint of another size is refused
+    s2, _ = __import__("paper_2312_00369_gb300.workloads", fromlist=["box3d"]).box3d(40, 20, 20)
+    other = pflbm.Solver3D(s2, precision=precision)
+    with pytest.raises(pflbm.PflbmError):
+        other.load(blob)
+    for s in (a, b, other):
+        s.close()
+
+
 def test_rejects_bad_mask_3d():
     from paper_2312_00369_gb300 import pflbm
     s = np.zeros((12, 8, 8), np.uint8)
