@@ -44,7 +44,7 @@ enum pflbm_status {
     PFLBM_ENOMEM = -2,   /* device allocation failed                         */
     PFLBM_EBADMASK = -3, /* rows 0, 1, ny-2, ny-1 of the mask are not solid  */
     PFLBM_ENUMERIC = -4, /* NaN or |u| >= 0.3 seen on the device             */
-    PFLBM_ETIMEOUT = -5, /* a bounded device wait gave up                    */
+    PFLBM_ETIMEOUT = -5, /* reserved: no kernel of this library waits on another */
     PFLBM_ECUDA = -6     /* a CUDA runtime call failed                       */
 };
 
