@@ -701,8 +701,11 @@ def main():
     if case.theta_field is not None:
         theta_h = pinned(torch, case.theta_field.shape, np.float32)
         theta_h[...] = case.theta_field
-    outs = (pinned(torch, (case.ny, case.nx), np.float64), pinned(torch, (case.ny, case.nx, 2), np.float64),
-            pinned(torch, (case.ny, case.nx), np.float64))
+    # read-back in the solve's own precision class: float64 for FP64 solves,
+    # float32 (pflbm_get_f32) for FP32 and 16-bit solves
+    rb = np.float64 if args.precision == "fp64" else np.float32
+    outs = (pinned(torch, (case.ny, case.nx), rb), pinned(torch, (case.ny, case.nx, 2), rb),
+            pinned(torch, (case.ny, case.nx), rb))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -713,7 +716,7 @@ def main():
         for d in case.droplets:
             s2.init_droplet(*d)
         s2.step(e2e_steps)
-        phi, u, p = s2.get(out=outs)
+        phi, u, p = s2.get(out=outs) if rb is np.float64 else s2.get_f32(out=outs)
         s2.close()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -745,7 +748,8 @@ def main():
             "e2e": {"value": whole_job_mlups(world, N, e2e_steps, e2e_s), "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
                     "steps_per_solve": e2e_steps,
-                    "includes": "create (mask upload, geometry), droplet init, steps, get",
+                    "includes": "create (mask upload, geometry), droplet init, steps, get (float64 for "
+                                "FP64 solves, float32 otherwise)",
                     "host_buffers": "pinned"},
             "gpu_launches": args.steps,
             "clocks": clocks,

@@ -152,6 +152,9 @@ int pflbm_step(pflbm_t* h, int64_t n);
  * p [ny][nx] (u = p = 0 on zeta = 0 nodes). Any pointer may be NULL.
  * Caller-owned host buffers. */
 int pflbm_get(pflbm_t* h, double* phi, double* u, double* p);
+/* The same fields rounded to float (round to nearest), for callers that
+ * read back FP32 or 16-bit solves: half the bytes of pflbm_get. */
+int pflbm_get_f32(pflbm_t* h, float* phi, float* u, float* p);
 /* Same into caller-owned DEVICE buffers (no host copy, asynchronous). */
 int pflbm_get_device(pflbm_t* h, double* phi, double* u, double* p);
 

@@ -2,6 +2,7 @@
 // documented in include/pflbm.h): argument checks, device memory, streams,
 // error codes. Every computation runs in the kernels of geometry.cu, step.cu
 // and diag.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -159,6 +160,7 @@ void release(pflbm_t* h)
     dfree(h, h->red, s.red);
     dfree(h, h->pts, s.pts);
     dfree(h, h->out, h->out_bytes);
+    if (h->out_f) dfree(h, h->out_f, (size_t)h->nx * h->ny * 4 * sizeof(float));
     dfree(h, h->dstatus, sizeof(int) * 4);
     if (h->hstatus) cudaFreeHost(h->hstatus);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -206,6 +208,12 @@ int ensure_out(pflbm_t* h)
     h->out = (double*)p;
     h->out_bytes = bytes;
     return PFLBM_OK;
+}
+
+__global__ void k_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 }  // namespace
@@ -483,6 +491,32 @@ int pflbm_get(pflbm_t* h, double* phi, double* u, double* p)
     if (phi) CK(cudaMemcpyAsync(phi, dphi, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (u) CK(cudaMemcpyAsync(u, du, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (p) CK(cudaMemcpyAsync(p, dp, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
+int pflbm_get_f32(pflbm_t* h, float* phi, float* u, float* p)
+{
+    if (int rc = check_handle(h)) return rc;
+    DeviceGuard g(h->device);
+    if (int rc = materialize(h)) return rc;
+    if (int rc = ensure_out(h)) return rc;
+    size_t N = (size_t)h->nx * h->ny;
+    if (!h->out_f) {
+        void* q = nullptr;
+        if (int rc = dalloc(h, &q, 4 * N * sizeof(float))) return rc;
+        h->out_f = (float*)q;
+    }
+    double* dphi = h->out;
+    double* du = h->out + N;
+    double* dp = h->out + 3 * N;
+    CK(launch_macro(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr));
+    // the dense fields are contiguous (phi, u, p at offsets 0, N, 3N): one conversion
+    k_to_float<<<(unsigned)std::min<size_t>((4 * N + 255) / 256, 4096), 256, 0, h->stream>>>(h->out, h->out_f, 4 * N);
+    CK(cudaGetLastError());
+    if (phi) CK(cudaMemcpyAsync(phi, h->out_f, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK(cudaMemcpyAsync(u, h->out_f + N, 2 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (p) CK(cudaMemcpyAsync(p, h->out_f + 3 * N, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return read_status(h);
 }

@@ -118,6 +118,7 @@ struct pflbm {
     int pts_cap = 0;
     double* out = nullptr;        // read-back scratch (4 dense [ny][nx] doubles)
     size_t out_bytes = 0;
+    float* out_f = nullptr;       // FP32 read-back scratch (4 dense [ny][nx] floats), on first use
     int* dstatus = nullptr;       // device status word
     int* hstatus = nullptr;       // pinned host mirror
     int cur = 0;                  // which pop buffer holds the current state

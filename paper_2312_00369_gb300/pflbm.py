@@ -114,6 +114,7 @@ _SIGS = {
     "pflbm_step": (ctypes.c_int, [_H, ctypes.c_int64]),
     "pflbm_get": (ctypes.c_int, [_H, _dp, _dp, _dp]),
     "pflbm_get_device": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pflbm_get_f32": (ctypes.c_int, [_H, _fp, _fp, _fp]),
     "pflbm_mass": (ctypes.c_int, [_H, _dp]),
     "pflbm_phi_mass_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -335,6 +336,18 @@ class Solver:
             if a.shape != shp or a.dtype != np.float64 or not a.flags.c_contiguous:
                 raise ValueError(f"output array must be C-contiguous float64 {shp}")
         _check(lib().pflbm_get(self._h, _p(phi), _p(u), _p(p)))
+        return phi, u, p
+
+    def get_f32(self, out=None):
+        """As get(), rounded to float32 on the device (half the bytes)."""
+        shapes = ((self.ny, self.nx), (self.ny, self.nx, 2), (self.ny, self.nx))
+        if out is None:
+            out = tuple(np.empty(sh, np.float32) for sh in shapes)
+        for a, sh in zip(out, shapes):
+            if a.shape != sh or a.dtype != np.float32 or not a.flags.c_contiguous:
+                raise ValueError(f"output array must be C-contiguous float32 {sh}")
+        phi, u, p = out
+        _check(lib().pflbm_get_f32(self._h, _p(phi, _fp), _p(u, _fp), _p(p, _fp)))
         return phi, u, p
 
     def get_device(self, phi=None, u=None, p=None):

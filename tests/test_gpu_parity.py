@@ -156,6 +156,21 @@ def test_full_size_many_droplets_sampled_columns():
         assert np.max(np.abs(p[:, x] - r["p"])) <= 1e-6
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_get_f32_is_get_rounded(precision):
+    # the FP32 read-back is the FP64 one rounded to nearest, element by element
+    case = oj.case_by_name("incline45_ragged")
+    s = solver(case, precision)
+    s.step(37)
+    phi, u, p = s.get()
+    pf, uf, qf = s.get_f32()
+    s.close()
+    assert pf.dtype == np.float32
+    assert np.array_equal(pf, phi.astype(np.float32))
+    assert np.array_equal(uf, u.astype(np.float32))
+    assert np.array_equal(qf, p.astype(np.float32))
+
+
 # ---------------------------------------------------------- diagnostics --
 def test_mass_and_contact_angle_fp64():
     case = oj.case_by_name("flat60")
