@@ -550,8 +550,8 @@ def run_3d(args, torch, rank, world, local):
     e2e_steps = args.e2e_steps
     solid_h = pinned(torch, case.solid.shape, np.uint8)
     solid_h[...] = case.solid
-    outs = (pinned(torch, case.shape, np.float64), pinned(torch, case.shape + (3,), np.float64),
-            pinned(torch, case.shape, np.float64))
+    rb = np.float64 if prec == "fp64" else np.float32
+    outs = (pinned(torch, case.shape, rb), pinned(torch, case.shape + (3,), rb), pinned(torch, case.shape, rb))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -560,7 +560,7 @@ def run_3d(args, torch, rank, world, local):
         for d in case.droplets:
             s2.init_droplet(*d)
         s2.step(e2e_steps)
-        phi, u, p = s2.get(out=outs)
+        phi, u, p = s2.get(out=outs) if rb is np.float64 else s2.get_f32(out=outs)
         s2.close()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -589,7 +589,8 @@ def run_3d(args, torch, rank, world, local):
                     "h2d_bytes_per_step": case.solid.nbytes / e2e_steps,
                     "d2h_bytes_per_step": (phi.nbytes + u.nbytes + p.nbytes) / e2e_steps,
                     "steps_per_solve": e2e_steps,
-                    "includes": "create (mask upload, geometry), droplet init, steps, get",
+                    "includes": "create (mask upload, geometry), droplet init, steps, get (float64 for "
+                                "FP64 solves, float32 otherwise)",
                     "host_buffers": "pinned"},
             "gpu_launches": (1 if args.path3d == "fused" else 3) * args.steps,
             "clocks": clocks,

@@ -308,6 +308,8 @@ int pflbm3d_step(pflbm3d_t* h, int64_t n);
 /* phi [N] (ghost values on ghost nodes, 0 inside the solid), u [N][3] and p
  * [N] (0 off zeta = 1 nodes) into host arrays; any may be NULL. Synchronous. */
 int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p);
+/* The same fields rounded to float (round to nearest): half the bytes. */
+int pflbm3d_get_f32(pflbm3d_t* h, float* phi, float* u, float* p);
 /* sum of the g_i over zeta = 1 nodes, FP64, fixed order. Synchronous. */
 int pflbm3d_mass(pflbm3d_t* h, double* out);
 /* node classes (pflbm_node_class) and a_v into host arrays [N]; either may

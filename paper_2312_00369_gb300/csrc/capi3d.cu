@@ -19,6 +19,12 @@ using namespace pfk3;
 
 namespace {
 
+__global__ void k3_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
 size_t pop3_bytes(int prec, size_t plane)
 {
     return prec == PFLBM_FP64 ? 26 * plane * 8 : 26 * plane * 4;  // g_0 plane holds its storage form
@@ -46,7 +52,7 @@ void release3(pflbm3d_t* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* bufs[] = {h->cls, h->solid, h->av, h->wet, h->pop[0], h->pop[1], h->sprev, h->phi, h->phi0, h->mu0,
-                    h->red, h->out, h->dstatus, h->ghosts, h->gflag, h->pts};
+                    h->red, h->out, h->dstatus, h->ghosts, h->gflag, h->pts, h->out_f};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -273,6 +279,32 @@ int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p)
     if (phi) CK3(cudaMemcpyAsync(phi, dphi, N * 8, cudaMemcpyDeviceToHost, h->stream));
     if (u) CK3(cudaMemcpyAsync(u, du, 3 * N * 8, cudaMemcpyDeviceToHost, h->stream));
     if (p) CK3(cudaMemcpyAsync(p, dp, N * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    return PFLBM_OK;
+}
+
+int pflbm3d_get_f32(pflbm3d_t* h, float* phi, float* u, float* p)
+{
+    if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    if (int rc = materialize3(h)) return rc;
+    const size_t N = (size_t)h->nx * h->ny * h->nz;
+    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        h->out = nullptr;
+        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+    }
+    if (!h->out_f && cudaMalloc((void**)&h->out_f, N * 5 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        h->out_f = nullptr;
+        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+    }
+    double *dphi = h->out, *du = h->out + N, *dp = h->out + 4 * N;
+    CK3(launch_macro(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr));
+    k3_to_float<<<(unsigned)std::min<size_t>((5 * N + 255) / 256, 4096), 256, 0, h->stream>>>(h->out, h->out_f, 5 * N);
+    CK3(cudaGetLastError());
+    if (phi) CK3(cudaMemcpyAsync(phi, h->out_f, N * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK3(cudaMemcpyAsync(u, h->out_f + N, 3 * N * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (p) CK3(cudaMemcpyAsync(p, h->out_f + 4 * N, N * 4, cudaMemcpyDeviceToHost, h->stream));
     CK3(cudaStreamSynchronize(h->stream));
     return PFLBM_OK;
 }

@@ -22,6 +22,7 @@ struct pflbm3d {
     double* mu0 = nullptr;
     double* red = nullptr;
     double* out = nullptr;
+    float* out_f = nullptr;     // FP32 read-back scratch (5 dense fields), on first use
     int* dstatus = nullptr;
     double* pts = nullptr;      // contact-angle crossings (3 doubles each)
     int pts_cap = 0;

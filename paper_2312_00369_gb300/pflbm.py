@@ -142,6 +142,7 @@ _SIGS = {
     "pflbm3d_init_phi": (ctypes.c_int, [_H, _dp]),
     "pflbm3d_step": (ctypes.c_int, [_H, ctypes.c_int64]),
     "pflbm3d_get": (ctypes.c_int, [_H, _dp, _dp, _dp]),
+    "pflbm3d_get_f32": (ctypes.c_int, [_H, _fp, _fp, _fp]),
     "pflbm3d_mass": (ctypes.c_int, [_H, _dp]),
     "pflbm3d_geometry": (ctypes.c_int, [_H, _u8p, _dp]),
     "pflbm3d_check": (ctypes.c_int, [_H]),
@@ -531,6 +532,19 @@ class Solver3D:
             if a.shape != sh or a.dtype != np.float64 or not a.flags.c_contiguous:
                 raise ValueError(f"output array must be C-contiguous float64 {sh}")
         _check(lib().pflbm3d_get(self._h, _p(phi), _p(u), _p(p)))
+        return phi, u, p
+
+    def get_f32(self, out=None):
+        """As get(), rounded to float32 on the device (half the bytes)."""
+        shp = (self.nz, self.ny, self.nx)
+        shapes = (shp, shp + (3,), shp)
+        if out is None:
+            out = tuple(np.empty(sh, np.float32) for sh in shapes)
+        for a, sh in zip(out, shapes):
+            if a.shape != sh or a.dtype != np.float32 or not a.flags.c_contiguous:
+                raise ValueError(f"output array must be C-contiguous float32 {sh}")
+        phi, u, p = out
+        _check(lib().pflbm3d_get_f32(self._h, _p(phi, _fp), _p(u, _fp), _p(p, _fp)))
         return phi, u, p
 
     def mass(self):

@@ -178,6 +178,20 @@ def test_checkpoint_resume_3d(precision):
         s.close()
 
 
+def test_get_f32_is_get_rounded_3d():
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.case3d_by_name("sphere3d")
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp32", **c.physical())
+    for d in c.droplets:
+        s.init_droplet(*d)
+    s.step(20)
+    full = s.get()
+    low = s.get_f32()
+    s.close()
+    for a, b in zip(full, low):
+        assert b.dtype == np.float32 and np.array_equal(b, a.astype(np.float32))
+
+
 def test_rejects_bad_mask_3d():
     from paper_2312_00369_gb300 import pflbm
     s = np.zeros((12, 8, 8), np.uint8)
