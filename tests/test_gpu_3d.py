@@ -192,6 +192,37 @@ def test_get_f32_is_get_rounded_3d():
         assert b.dtype == np.float32 and np.array_equal(b, a.astype(np.float32))
 
 
+def test_init_phi_and_edge_cases_3d():
+    # a general initial field (init_phi) against the oracle; step(0) is a
+    # no-op; a lattice without liquid stays exactly at rest
+    import oracle
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.case3d_by_name("incline3d")
+    z, y, x = np.mgrid[0:c.shape[0], 0:c.shape[1], 0:c.shape[2]]
+    phi0 = 0.5 + 0.5 * np.tanh(2 * (6.0 - np.sqrt((x - 17.3) ** 2 + (y - 9.6) ** 2 + (z - 15.1) ** 2)) / 4.0)
+    phi0 = np.maximum(phi0, 0.5 + 0.5 * np.tanh((z - 33.0) / 2.0))      # plus a liquid layer near the top
+    o = oracle.Oracle3D(c.solid, theta_deg=c.theta_deg, **c.physical())
+    o.init_phi(phi0)
+    o.step(60)
+    r = o.get()
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp64", **c.physical())
+    s.init_phi(phi0)
+    before = s.get()
+    s.step(0)
+    assert s.steps == 0 and all(np.array_equal(a, b) for a, b in zip(before, s.get()))
+    s.step(60)
+    g = s.get()
+    s.close()
+    assert np.max(np.abs(g[0] - r[0])) <= 1e-10 and np.max(np.abs(g[1] - r[1])) <= 1e-12
+    e = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp32", **c.physical())
+    e.init_phi(np.zeros(c.shape))
+    e.step(50)
+    e.check()
+    phi, u, p = e.get()
+    assert np.all(phi == 0) and np.all(u == 0) and np.all(p == 0) and e.mass() == 0.0
+    e.close()
+
+
 def test_rejects_bad_mask_3d():
     from paper_2312_00369_gb300 import pflbm
     s = np.zeros((12, 8, 8), np.uint8)

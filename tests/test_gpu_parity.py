@@ -171,6 +171,24 @@ def test_get_f32_is_get_rounded(precision):
     assert np.array_equal(qf, p.astype(np.float32))
 
 
+def test_edge_cases_2d():
+    # step(0) is a no-op; a lattice without liquid stays exactly at rest
+    case = oj.case_by_name("incline45_ragged")
+    s = solver(case, "fp32")
+    before = s.get()
+    s.step(0)
+    assert all(np.array_equal(a, b) for a, b in zip(before, s.get()))
+    s.close()
+    from paper_2312_00369_gb300.pflbm import Solver
+    e = Solver(case.solid, theta_deg=case.theta_deg, precision="fp32", **case.physical())
+    e.init_phi(np.zeros(case.solid.shape))
+    e.step(50)
+    e.check()
+    phi, u, p = e.get()
+    assert np.all(phi == 0) and np.all(u == 0) and np.all(p == 0) and e.mass() == 0.0
+    e.close()
+
+
 # ---------------------------------------------------------- diagnostics --
 def test_mass_and_contact_angle_fp64():
     case = oj.case_by_name("flat60")
