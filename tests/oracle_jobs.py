@@ -197,3 +197,38 @@ def window3d_run(full_kwargs, xc, yc, half, steps):
     o.step(steps)
     phi, u, p = o.get()
     return dict(phi=phi[:, half, half], u=u[:, half, half], p=p[:, half, half])
+
+
+# ---- the largest 2D lattice the library accepts ------------------------------
+
+MAX2D = dict(nx=16384, ny=7280)           # 18 * ny * pitch = 2146959360 < 2^31
+
+
+def max2d_case():
+    """Flat channel of the largest accepted size with a droplet hanging from
+    the top wall at the far corner (the highest indices) and one on the
+    bottom wall."""
+    nx, ny = MAX2D["nx"], MAX2D["ny"]
+    s, wall = wl.flat_channel(nx, ny)
+    drops = [(16300.0, ny - 1.5, 20.0), (700.0, 1.5, 20.0)]
+    return wl.Case("max2d", s, drops, wall, theta_deg=70.0, steps=6)
+
+
+def max2d_window_run(x_centre, half, steps):
+    """Oracle on the full-height window [x_centre - half, x_centre + half] of
+    max2d_case() (the window wraps at its own edges; the centre column is
+    farther than 2 * steps + 1 from them)."""
+    case = max2d_case()
+    nx, ny = case.nx, case.ny
+    xs = np.arange(x_centre - half, x_centre + half + 1) % nx
+    solid = np.ascontiguousarray(case.solid[:, xs])
+    o = oracle.Oracle(solid, theta_deg=case.theta_deg, **case.physical())
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, len(xs)))
+    x = np.broadcast_to(xs[None, :].astype(float), y.shape)
+    phi0 = None
+    for (x0, y0, R) in case.droplets:
+        phi0 = oracle.droplet_phi(x, y, x0, y0, R, case.W, nx, out=phi0)
+    o.init_phi(phi0)
+    o.step(steps)
+    phi, u, p = o.get()
+    return dict(phi=phi[:, half], u=u[:, half], p=p[:, half])

@@ -32,6 +32,7 @@ _JOBS = {
     "flat_chi3": (oj.run_case, ("flat_chi3",)),
     "incline_w8": (oj.run_case, ("incline_w8",)),
 }
+_JOBS["max2d_win"] = (oj.max2d_window_run, (16300, 14, 6))
 FULL = dict(nx=4096, ny=2048, n_drops=64, seed=2312)
 WIN_STEPS, WIN_HALF = 12, 40
 WIN_X = [0, 1000, 2047, 3333, 4095]
@@ -187,6 +188,29 @@ def test_edge_cases_2d():
     phi, u, p = e.get()
     assert np.all(phi == 0) and np.all(u == 0) and np.all(p == 0) and e.mass() == 0.0
     e.close()
+
+
+def test_largest_accepted_lattice():
+    # 16384 x 7280 (18 * ny * pitch just below 2^31): the highest population
+    # indices. A droplet hangs from the top wall at the far corner; its
+    # column is compared with an oracle window of the same input.
+    case = oj.max2d_case()
+    s = solver(case, "fp32")
+    s.step(case.steps)
+    s.check()
+    ny, nx = case.solid.shape
+    phi_t = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    u_t = torch.empty((ny, nx, 2), dtype=torch.float64, device="cuda")
+    p_t = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    s.get_device(phi_t, u_t, p_t)
+    torch.cuda.synchronize()
+    phi, u, p = (t[:, 16300].cpu().numpy() for t in (phi_t, u_t, p_t))
+    s.close()
+    r = ref("max2d_win")
+    assert phi[-40:].max() > 0.9                     # the corner droplet is in the column
+    assert np.max(np.abs(phi - r["phi"])) <= 1e-5
+    assert np.max(np.abs(u - r["u"])) <= 1e-6
+    assert np.max(np.abs(p - r["p"])) <= 1e-6
 
 
 # ---------------------------------------------------------- diagnostics --
