@@ -171,6 +171,18 @@ def run3d_case(name, steps=None):
     return out
 
 
+MAX3D = dict(nx=512, ny=512, nz=315)     # 26 * nz * ny * pitch = 2146959360 < 2^31
+
+
+def max3d_case():
+    """The largest accepted 3D box with a droplet hanging from the top wall at
+    the far corner (the highest indices) and one on the bottom wall."""
+    s, zw = wl.box3d(MAX3D["nx"], MAX3D["ny"], MAX3D["nz"])
+    top = MAX3D["nz"] - 1.5
+    return wl.Case3D("max3d", s, [(500.0, 500.0, top, 14.0), (60.0, 60.0, zw, 14.0)], zw, theta_deg=70.0,
+                     steps=8)
+
+
 def window3d_run(full_kwargs, xc, yc, half, steps):
     """Run the 3D oracle on a full-height window [xc - half, xc + half] x
     [yc - half, yc + half] of a large many-droplet box, built from the same
@@ -178,7 +190,7 @@ def window3d_run(full_kwargs, xc, yc, half, steps):
     the periods of the full box (pointwise maximum over droplets). Nodes
     farther than 2 * steps + 1 from the window edges do not feel the wrong
     periodic wrap of the window, so the centre column equals the full run."""
-    case = wl.many_droplets_3d(**full_kwargs)
+    case = max3d_case() if full_kwargs == "max3d" else wl.many_droplets_3d(**full_kwargs)
     nz, ny_full, nx_full = case.shape
     xs = np.arange(xc - half, xc + half + 1) % nx_full
     ys = np.arange(yc - half, yc + half + 1) % ny_full

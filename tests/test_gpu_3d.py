@@ -41,6 +41,7 @@ def oracle_pool():
         _fut[name] = _pool.apply_async(oj.run3d_case, (name,))
     for xc, yc in _win_centres():
         _fut[("win3", xc, yc)] = _pool.apply_async(oj.window3d_run, (FULL3, xc, yc, WIN3_HALF, WIN3_STEPS))
+    _fut["max3d"] = _pool.apply_async(oj.window3d_run, ("max3d", 507, 500, WIN3_HALF, 8))
     yield
     _pool.close()
     _pool.join()
@@ -221,6 +222,27 @@ def test_init_phi_and_edge_cases_3d():
     phi, u, p = e.get()
     assert np.all(phi == 0) and np.all(u == 0) and np.all(p == 0) and e.mass() == 0.0
     e.close()
+
+
+def test_largest_accepted_box_3d():
+    # 512 x 512 x 315 (26 * nz * ny * pitch just below 2^31): the highest
+    # population indices; the column through the edge of a droplet hanging
+    # from the top wall at the far corner against an oracle window
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.max3d_case()
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp32", **c.physical())
+    for d in c.droplets:
+        s.init_droplet(*d)
+    s.step(c.steps)
+    s.check()
+    phi, u, p = s.get_f32()
+    s.close()
+    r = _fut["max3d"].get(timeout=900)
+    col = (slice(None), 500, 507)
+    assert r["phi"][-20:].max() > 0.9 and r["phi"].min() < 0.1
+    assert np.max(np.abs(phi[col] - r["phi"])) <= 1e-5
+    assert np.max(np.abs(u[col] - r["u"])) <= 1e-6
+    assert np.max(np.abs(p[col] - r["p"])) <= 1e-6
 
 
 def test_rejects_bad_mask_3d():
