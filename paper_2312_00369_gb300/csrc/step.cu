@@ -31,6 +31,14 @@
 #ifndef PFLBM_STEP_MINB
 #define PFLBM_STEP_MINB 6    // resident 256-thread CTAs per SM asked of k_step (FP32, 16-bit)
 #endif
+#ifndef PFLBM_L2_AHEAD
+// k_step: prefetch into L2 the rows of the tile this many CTAs later in
+// launch order (0: off). With 6 resident CTAs on each of 152 SMs, 228 is a
+// quarter of a wave: about 1.5 us before that CTA starts, short enough that
+// the lines are still in L2 when it reads them (measured optimum; at a whole
+// wave and beyond the lines are evicted first and the step slows down).
+#define PFLBM_L2_AHEAD 228
+#endif
 
 namespace pfk {
 namespace {
@@ -55,6 +63,7 @@ struct StepArgs {
     C gx, gy;            // body acceleration
     int varvisc;
     int dgdt;            // 0: backward difference of G (history read/written); 1: omitted
+    int pf_dx, pf_dy;    // k_step L2 prefetch target: PFLBM_L2_AHEAD CTAs on, in tiles
     int* status;
     // macroscopic output (read-back kernel only), dense [ny][nx]
     double* o_phi;
@@ -519,11 +528,46 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     if (!a.dgdt) a.sprev[k] = s_now;
 }
 
+// L2 prefetch of the rows that a later tile reads: the 18 population planes
+// (g_0 storage included), the u.grad(phi) history and the node bytes. The
+// target is PFLBM_L2_AHEAD CTAs later in launch order, (pf_dx, pf_dy) tiles
+// from this one. One row segment per thread; a segment of 32 nodes is at
+// most 128 B and starts on a 128 B line (FP32 and 16-bit storage; x0 is a
+// multiple of 32 and the pitch of 64). Every address lies inside the
+// lattice's arrays: the tile exists and y < ny; offsets stay below
+// 18 * plane < 2^31.
+template <int PREC>
+__device__ __forceinline__ void prefetch_tile_l2(const StepArgs<PREC>& a, int bx, int by, int ntx, int nty)
+{
+    static_assert(TY == 8, "one row of the tile per thread of an 8-thread group");
+    if (PREC == PFLBM_FP64) return;
+    int px = bx + a.pf_dx, py = by + a.pf_dy;
+    if (px >= ntx) { px -= ntx; ++py; }
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int q = tid >> 3, gy = py * TY + (tid & 7);
+    if (py >= nty || q >= 20 || gy >= a.ny) return;
+    const int row = gy * a.pitch + px * TX;
+    const void* p;
+    if (q < 18) {
+        // FP32: g_0 is g plane 0, plane 9 of the buffer; 16-bit: its own array
+        if (PREC == PFLBM_FP32 || q != 9) p = a.in.f + (q * a.plane + row);
+        else p = a.in.g0 + row;
+    } else if (q == 18) {
+        if (a.dgdt) return;
+        p = a.sprev + row;
+    } else {
+        if (a.tiles[py * ntx + px]) return;     // an all-fluid tile does not read its node bytes
+        p = a.cls + row;
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int PREC, bool COLLIDE, int VV>
 __global__ void __launch_bounds__(TX * TY, PREC == PFLBM_FP64 ? 1 : PFLBM_STEP_MINB) k_step(StepArgs<PREC> a)
 {
     __shared__ uint8_t s_cls[TY + 6][TX + 6];
     __shared__ typename Store<PREC>::C s_phi[TY + 4][TX + 4];
+    if (COLLIDE && PFLBM_L2_AHEAD > 0) prefetch_tile_l2<PREC>(a, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
     step_tile<PREC, COLLIDE, VV>(a, blockIdx.x, blockIdx.y, gridDim.x, s_cls, s_phi);
 }
 
@@ -584,6 +628,8 @@ StepArgs<PREC> make_args(pflbm_t* h)
     a.force_pre = (C)(1.0 - 1.0 / (2.0 * q.tau_f));
     a.alpha = (C)q.alpha;
     a.varvisc = (q.nu_l > 0 && q.nu_g > 0) ? 1 : 0;
+    a.pf_dx = PFLBM_L2_AHEAD % tiles_x(h->nx);
+    a.pf_dy = PFLBM_L2_AHEAD / tiles_x(h->nx);
     a.dgdt = q.dgdt_mode;
     a.tau_g3h = (C)(3.0 * q.nu_g + 0.5);
     a.dtau3 = (C)(3.0 * (q.nu_l - q.nu_g));
