@@ -80,13 +80,22 @@ __device__ __forceinline__ typename Store<PREC>::C pull(const typename Store<PRE
 {
     using T = Store<PREC>;
     constexpr int X = cx(I), Y = cy(I), O = opp(I);
-    if (!CHECK || zeta_of(s_cls[sy - Y][sx - X])) {
-        return T::template ldp<I>(base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)]);
-    }
-    if (zeta_of(s_cls[sy + Y][sx + X])) {
-        return T::template ldp<O>(base[O * plane + (gy + Y) * pitch + wrap1(gx + X, nx)]);
-    }
-    return T::template ldp<O>(base[O * plane + gy * pitch + gx]);
+    if (!CHECK) return T::template ldp<I>(base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)]);
+    // one load from the selected source, no branch (a warp whose lanes pick
+    // different sources still issues one load); I and O share a storage unit
+    static_assert(T::template unit<I>() == T::template unit<O>(), "opposite directions share a unit");
+    int src = O * plane + gy * pitch + gx;
+    if (zeta_of(s_cls[sy + Y][sx + X])) src = O * plane + (gy + Y) * pitch + wrap1(gx + X, nx);
+    if (zeta_of(s_cls[sy - Y][sx - X])) src = I * plane + (gy - Y) * pitch + wrap1(gx - X, nx);
+    return T::template ldp<I>(base[src]);
+}
+
+// Whether a node takes the bounce-back pull. Per warp: if any active lane
+// has an unknown link, all take it (for a node without one it reads what
+// the plain pull reads), so a warp issues one set of loads.
+__device__ __forceinline__ bool has_link(uint8_t code)
+{
+    return __any_sync(__activemask(), (code & F_LINK) != 0);
 }
 
 template <int PREC, bool CHECK>
@@ -239,7 +248,7 @@ __device__ __forceinline__ void ring_phi(const StepArgs<PREC>& a, const uint8_t 
     if (zeta_of(c)) {
         const int gy = y0 - 2 + py, xr = x0 - 2 + px;
         const int gx = tiny ? wrapn(xr, a.nx) : wrap1(xr, a.nx);
-        if (c & F_LINK)
+        if (has_link(c))
             ph = pulled_phi<PREC, true>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
         else
             ph = pulled_phi<PREC, false>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
@@ -283,7 +292,7 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
         int gx = wx(x0 + tx), gy = y0 + ty;
         C ph = C(0);
         if (gy < ny && zeta_of(own)) {
-            if (own & F_LINK)
+            if (has_link(own))
                 pull_g<PREC, true>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
             else
                 pull_g<PREC, false>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
@@ -439,7 +448,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     const C Fx = fmadd(mu, gpx, rho * a.gx), Fy = fmadd(mu, gpy, rho * a.gy);
 
     // ---- hydrodynamic moments (Sec. 2.1.2) ----
-    if (code & F_LINK)
+    if (!fluid_tile && has_link(code))
         pull_f<PREC, true>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
     else if (!(PFLBM_PREFETCH_F && fluid_tile))
         pull_f<PREC, false>(f, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);

@@ -98,11 +98,15 @@ __device__ __forceinline__ typename Store<PREC>::C pull3(const Args3<PREC>& a, c
 {
     using T = Store<PREC>;
     constexpr int X = q19x(I), Y = q19y(I), Z = q19z(I), O = q19o(I);
+    static_assert(PREC == PFLBM_FP32 || PREC == PFLBM_FP64, "3D storage: loads are bare");
     const int src = nbr(a, x, y, z, -X, -Y, -Z);
-    if (!check || zeta_of(a.cls[src])) return T::template ld<I>(base[I * a.plane + src]);
+    if (!check) return T::template ld<I>(base[I * a.plane + src]);
+    // both class bytes read at once, then one load from the selected source
     const int dst = nbr(a, x, y, z, X, Y, Z);
-    if (zeta_of(a.cls[dst])) return T::template ld<O>(base[O * a.plane + dst]);
-    return T::template ld<O>(base[O * a.plane + k]);
+    int at = O * a.plane + k;
+    if (zeta_of(a.cls[dst])) at = O * a.plane + dst;
+    if (zeta_of(a.cls[src])) at = I * a.plane + src;
+    return T::template ld<I>(base[at]);
 }
 
 template <int PREC>
