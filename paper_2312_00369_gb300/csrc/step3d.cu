@@ -25,7 +25,10 @@
 using namespace pfk;
 
 #ifndef PFLBM3D_STEP_MINB
-#define PFLBM3D_STEP_MINB 4   // resident 256-thread CTAs per SM asked of the FP32 step kernel
+#define PFLBM3D_STEP_MINB 4   // resident 256-thread CTAs per SM asked of the FP32 step kernel (64 registers)
+#endif
+#ifndef PFLBM3D_FUSED_MINB
+#define PFLBM3D_FUSED_MINB 4  // the same for the fused z-marching kernel
 #endif
 
 #ifndef PFLBM3D_FUSED_STEP_FIRST
@@ -126,23 +129,24 @@ __device__ __forceinline__ void pull_g7(const Args3<PREC>& a, int x, int y, int 
 template <typename C>
 __device__ __forceinline__ C sum6(const C v[7]) { return ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]); }
 
-// (1) phi on zeta = 1 nodes. Warps without a bounce-back link take the
-// branch-free pull (all loads independent).
+// (1) phi on zeta = 1 nodes. The node byte and the plain pull are issued
+// together (one memory latency, not two); a warp with a bounce-back link
+// then pulls again with the checks. Planes 0 and nz - 1 hold no zeta = 1
+// node (the two outer planes of the mask are solid), so every plain pull
+// here stays inside the box.
 template <int PREC>
 __global__ void __launch_bounds__(256) k3_phi(Args3<PREC> a)
 {
     using C = typename Store<PREC>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-    if (x >= a.nx || y >= a.ny) return;
+    if (x >= a.nx || y >= a.ny || z == 0 || z == a.nz - 1) return;
     const int k = (z * a.ny + y) * a.pitch + x;
     const uint8_t c = a.cls[k];
-    if (!zeta_of(c)) return;
     C v[7];
     typename Store<PREC>::G0T r;
-    if (__any_sync(__activemask(), (c & F_LINK) != 0))
-        pull_g7<PREC>(a, x, y, z, k, (c & F_LINK) != 0, v, r);
-    else
-        pull_g7<PREC>(a, x, y, z, k, false, v, r);
+    pull_g7<PREC>(a, x, y, z, k, false, v, r);
+    if (!zeta_of(c)) return;
+    if (__any_sync(__activemask(), (c & F_LINK) != 0)) pull_g7<PREC>(a, x, y, z, k, (c & F_LINK) != 0, v, r);
     a.phi[k] = v[0] + sum6(v);
 }
 
@@ -251,6 +255,12 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     f[16] = pull3<16, PREC>(a, a.f_in, x, y, z, k, check);
     f[17] = pull3<17, PREC>(a, a.f_in, x, y, z, k, check);
     f[18] = pull3<18, PREC>(a, a.f_in, x, y, z, k, check);
+    // the g pull and the history with the f pulls (one memory round trip,
+    // not one after the f stores); the g collision then precedes the f one
+    C g[7];
+    typename T::G0T raw0;
+    load_g(g, raw0);
+    const C sp = (COLLIDE && !a.dgdt) ? a.sprev[k] : C(0);
     C m[3] = {C(0), C(0), C(0)}, fsum = C(0);
 #pragma unroll
     for (int i = 1; i < 19; i += 2) {
@@ -274,6 +284,20 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
         return;
     }
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
+    // ---- phase lattice (D3Q7): G_i = w_i h_i (3/2 s - 1/2 s_prev), h_0 = -5/2, h_i = -1/2 ----
+    auto collide_g = [&](const C (&g)[7], typename T::G0T raw0, C sp) {
+        const C s_now = fmadd(u[2], gp[2], fmadd(u[1], gp[1], u[0] * gp[0]));
+        const C src = a.dgdt ? s_now : fmadd(C(1.5), s_now, C(-0.5) * sp);
+        const C am = a.alpha * mu;
+        // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu - src / 2), the same for i = 1..6
+        const C gm = q7w<C>(1) * fmadd(C(-0.5), src, a.omega_g * am), omg = C(1) - a.omega_g;
+#pragma unroll
+        for (int i = 1; i < 7; ++i) a.g_out[i * a.plane + k] = T::template st<1>(fmadd(omg, g[i], gm));
+        const C d0 = fmadd(a.omega_g, fmadd(C(-0.75), am, sum6(g)), (q7w<C>(0) * C(-2.5)) * src);
+        a.g0_out[k] = T::g0_add(raw0, d0, a.status);
+        if (!a.dgdt) a.sprev[k] = s_now;
+    };
+    collide_g(g, raw0, sp);
     a.f_out[k] = T::template st<0>(fmadd(a.omega_f, fmadd(-(C(0.5) * rho), uu, C(-2) * p) - f[0], f[0]));
     PairK<C> K;
     K.base = a.omega_f * fmadd(-(C(1.5) * rho), uu, C(3) * p);
@@ -290,20 +314,6 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
     collide_pair<PREC, 13>(a, f[13], f[14], K, u, F, dr, k);
     collide_pair<PREC, 15>(a, f[15], f[16], K, u, F, dr, k);
     collide_pair<PREC, 17>(a, f[17], f[18], K, u, F, dr, k);
-    // ---- phase lattice (D3Q7): G_i = w_i h_i (3/2 s - 1/2 s_prev), h_0 = -5/2, h_i = -1/2 ----
-    C g[7];
-    typename T::G0T raw0;
-    load_g(g, raw0);
-    const C s_now = fmadd(u[2], gp[2], fmadd(u[1], gp[1], u[0] * gp[0]));
-    const C src = a.dgdt ? s_now : fmadd(C(1.5), s_now, C(-0.5) * a.sprev[k]);
-    const C am = a.alpha * mu;
-    // g*_i = (1 - omega_g) g_i + w_i (omega_g alpha mu - src / 2), the same for i = 1..6
-    const C gm = q7w<C>(1) * fmadd(C(-0.5), src, a.omega_g * am), omg = C(1) - a.omega_g;
-#pragma unroll
-    for (int i = 1; i < 7; ++i) a.g_out[i * a.plane + k] = T::template st<1>(fmadd(omg, g[i], gm));
-    const C d0 = fmadd(a.omega_g, fmadd(C(-0.75), am, sum6(g)), (q7w<C>(0) * C(-2.5)) * src);
-    a.g0_out[k] = T::g0_add(raw0, d0, a.status);
-    if (!a.dgdt) a.sprev[k] = s_now;
 }
 
 template <int PREC, bool COLLIDE>
@@ -464,7 +474,7 @@ __device__ __forceinline__ void fused_fill_plane(const Args3<PREC>& a, FusedSmem
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(256, PREC == PFLBM_FP64 ? 1 : PFLBM3D_STEP_MINB)
+__global__ void __launch_bounds__(256, PREC == PFLBM_FP64 ? 1 : PFLBM3D_FUSED_MINB)
 k3_fused(Args3<PREC> a, int zc, const uint8_t* __restrict__ gflag)
 {
     using C = typename Store<PREC>::C;
