@@ -265,7 +265,8 @@ const char* pflbm_last_error(void);
  * -x-z, +x-z, -x+z, +y+z, -y-z, +y-z, -y+z); D3Q7 is the first seven.
  * Classes as in 2D with the 18-neighbourhood of D3Q19 for "neighbour".
  * Precision: PFLBM_FP64 or PFLBM_FP32 (g_0 in 32-bit fixed point as in 2D).
- * The library allocates its device memory with cudaMalloc; the state takes
+ * The library allocates its device memory with cudaMalloc, or with the
+ * allocator callbacks of pflbm3d_params_t when they are set; the state takes
  * 2 x 26 population planes of nz*ny*pitch elements (pitch = nx rounded up to
  * 64) plus 8 further planes. Sizes: nx, ny >= 3, 5 <= nz <= 65535,
  * ny <= 524280, 26 nz ny pitch < 2^31 (EINVAL otherwise). Error behaviour as
@@ -284,6 +285,11 @@ typedef struct {
     int step_path;               /* enum pflbm3d_step_path; the results are identical */
     int fused_zc;                /* planes per CTA of the fused step; <= 0: chosen by the library */
     int dgdt_mode;               /* as pflbm_params_t.dgdt_mode: 0 backward difference, 1 omitted */
+    /* Optional device allocator, as in pflbm_params_t (both NULL: cudaMalloc /
+     * cudaFree). Every buffer is returned through free at pflbm3d_destroy. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* ctx);
+    void* alloc_ctx;
 } pflbm3d_params_t;
 
 /* How a 3D step runs. PFLBM3D_FUSED: one launch; each CTA marches a 32 x 8

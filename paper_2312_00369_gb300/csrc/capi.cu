@@ -210,10 +210,12 @@ int ensure_out(pflbm_t* h)
     return PFLBM_OK;
 }
 
-__global__ void k_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n)
+// Sets *flag when a value of the [ny][pitch] angle field (first nx columns)
+// is not finite.
+__global__ void k_theta_finite(const float* __restrict__ theta, int nx, int ny, int pitch, int* flag)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x < nx && y < ny && !isfinite(theta[(size_t)y * pitch + x])) atomicOr(flag, 1);
 }
 
 }  // namespace
@@ -282,10 +284,7 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
             !prm->solid_mask[(size_t)(ny - 1) * nx + x])
             return fail(PFLBM_EBADMASK, "rows 0, 1, ny-2 and ny-1 of the solid mask must be solid");
     }
-    if (prm->theta_field_deg) {
-        for (size_t k = 0; k < (size_t)nx * ny; ++k)
-            if (!std::isfinite(prm->theta_field_deg[k])) return fail(PFLBM_EINVAL, "theta field has a non-finite value");
-    }
+    // a non-finite value in the angle field is found on the device, after the copy
     pflbm_t* h = new (std::nothrow) pflbm();
     if (!h) return fail(PFLBM_ENOMEM, "host allocation failed");
     h->nx = nx;
@@ -361,6 +360,7 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
         return fail(PFLBM_ENOMEM, "cudaMallocHost failed");
     }
     h->hstatus[0] = 0;
+    h->hstatus[1] = 0;
 #define CKR(call)                                                 \
     do {                                                          \
         cudaError_t e_ = (call);                                  \
@@ -376,11 +376,21 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
     if (prm->theta_field_deg)
         CKR(cudaMemcpy2DAsync(h->theta, h->pitch * sizeof(float), prm->theta_field_deg, nx * sizeof(float),
                               nx * sizeof(float), ny, cudaMemcpyHostToDevice, h->stream));
+    if (prm->theta_field_deg) {
+        dim3 b(32, 8), g((nx + 31) / 32, (ny + 7) / 8);
+        k_theta_finite<<<g, b, 0, h->stream>>>(h->theta, nx, ny, h->pitch, h->dstatus + 1);
+        CKR(cudaGetLastError());
+        CKR(cudaMemcpyAsync(h->hstatus + 1, h->dstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    }
     CKR(launch_classify(h));
     CKR(launch_tile_flags(h));
     CKR(launch_wet(h));
     CKR(cudaStreamSynchronize(h->stream));
 #undef CKR
+    if (prm->theta_field_deg && h->hstatus[1] != 0) {
+        release(h);
+        return fail(PFLBM_EINVAL, "theta field has a non-finite value");
+    }
     *out = h;
     return PFLBM_OK;
 }
@@ -500,23 +510,21 @@ int pflbm_get_f32(pflbm_t* h, float* phi, float* u, float* p)
     if (int rc = check_handle(h)) return rc;
     DeviceGuard g(h->device);
     if (int rc = materialize(h)) return rc;
-    if (int rc = ensure_out(h)) return rc;
     size_t N = (size_t)h->nx * h->ny;
     if (!h->out_f) {
         void* q = nullptr;
         if (int rc = dalloc(h, &q, 4 * N * sizeof(float))) return rc;
         h->out_f = (float*)q;
     }
-    double* dphi = h->out;
-    double* du = h->out + N;
-    double* dp = h->out + 3 * N;
-    CK(launch_macro(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr));
-    // the dense fields are contiguous (phi, u, p at offsets 0, N, 3N): one conversion
-    k_to_float<<<(unsigned)std::min<size_t>((4 * N + 255) / 256, 4096), 256, 0, h->stream>>>(h->out, h->out_f, 4 * N);
-    CK(cudaGetLastError());
-    if (phi) CK(cudaMemcpyAsync(phi, h->out_f, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    if (u) CK(cudaMemcpyAsync(u, h->out_f + N, 2 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    if (p) CK(cudaMemcpyAsync(p, h->out_f + 3 * N, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    // the read-back kernel writes the float fields directly (phi, u, p at
+    // offsets 0, N, 3N): no FP64 scratch
+    float* fphi = h->out_f;
+    float* fu = h->out_f + N;
+    float* fp = h->out_f + 3 * N;
+    CK(launch_macro_f32(h, phi ? fphi : nullptr, u ? fu : nullptr, p ? fp : nullptr));
+    if (phi) CK(cudaMemcpyAsync(phi, fphi, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK(cudaMemcpyAsync(u, fu, 2 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (p) CK(cudaMemcpyAsync(p, fp, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return read_status(h);
 }

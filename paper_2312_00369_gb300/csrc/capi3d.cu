@@ -19,12 +19,6 @@ using namespace pfk3;
 
 namespace {
 
-__global__ void k3_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
-}
-
 size_t pop3_bytes(int prec, size_t plane)
 {
     return prec == PFLBM_FP64 ? 26 * plane * 8 : 26 * plane * 4;  // g_0 plane holds its storage form
@@ -47,14 +41,33 @@ int materialize3(pflbm3d_t* h)
     return PFLBM_OK;
 }
 
+// Device buffer of `bytes` from the handle's allocator (or cudaMalloc) into *p;
+// PFLBM_ENOMEM on failure.
+int alloc3(pflbm3d_t* h, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (h->alloc_fn) {
+        *p = h->alloc_fn(bytes, h->alloc_ctx);
+    } else if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+    }
+    if (!*p) return fail3(PFLBM_ENOMEM, h->alloc_fn ? "allocator callback returned NULL" : "cudaMalloc failed");
+    h->allocs.emplace_back(*p, bytes);
+    return PFLBM_OK;
+}
+
 void release3(pflbm3d_t* h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void* bufs[] = {h->cls, h->solid, h->av, h->wet, h->pop[0], h->pop[1], h->sprev, h->phi, h->phi0, h->mu0,
-                    h->red, h->out, h->dstatus, h->ghosts, h->gflag, h->pts, h->out_f};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
+    for (auto& a : h->allocs) {
+        if (h->free_fn)
+            h->free_fn(a.first, a.second, h->alloc_ctx);
+        else
+            cudaFree(a.first);
+    }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -106,6 +119,9 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
     h->nz = p->nz;
     h->pitch = pitch;
     h->precision = p->precision;
+    h->alloc_fn = p->alloc;
+    h->free_fn = p->free;
+    h->alloc_ctx = p->alloc_ctx;
     int dev = p->device;
     if (dev < 0) cudaGetDevice(&dev);
     h->device = dev;
@@ -136,10 +152,9 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
         {&h->sprev, plane * cs}, {&h->phi, plane * cs}, {(void**)&h->phi0, plane * 8}, {(void**)&h->mu0, plane * 8},
         {(void**)&h->red, (kMassBlocks + 32) * 8}, {(void**)&h->dstatus, 16}};
     for (auto& b : bufs) {
-        if (cudaMalloc(b.ptr, b.bytes) != cudaSuccess) {
-            cudaGetLastError();
+        if (int rc = alloc3(h, b.ptr, b.bytes)) {
             release3(h);
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+            return rc;
         }
     }
     cudaMemsetAsync(h->pop[0], 0, pop3_bytes(p->precision, plane), h->stream);
@@ -177,10 +192,9 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
             zc = zc < 8 ? 8 : (zc > 64 ? 64 : zc);
         }
         h->fused_zc = zc > nzz ? nzz : zc;
-        if (cudaMalloc((void**)&h->gflag, (size_t)tiles * h->nz) != cudaSuccess) {
-            cudaGetLastError();
+        if (int rc = alloc3(h, (void**)&h->gflag, (size_t)tiles * h->nz)) {
             release3(h);
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+            return rc;
         }
         launch_ghost_flags(h);
     }
@@ -190,10 +204,9 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
     cudaMemcpyAsync(&h->n_ghosts, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess && h->n_ghosts > 0) {
-        if (cudaMalloc((void**)&h->ghosts, (size_t)h->n_ghosts * sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
+        if (int rc = alloc3(h, (void**)&h->ghosts, (size_t)h->n_ghosts * sizeof(int))) {
             release3(h);
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
+            return rc;
         }
         cudaMemsetAsync(cnt, 0, sizeof(int), h->stream);
         launch_ghost_collect(h, cnt, h->ghosts);
@@ -269,11 +282,8 @@ int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p)
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
     if (int rc = materialize3(h)) return rc;
     const size_t N = (size_t)h->nx * h->ny * h->nz;
-    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        h->out = nullptr;
-        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-    }
+    if (!h->out)
+        if (int rc = alloc3(h, (void**)&h->out, N * 5 * sizeof(double))) return rc;
     double *dphi = h->out, *du = h->out + N, *dp = h->out + 4 * N;
     CK3(launch_macro(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr));
     if (phi) CK3(cudaMemcpyAsync(phi, dphi, N * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -288,23 +298,14 @@ int pflbm3d_get_f32(pflbm3d_t* h, float* phi, float* u, float* p)
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
     if (int rc = materialize3(h)) return rc;
     const size_t N = (size_t)h->nx * h->ny * h->nz;
-    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        h->out = nullptr;
-        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-    }
-    if (!h->out_f && cudaMalloc((void**)&h->out_f, N * 5 * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        h->out_f = nullptr;
-        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-    }
-    double *dphi = h->out, *du = h->out + N, *dp = h->out + 4 * N;
-    CK3(launch_macro(h, phi ? dphi : nullptr, u ? du : nullptr, p ? dp : nullptr));
-    k3_to_float<<<(unsigned)std::min<size_t>((5 * N + 255) / 256, 4096), 256, 0, h->stream>>>(h->out, h->out_f, 5 * N);
-    CK3(cudaGetLastError());
-    if (phi) CK3(cudaMemcpyAsync(phi, h->out_f, N * 4, cudaMemcpyDeviceToHost, h->stream));
-    if (u) CK3(cudaMemcpyAsync(u, h->out_f + N, 3 * N * 4, cudaMemcpyDeviceToHost, h->stream));
-    if (p) CK3(cudaMemcpyAsync(p, h->out_f + 4 * N, N * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (!h->out_f)
+        if (int rc = alloc3(h, (void**)&h->out_f, N * 5 * sizeof(float))) return rc;
+    // the read-back kernel writes the float fields directly: no FP64 scratch
+    float *fphi = h->out_f, *fu = h->out_f + N, *fp = h->out_f + 4 * N;
+    CK3(launch_macro_f32(h, phi ? fphi : nullptr, u ? fu : nullptr, p ? fp : nullptr));
+    if (phi) CK3(cudaMemcpyAsync(phi, fphi, N * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK3(cudaMemcpyAsync(u, fu, 3 * N * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (p) CK3(cudaMemcpyAsync(p, fp, N * 4, cudaMemcpyDeviceToHost, h->stream));
     CK3(cudaStreamSynchronize(h->stream));
     return PFLBM_OK;
 }
@@ -342,18 +343,11 @@ int pflbm3d_contact_angle(pflbm3d_t* h, const pflbm3d_wall_t* wall, double* thet
     if (wall->type != 0 && wall->type != 1) return fail3(PFLBM_EINVAL, "wall type must be 0 or 1");
     if (int rc = materialize3(h)) return rc;
     const size_t N = (size_t)h->nx * h->ny * h->nz;
-    if (!h->out && cudaMalloc((void**)&h->out, N * 5 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        h->out = nullptr;
-        return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-    }
+    if (!h->out)
+        if (int rc = alloc3(h, (void**)&h->out, N * 5 * sizeof(double))) return rc;
     if (!h->pts) {
         const long long cap = std::min<long long>(3LL * (long long)N, 1LL << 22);
-        if (cudaMalloc((void**)&h->pts, (size_t)cap * 3 * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            h->pts = nullptr;
-            return fail3(PFLBM_ENOMEM, "cudaMalloc failed");
-        }
+        if (int rc = alloc3(h, (void**)&h->pts, (size_t)cap * 3 * sizeof(double))) return rc;
         h->pts_cap = (int)cap;
     }
     double* dphi = h->out;

@@ -3,6 +3,9 @@
 // pflbm3d_* entry points). Not part of the ABI.
 #pragma once
 
+#include <utility>
+#include <vector>
+
 #include "pflbm_internal.cuh"
 
 struct pflbm3d {
@@ -34,6 +37,11 @@ struct pflbm3d {
     int cur = 0;
     bool replace_phi = true, init_pending = false;
     int64_t steps = 0;
+    // optional device allocator (both NULL: cudaMalloc / cudaFree)
+    void* (*alloc_fn)(size_t, void*) = nullptr;
+    void (*free_fn)(void*, size_t, void*) = nullptr;
+    void* alloc_ctx = nullptr;
+    std::vector<std::pair<void*, size_t>> allocs;   // every device buffer, freed at destroy
 };
 
 namespace pfk3 {
@@ -44,6 +52,8 @@ constexpr int kMassBlocks = 1216;   // FP64 mass partials (8 per SM on 152 SMs)
 cudaError_t launch_step(pflbm3d_t* h);
 // phi, u, p of the current state into dense device arrays [nz][ny][nx] (any may be NULL)
 cudaError_t launch_macro(pflbm3d_t* h, double* phi, double* u, double* p);
+// the same fields rounded to float (round to nearest)
+cudaError_t launch_macro_f32(pflbm3d_t* h, float* phi, float* u, float* p);
 // initial populations from h->phi0 (ghost fill, mu, f = 0, g = g^eq)
 cudaError_t launch_init(pflbm3d_t* h);
 // sum of the pulled g over zeta = 1 nodes into *d_out (FP64, fixed order)

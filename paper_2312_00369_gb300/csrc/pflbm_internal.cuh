@@ -147,6 +147,7 @@ cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, 
 cudaError_t launch_init_populations(pflbm_t* h);
 cudaError_t launch_step(pflbm_t* h);
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p);
+cudaError_t launch_macro_f32(pflbm_t* h, float* phi, float* u, float* p);   // rounded to nearest
 size_t step_args_bytes(int precision);
 void write_step_args(pflbm_t* h, int flip, void* dst);   // flip: in/out swapped
 cudaError_t launch_step_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,

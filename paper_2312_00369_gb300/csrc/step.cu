@@ -69,6 +69,10 @@ struct StepArgs {
     double* o_phi;
     double* o_u;
     double* o_p;
+    // the same fields rounded to float (read-back kernel only)
+    float* f_phi;
+    float* f_u;
+    float* f_p;
 };
 
 // Pull of direction I at node (gx, gy), whose class byte sits at s_cls[sy][sx].
@@ -431,6 +435,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
             if (a.o_phi) a.o_phi[o] = (double)s_phi[ty + 2][tx + 2];
             if (a.o_u) { a.o_u[2 * o] = 0.0; a.o_u[2 * o + 1] = 0.0; }
             if (a.o_p) a.o_p[o] = 0.0;
+            if (a.f_phi) a.f_phi[o] = (float)s_phi[ty + 2][tx + 2];
+            if (a.f_u) { a.f_u[2 * o] = 0.0f; a.f_u[2 * o + 1] = 0.0f; }
+            if (a.f_p) a.f_p[o] = 0.0f;
         }
         return;
     }
@@ -473,6 +480,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
         if (a.o_phi) a.o_phi[o] = (double)ph;
         if (a.o_u) { a.o_u[2 * o] = (double)ux; a.o_u[2 * o + 1] = (double)uy; }
         if (a.o_p) a.o_p[o] = (double)p;
+        if (a.f_phi) a.f_phi[o] = (float)ph;
+        if (a.f_u) { a.f_u[2 * o] = (float)ux; a.f_u[2 * o + 1] = (float)uy; }
+        if (a.f_p) a.f_p[o] = (float)p;
         return;
     }
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
@@ -665,11 +675,14 @@ __global__ void k_init_droplet(const uint8_t* __restrict__ cls, double* __restri
     size_t k = (size_t)y * pitch + x;
     if (!zeta_of(cls[k])) return;
     double dx = fabs((double)x - x0);
-    dx = fmod(dx, (double)nx);
-    if (dx > 0.5 * nx) dx = nx - dx;       // x-periodic distance
-    double dy = (double)y - y0;
-    double r = sqrt(dx * dx + dy * dy);
-    double v = 0.5 + 0.5 * tanh(2.0 * (R - r) / W);
+    if (dx >= nx) dx = fmod(dx, (double)nx);   // exact; only for a period or more
+    if (dx > 0.5 * nx) dx = nx - dx;           // x-periodic distance
+    const double dy = (double)y - y0, r2 = dx * dx + dy * dy;
+    // beyond |R| + 10 W the profile is 0 in FP64 (tanh(-20) rounds to -1):
+    // the bounding box's corners are skipped like the nodes outside it
+    const double reach = fabs(R) + 10.0 * W;
+    if (r2 > reach * reach) return;
+    const double v = 0.5 + 0.5 * tanh(2.0 * (R - sqrt(r2)) / W);
     if (v > phi[k]) phi[k] = v;
 }
 
@@ -710,23 +723,27 @@ __global__ void k_init_mu(const uint8_t* __restrict__ cls, const C* __restrict__
     size_t k = (size_t)y * pitch + x;
     uint8_t code = cls[k];
     if (!zeta_of(code)) { mu[k] = 0.0; sprev[k] = (C)0; return; }
-    auto at = [&](int dx, int dy) { return phi[(size_t)(y + dy) * pitch + wrap1(x + dx, nx)]; };
-    double c = phi[k];
-    double E = at(1, 0), Wv = at(-1, 0), N = at(0, 1), S = at(0, -1);
-    double NE = at(1, 1), NW = at(-1, 1), SW = at(-1, -1), SE = at(1, -1);
-    // multiplications by rounded reciprocals: FP64 division is slow on this part
-    double gpx = (E - Wv) * (1.0 / 3.0) + ((NE + SE) - (NW + SW)) * (1.0 / 12.0);
-    double gpy = (N - S) * (1.0 / 3.0) + ((NE + NW) - (SE + SW)) * (1.0 / 12.0);
-    double lap = ((E + Wv) + (N + S)) * (2.0 / 3.0) + ((NE + NW) + (SE + SW)) * (1.0 / 6.0) - c * (10.0 / 3.0);
-    double wv = (code & F_WET) ? (double)wet[k] : 0.0;
-    double m = 4.0 * q.beta * c * (c - 1.0) * (c - 0.5) - q.kappa * lap - wv * (c - c * c);
-    mu[k] = m;
+    // in the precision of the step's arithmetic (C): FP64 for FP64 solves,
+    // FP32 otherwise (FP64 arithmetic is slow on this part, and a 32-bit
+    // state stores mu only through g_i^eq = w_i alpha mu, rounded to 32 or
+    // 16 bits; phi = sum g_i stays exact through g_0)
+    auto at = [&](int dx, int dy) { return (C)phi[(size_t)(y + dy) * pitch + wrap1(x + dx, nx)]; };
+    const C c = (C)phi[k];
+    const C E = at(1, 0), Wv = at(-1, 0), N = at(0, 1), S = at(0, -1);
+    const C NE = at(1, 1), NW = at(-1, 1), SW = at(-1, -1), SE = at(1, -1);
+    // multiplications by rounded reciprocals: division is slow
+    const C gpx = (E - Wv) * (C(1) / C(3)) + ((NE + SE) - (NW + SW)) * (C(1) / C(12));
+    const C gpy = (N - S) * (C(1) / C(3)) + ((NE + NW) - (SE + SW)) * (C(1) / C(12));
+    const C lap = ((E + Wv) + (N + S)) * (C(2) / C(3)) + ((NE + NW) + (SE + SW)) * (C(1) / C(6)) - c * (C(10) / C(3));
+    const C wv = (code & F_WET) ? wet[k] : C(0);
+    const C m = C(4) * (C)q.beta * c * (c - C(1)) * (c - C(0.5)) - (C)q.kappa * lap - wv * (c - c * c);
+    mu[k] = (double)m;
     // u at t = 0 from f = 0: u = F / (2 rho), F = mu grad(phi) + rho g; the
     // history of the first step is u.grad(phi)
-    double rho = q.rho_g + (q.rho_l - q.rho_g) * c;
-    const double half_inv_rho = 0.5 / rho;
-    double ux = (m * gpx + rho * q.gx) * half_inv_rho, uy = (m * gpy + rho * q.gy) * half_inv_rho;
-    sprev[k] = (C)(ux * gpx + uy * gpy);
+    const C rho = (C)q.rho_g + (C)(q.rho_l - q.rho_g) * c;
+    const C half_inv_rho = C(0.5) / rho;
+    const C ux = (m * gpx + rho * (C)q.gx) * half_inv_rho, uy = (m * gpy + rho * (C)q.gy) * half_inv_rho;
+    sprev[k] = ux * gpx + uy * gpy;
 }
 
 // g_J^eq (J != 0) in storage form; returns the rounding residual.
@@ -783,12 +800,16 @@ __global__ void k_init_pop(const uint8_t* __restrict__ cls, const double* __rest
 dim3 grid2d(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
 template <int PREC, bool COLLIDE>
-cudaError_t run_step_kernel(pflbm_t* h, double* o_phi, double* o_u, double* o_p)
+cudaError_t run_step_kernel(pflbm_t* h, double* o_phi, double* o_u, double* o_p, float* f_phi = nullptr,
+                            float* f_u = nullptr, float* f_p = nullptr)
 {
     StepArgs<PREC> a = make_args<PREC>(h);
     a.o_phi = o_phi;
     a.o_u = o_u;
     a.o_p = o_p;
+    a.f_phi = f_phi;
+    a.f_u = f_u;
+    a.f_p = f_p;
     dim3 b(TX, TY), g(tiles_x(h->nx), tiles_y(h->ny));
     if (a.varvisc)
         k_step<PREC, COLLIDE, 1><<<g, b, 0, h->stream>>>(a);
@@ -938,6 +959,16 @@ cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p)
         case PFLBM_FP32: return run_step_kernel<PFLBM_FP32, false>(h, phi, u, p);
         case PFLBM_BF16: return run_step_kernel<PFLBM_BF16, false>(h, phi, u, p);
         default: return run_step_kernel<PFLBM_FP16, false>(h, phi, u, p);
+    }
+}
+
+cudaError_t launch_macro_f32(pflbm_t* h, float* phi, float* u, float* p)
+{
+    switch (h->precision) {
+        case PFLBM_FP64: return run_step_kernel<PFLBM_FP64, false>(h, nullptr, nullptr, nullptr, phi, u, p);
+        case PFLBM_FP32: return run_step_kernel<PFLBM_FP32, false>(h, nullptr, nullptr, nullptr, phi, u, p);
+        case PFLBM_BF16: return run_step_kernel<PFLBM_BF16, false>(h, nullptr, nullptr, nullptr, phi, u, p);
+        default: return run_step_kernel<PFLBM_FP16, false>(h, nullptr, nullptr, nullptr, phi, u, p);
     }
 }
 

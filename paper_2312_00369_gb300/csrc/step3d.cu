@@ -86,6 +86,9 @@ struct Args3 {
     double* o_phi;
     double* o_u;
     double* o_p;
+    float* f_phi;     // the same fields rounded to float (read-back only)
+    float* f_u;
+    float* f_p;
 };
 
 template <int PREC>
@@ -281,6 +284,9 @@ __device__ __forceinline__ void step_node(const Args3<PREC>& a, int x, int y, in
         if (a.o_phi) a.o_phi[o] = (double)ph;
         if (a.o_u) { a.o_u[3 * o] = u[0]; a.o_u[3 * o + 1] = u[1]; a.o_u[3 * o + 2] = u[2]; }
         if (a.o_p) a.o_p[o] = (double)p;
+        if (a.f_phi) a.f_phi[o] = (float)ph;
+        if (a.f_u) { a.f_u[3 * o] = (float)u[0]; a.f_u[3 * o + 1] = (float)u[1]; a.f_u[3 * o + 2] = (float)u[2]; }
+        if (a.f_p) a.f_p[o] = (float)p;
         return;
     }
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
@@ -329,6 +335,9 @@ __global__ void __launch_bounds__(256, PREC == PFLBM_FP64 ? 1 : PFLBM3D_STEP_MIN
             if (a.o_phi) a.o_phi[o] = (double)a.phi[k];
             if (a.o_u) { a.o_u[3 * o] = 0.0; a.o_u[3 * o + 1] = 0.0; a.o_u[3 * o + 2] = 0.0; }
             if (a.o_p) a.o_p[o] = 0.0;
+            if (a.f_phi) a.f_phi[o] = (float)a.phi[k];
+            if (a.f_u) { a.f_u[3 * o] = 0.0f; a.f_u[3 * o + 1] = 0.0f; a.f_u[3 * o + 2] = 0.0f; }
+            if (a.f_p) a.f_p[o] = 0.0f;
         }
         return;
     }
@@ -639,11 +648,18 @@ __global__ void k3_droplet(const uint8_t* cls, double* phi, int nx, int ny, int 
     if (y < 0) y += ny;
     const size_t k = ((size_t)z * ny + y) * pitch + x;
     if (!zeta_of(cls[k])) return;
+    // periodic distances (fmod, exact, only for a distance of a period or more)
     double dx = fabs(x - x0), dy = fabs(y - y0);
-    dx = fmod(dx, (double)nx); if (dx > 0.5 * nx) dx = nx - dx;
-    dy = fmod(dy, (double)ny); if (dy > 0.5 * ny) dy = ny - dy;
-    const double dz = z - z0, r = sqrt(dx * dx + dy * dy + dz * dz);
-    const double v = 0.5 + 0.5 * tanh(2.0 * (R - r) / W);
+    if (dx >= nx) dx = fmod(dx, (double)nx);
+    if (dx > 0.5 * nx) dx = nx - dx;
+    if (dy >= ny) dy = fmod(dy, (double)ny);
+    if (dy > 0.5 * ny) dy = ny - dy;
+    const double dz = z - z0, r2 = dx * dx + dy * dy + dz * dz;
+    // beyond |R| + 10 W the profile is 0 in FP64 (tanh(-20) rounds to -1):
+    // the bounding box's corners are skipped like the nodes outside it
+    const double reach = fabs(R) + 10.0 * W;
+    if (r2 > reach * reach) return;
+    const double v = 0.5 + 0.5 * tanh(2.0 * (R - sqrt(r2)) / W);
     if (v > phi[k]) phi[k] = v;
 }
 
@@ -681,23 +697,26 @@ __global__ void k3_init_pop(Args3<PREC> a, const double* phi0, double* mu0, Para
     a.sprev[k] = C(0);
     const uint8_t code = a.cls[k];
     if (!zeta_of(code)) return;
-    // mu of the initial field (Eq. chemical_potencial2), FP64
-    const double ph = phi0[k];
-    double gp[3] = {0, 0, 0}, lap = 0.0;
+    // mu of the initial field (Eq. chemical_potencial2) in the precision of the
+    // step's arithmetic (FP64 for FP64 solves, FP32 otherwise: FP64 arithmetic
+    // is slow on this part); phi itself stays FP64, so g_0 + sum g_i = phi0
+    const double phd = phi0[k];
+    const C ph = (C)phd;
+    C gp[3] = {C(0), C(0), C(0)}, lap = C(0);
     for (int i = 1; i < 19; ++i) {
-        const double v = phi0[nbr(a, x, y, z, q19x(i), q19y(i), q19z(i))];
-        const double w3 = 3.0 * q19w<double>(i);
-        gp[0] += w3 * q19x(i) * v;
-        gp[1] += w3 * q19y(i) * v;
-        gp[2] += w3 * q19z(i) * v;
-        lap += 2.0 * w3 * (v - ph);
+        const C v = (C)phi0[nbr(a, x, y, z, q19x(i), q19y(i), q19z(i))];
+        const C w3 = C(3) * q19w<C>(i);
+        gp[0] += w3 * C(q19x(i)) * v;
+        gp[1] += w3 * C(q19y(i)) * v;
+        gp[2] += w3 * C(q19z(i)) * v;
+        lap += C(2) * w3 * (v - ph);
     }
-    const double wet = (code & F_WET) ? (double)a.wet[k] : 0.0;
-    const double mu = 4.0 * q.beta * ph * (ph - 1.0) * (ph - 0.5) - q.kappa * lap - wet * (ph - ph * ph);
-    mu0[k] = mu;
-    const double rho = q.rho_g + (q.rho_l - q.rho_g) * ph, h = 0.5 / rho;
-    a.sprev[k] = (C)((mu * gp[0] * gp[0] + mu * gp[1] * gp[1] + mu * gp[2] * gp[2]) * h);
-    a.g0_in[k] = T::g0_from_double(ph - 0.75 * q.alpha * mu);
+    const C wet = (code & F_WET) ? a.wet[k] : C(0);
+    const C mu = C(4) * (C)q.beta * ph * (ph - C(1)) * (ph - C(0.5)) - (C)q.kappa * lap - wet * (ph - ph * ph);
+    mu0[k] = (double)mu;
+    const C rho = (C)q.rho_g + (C)(q.rho_l - q.rho_g) * ph, h = C(0.5) / rho;
+    a.sprev[k] = (mu * gp[0] * gp[0] + mu * gp[1] * gp[1] + mu * gp[2] * gp[2]) * h;
+    a.g0_in[k] = T::g0_from_double(phd - 0.75 * q.alpha * (double)mu);
 }
 
 // g_i (i != 0) of the first pull: g_i^eq(mu) at x + c_i, or at x itself when
@@ -819,12 +838,16 @@ cudaError_t step3_prec(pflbm3d_t* h)
 }
 
 template <int PREC>
-cudaError_t macro3_prec(pflbm3d_t* h, double* phi, double* u, double* p)
+cudaError_t macro3_prec(pflbm3d_t* h, double* phi, double* u, double* p, float* fphi = nullptr, float* fu = nullptr,
+                        float* fp = nullptr)
 {
     Args3<PREC> a = make3<PREC>(h, h->cur);
     a.o_phi = phi;
     a.o_u = u;
     a.o_p = p;
+    a.f_phi = fphi;
+    a.f_u = fu;
+    a.f_p = fp;
     dim3 b(32, 8), g = grid3(h);
     k3_phi<PREC><<<g, b, 0, h->stream>>>(a);
     if (h->n_ghosts) k3_ghost<PREC><<<(h->n_ghosts + 255) / 256, 256, 0, h->stream>>>(a, h->ghosts, h->n_ghosts);
@@ -865,6 +888,12 @@ cudaError_t launch_step(pflbm3d_t* h)
 cudaError_t launch_macro(pflbm3d_t* h, double* phi, double* u, double* p)
 {
     return h->precision == PFLBM_FP64 ? macro3_prec<PFLBM_FP64>(h, phi, u, p) : macro3_prec<PFLBM_FP32>(h, phi, u, p);
+}
+
+cudaError_t launch_macro_f32(pflbm3d_t* h, float* phi, float* u, float* p)
+{
+    return h->precision == PFLBM_FP64 ? macro3_prec<PFLBM_FP64>(h, nullptr, nullptr, nullptr, phi, u, p)
+                                      : macro3_prec<PFLBM_FP32>(h, nullptr, nullptr, nullptr, phi, u, p);
 }
 
 cudaError_t launch_init(pflbm3d_t* h)

@@ -55,7 +55,8 @@ class Params3D(ctypes.Structure):
                 ("M", ctypes.c_double), ("tau_f", ctypes.c_double), ("rho_l", ctypes.c_double),
                 ("rho_g", ctypes.c_double), ("tau_g", ctypes.c_double), ("precision", ctypes.c_int),
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("step_path", ctypes.c_int),
-                ("fused_zc", ctypes.c_int), ("dgdt_mode", ctypes.c_int)]
+                ("fused_zc", ctypes.c_int), ("dgdt_mode", ctypes.c_int),
+                ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p)]
 
 
 class Wall3D(ctypes.Structure):
@@ -464,13 +465,14 @@ class Solver3D:
 
     ``solid``: uint8 [nz, ny, nx] mask (1 = solid; planes z = 0, 1, nz-2,
     nz-1 solid). ``precision``: "fp64" or "fp32". ``step_path``: "auto",
-    "fused" (one launch per step) or "three_pass". The library allocates its own device
-    memory; work runs on ``stream`` (default: the current stream).
+    "fused" (one launch per step) or "three_pass". Work runs on ``stream``
+    (default: the current stream). Memory comes from PyTorch's caching
+    allocator unless ``torch_memory=False`` (then cudaMalloc).
     """
 
     def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
                  rho_l=1.0, rho_g=0.1, tau_g=0.0, precision="fp32", device=None, stream=None,
-                 step_path="auto", fused_zc=0, dgdt_mode=0):
+                 step_path="auto", fused_zc=0, dgdt_mode=0, torch_memory=True):
         import torch
         L = lib()
         solid = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -492,6 +494,10 @@ class Solver3D:
         p.step_path = {"auto": 0, "fused": 1, "three_pass": 2}[step_path]
         p.fused_zc = int(fused_zc)
         p.dgdt_mode = int(dgdt_mode)
+        if torch_memory:
+            p.alloc = _TORCH_ALLOC
+            p.free = _TORCH_FREE
+            p.alloc_ctx = ctypes.c_void_p(_alloc_ctx(dev, stream.cuda_stream))
         h = _H()
         _check(L.pflbm3d_create(ctypes.byref(h), ctypes.byref(p)))
         self._h = h

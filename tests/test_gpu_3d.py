@@ -179,10 +179,11 @@ def test_checkpoint_resume_3d(precision):
         s.close()
 
 
-def test_get_f32_is_get_rounded_3d():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_get_f32_is_get_rounded_3d(precision):
     from paper_2312_00369_gb300 import pflbm
     c = oj.case3d_by_name("sphere3d")
-    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp32", **c.physical())
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision=precision, **c.physical())
     for d in c.droplets:
         s.init_droplet(*d)
     s.step(20)
@@ -250,3 +251,23 @@ def test_rejects_bad_mask_3d():
     s = np.zeros((12, 8, 8), np.uint8)
     with pytest.raises(pflbm.PflbmError):
         pflbm.Solver3D(s)
+
+
+@pytest.mark.parametrize("path", ["three_pass", "fused"])
+def test_allocator_choice_does_not_change_results_3d(path):
+    # the default takes device memory from PyTorch's caching allocator; with
+    # torch_memory=False the library calls cudaMalloc. Same state either way.
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.case3d_by_name("sphere3d")
+    outs = []
+    for tm in (True, False):
+        s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp32", step_path=path,
+                           torch_memory=tm, **c.physical())
+        for d in c.droplets:
+            s.init_droplet(*d)
+        s.step(40)
+        s.check()
+        outs.append(s.get() + (s.mass(),))
+        s.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))

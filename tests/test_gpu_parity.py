@@ -157,7 +157,7 @@ def test_full_size_many_droplets_sampled_columns():
         assert np.max(np.abs(p[:, x] - r["p"])) <= 1e-6
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16"])
 def test_get_f32_is_get_rounded(precision):
     # the FP32 read-back is the FP64 one rounded to nearest, element by element
     case = oj.case_by_name("incline45_ragged")
@@ -297,6 +297,19 @@ def test_bad_mask_and_arguments():
     with pytest.raises(PflbmError) as e:
         Solver(solid, tau_f=0.4)
     assert e.value.code == EINVAL
+    # a non-finite angle anywhere in the field (found on the device at create)
+    for bad in (np.nan, np.inf):
+        field = np.full(solid.shape, 60.0, np.float32)
+        field[11, 17] = bad
+        with pytest.raises(PflbmError) as e:
+            Solver(solid, theta_field=field)
+        assert e.value.code == EINVAL
+    field = np.full(solid.shape, 60.0, np.float32)
+    s = Solver(solid, theta_field=field)     # the same field, finite: accepted
+    s.init_droplet(15, 1.5, 5)
+    s.step(3)
+    s.check()
+    s.close()
 
 
 def test_repeated_init_and_steps_match_oracle():
