@@ -663,6 +663,9 @@ StepArgs<PREC> make_args(pflbm_t* h)
 // ---------------------------------------------------------------------------
 // Eq. initialphi over the box x in [xlo, xlo + xw) (x periodic), y in
 // [ylo, yhi), combined with the field by maximum (a replacing call cleared it).
+// F32: the profile in FP32 (solves whose arithmetic is FP32 or 16-bit storage;
+// the FP64 tanh is slow on this part), else in FP64.
+template <bool F32>
 __global__ void k_init_droplet(const uint8_t* __restrict__ cls, double* __restrict__ phi, int nx, int ny,
                                int pitch, int xlo, int xw, int ylo, int yhi, double x0, double y0, double R,
                                double W)
@@ -682,7 +685,8 @@ __global__ void k_init_droplet(const uint8_t* __restrict__ cls, double* __restri
     // the bounding box's corners are skipped like the nodes outside it
     const double reach = fabs(R) + 10.0 * W;
     if (r2 > reach * reach) return;
-    const double v = 0.5 + 0.5 * tanh(2.0 * (R - sqrt(r2)) / W);
+    const double v = F32 ? (double)(0.5f + 0.5f * tanhf(2.0f * ((float)R - sqrtf((float)r2)) / (float)W))
+                         : 0.5 + 0.5 * tanh(2.0 * (R - sqrt(r2)) / W);
     if (v > phi[k]) phi[k] = v;
 }
 
@@ -851,8 +855,12 @@ cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, 
         xw = (int)(ceil(x0 + reach) - floor(x0 - reach)) + 1;
     }
     dim3 b(32, 8), g = grid2d(xw, yhi - ylo + 1, b);
-    k_init_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yhi + 1, x0, y0,
-                                           R, h->prm.W);
+    if (h->precision == PFLBM_FP64)
+        k_init_droplet<false><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yhi + 1,
+                                                      x0, y0, R, h->prm.W);
+    else
+        k_init_droplet<true><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yhi + 1,
+                                                     x0, y0, R, h->prm.W);
     return cudaGetLastError();
 }
 

@@ -637,6 +637,9 @@ __global__ void k3_wet(const double* av, C* wet, size_t n, double coef)
 // Outside r = R + 10 W the tanh profile is exactly 0 in FP64, so only the
 // droplet's bounding box (periodic in x and y) is evaluated; a replacing
 // call clears the field first.
+// F32: the profile in FP32 (solves whose arithmetic is FP32; the FP64 tanh is
+// slow on this part), else in FP64.
+template <bool F32>
 __global__ void k3_droplet(const uint8_t* cls, double* phi, int nx, int ny, int pitch, int xlo, int xw, int ylo,
                            int yw, int zlo, double x0, double y0, double z0, double R, double W)
 {
@@ -659,7 +662,8 @@ __global__ void k3_droplet(const uint8_t* cls, double* phi, int nx, int ny, int 
     // the bounding box's corners are skipped like the nodes outside it
     const double reach = fabs(R) + 10.0 * W;
     if (r2 > reach * reach) return;
-    const double v = 0.5 + 0.5 * tanh(2.0 * (R - sqrt(r2)) / W);
+    const double v = F32 ? (double)(0.5f + 0.5f * tanhf(2.0f * ((float)R - sqrtf((float)r2)) / (float)W))
+                         : 0.5 + 0.5 * tanh(2.0 * (R - sqrt(r2)) / W);
     if (v > phi[k]) phi[k] = v;
 }
 
@@ -941,8 +945,12 @@ cudaError_t launch_droplet(pflbm3d_t* h, int xlo, int xw, int ylo, int yw, int z
                            double z0, double R)
 {
     dim3 b(32, 8), g((xw + 31) / 32, (yw + 7) / 8, zn);
-    k3_droplet<<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yw, zlo, x0, y0, z0, R,
-                                       h->prm.W);
+    if (h->precision == PFLBM_FP64)
+        k3_droplet<false><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yw, zlo, x0,
+                                                  y0, z0, R, h->prm.W);
+    else
+        k3_droplet<true><<<g, b, 0, h->stream>>>(h->cls, h->phi0, h->nx, h->ny, h->pitch, xlo, xw, ylo, yw, zlo, x0,
+                                                 y0, z0, R, h->prm.W);
     return cudaGetLastError();
 }
 
