@@ -135,7 +135,9 @@ int pflbm_set_theta_field(pflbm_t* h, const float* theta_deg);
 /* Initial droplet of Eq. initialphi, phi = 1/2 + 1/2 tanh(2 (R - r) / W)
  * with r the x-periodic distance to (x0, y0). The first call after create or
  * after a step replaces phi; further calls keep the pointwise maximum. Sets
- * u = 0, p = 0 (f_i = 0) and g_i = g_i^eq(phi, mu) (Eq. H_i). Asynchronous. */
+ * u = 0, p = 0 (f_i = 0) and g_i = g_i^eq(phi, mu) (Eq. H_i). The profile
+ * and mu are evaluated in FP64 for PFLBM_FP64 handles, in FP32 otherwise
+ * (r itself in FP64); beyond r = |R| + 10 W phi is 0. Asynchronous. */
 int pflbm_init_droplet(pflbm_t* h, double x0, double y0, double R);
 /* General initial field phi [ny][nx] (host, copied; values on zeta = 0 nodes
  * are ignored); same initial populations as above. */
@@ -304,7 +306,8 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p);
 void pflbm3d_destroy(pflbm3d_t* h);
 /* Initial field: tanh sphere of radius R centred at (x0, y0, z0) (Eq.
  * initialphi), periodic in x and y; the first call after creation or a step
- * replaces the field, later calls take the maximum. */
+ * replaces the field, later calls take the maximum. Precision and reach as
+ * for pflbm_init_droplet. */
 int pflbm3d_init_droplet(pflbm3d_t* h, double x0, double y0, double z0, double R);
 /* Initial field from a host array [nz][ny][nx] (values on zeta = 0 nodes are
  * ignored). */
