@@ -27,6 +27,13 @@ using namespace pfk;
 #ifndef PFLBM3D_STEP_MINB
 #define PFLBM3D_STEP_MINB 4   // resident 256-thread CTAs per SM asked of the FP32 step kernel (64 registers)
 #endif
+#ifndef PFLBM3D_PHI_AHEAD
+// k3_phi: L2 prefetch of the tile this many CTAs later in launch order (0:
+// off). 1216 is one wave (8 resident CTAs on each of 152 SMs); measured
+// optimum, with 2432 as good and 4864 already slower. The same prefetch in
+// k3_step, whose tiles read eight times the bytes, slows it at every distance.
+#define PFLBM3D_PHI_AHEAD 1216
+#endif
 #ifndef PFLBM3D_FUSED_MINB
 #define PFLBM3D_FUSED_MINB 4  // the same for the fused z-marching kernel
 #endif
@@ -86,6 +93,7 @@ struct Args3 {
     double* o_phi;
     double* o_u;
     double* o_p;
+    int pf_dx, pf_dy, pf_dz;   // k3_phi L2 prefetch target: PFLBM3D_PHI_AHEAD CTAs on, in tiles
     float* f_phi;     // the same fields rounded to float (read-back only)
     float* f_u;
     float* f_p;
@@ -132,6 +140,27 @@ __device__ __forceinline__ void pull_g7(const Args3<PREC>& a, int x, int y, int 
 template <typename C>
 __device__ __forceinline__ C sum6(const C v[7]) { return ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]); }
 
+// L2 prefetch, for the phi pass, of the g rows and node bytes of the tile
+// PFLBM3D_PHI_AHEAD CTAs later in launch order: (pf_dx, pf_dy, pf_dz) tiles
+// from this one (32 x 8 at one z). Warps 0 and 1 only, one row segment per
+// thread (at most 128 B, on a 128 B line: x0 is a multiple of 32, the pitch
+// of 64). Every address lies inside the arrays: the tile exists, y < ny.
+template <int PREC>
+__device__ __forceinline__ void prefetch_phi_rows_l2(const Args3<PREC>& a)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, q = tid >> 3;
+    if (PREC == PFLBM_FP64 || q >= 8) return;
+    int tx = blockIdx.x + a.pf_dx, ty = blockIdx.y + a.pf_dy, tz = blockIdx.z + a.pf_dz;
+    if (tx >= (int)gridDim.x) { tx -= gridDim.x; ++ty; }
+    if (ty >= (int)gridDim.y) { ty -= gridDim.y; ++tz; }
+    const int y = ty * 8 + (tid & 7);
+    if (tz >= (int)gridDim.z || y >= a.ny) return;
+    const size_t row = ((size_t)tz * a.ny + y) * a.pitch + tx * 32;
+    const void* p = q == 0 ? (const void*)(a.g0_in + row)
+                  : q < 7 ? (const void*)(a.g_in + q * (size_t)a.plane + row) : (const void*)(a.cls + row);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // (1) phi on zeta = 1 nodes. The node byte and the plain pull are issued
 // together (one memory latency, not two); a warp with a bounce-back link
 // then pulls again with the checks. Planes 0 and nz - 1 hold no zeta = 1
@@ -141,6 +170,7 @@ template <int PREC>
 __global__ void __launch_bounds__(256) k3_phi(Args3<PREC> a)
 {
     using C = typename Store<PREC>::C;
+    if (PFLBM3D_PHI_AHEAD > 0) prefetch_phi_rows_l2<PREC>(a);
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     if (x >= a.nx || y >= a.ny || z == 0 || z == a.nz - 1) return;
     const int k = (z * a.ny + y) * a.pitch + x;
@@ -819,6 +849,14 @@ Args3<PREC> make3(pflbm3d_t* h, int in)
     a.alpha = (C)q.alpha;
     a.dgdt = q.dgdt_mode;
     a.status = h->dstatus;
+    {
+        // the prefetch distance of k3_phi split into tiles along x, y and z of
+        // its grid (grid3: 32 x 8 tiles, one z per CTA)
+        const long long gx = (h->nx + 31) / 32, gy = (h->ny + 7) / 8, ahead = PFLBM3D_PHI_AHEAD;
+        a.pf_dx = (int)(ahead % gx);
+        a.pf_dy = (int)((ahead / gx) % gy);
+        a.pf_dz = (int)(ahead / (gx * gy));
+    }
     return a;
 }
 
