@@ -395,7 +395,7 @@ def run_wsweep(args, torch, rank, world, local):
                     sv.init_droplet(*d)
                 runs.append((W, th, c, sv))
     b = Batch([r[3] for r in runs])
-    steps = args.steps if args.steps > 1000 else 20000
+    steps = long_solve_steps(args)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.step(steps)
@@ -432,13 +432,21 @@ def angle_cases_3d():
     return out
 
 
+def long_solve_steps(args, default=20000):
+    """Steps of a workload that runs solves to equilibrium: --steps when given
+    on the command line, else `default` (the timed-step default is far too
+    short for an equilibrium angle)."""
+    given = any(a == "--steps" or a.startswith("--steps=") for a in sys.argv[1:])
+    return args.steps if given else default
+
+
 def run_angles3d(args, torch, rank, world, local):
     """Equilibrium contact angles in 3D (the 3D column of the paper's angle
     comparison, Secs. 3.1-3.3): every case of angle_cases_3d() run for
     `steps` (default 20000) with the (1/2) dG/dt term as --dgdt (default for
     this workload: omitted), FP32; the fitted angle and its error per case."""
     from paper_2312_00369_gb300.pflbm import PflbmError, Solver3D
-    steps = args.steps if args.steps > 1000 else 20000
+    steps = long_solve_steps(args)
     stream = torch.cuda.Stream(device=local)
     table, lu, busy = {}, 0, 0.0
     for kind, th, c in angle_cases_3d():
@@ -635,9 +643,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     if args.workload in ("batched", "serving", "wsweep", "many_flat3d", "angles3d"):
-        if args.workload in ("angles3d", "serving") and "--dgdt" not in sys.argv:
+        if args.workload in ("angles3d", "serving", "wsweep") and "--dgdt" not in sys.argv:
             # long solves: the (1/2) dG/dt term omitted unless asked for (the
-            # backward difference is not at equilibrium by 1e4-2e4 steps)
+            # backward difference is not at equilibrium by 1e4-2e4 steps, and
+            # on the shallow staircase of the W sweep it goes unstable)
             args.dgdt = 1
         {"batched": run_batched, "serving": run_serving, "wsweep": run_wsweep,
          "many_flat3d": run_3d, "angles3d": run_angles3d}[args.workload](

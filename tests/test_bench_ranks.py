@@ -73,3 +73,17 @@ def test_reference_arm_prints_on_rank_zero_only():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_equilibrium_workloads_keep_their_step_count(monkeypatch):
+    # the angle and W-sweep workloads run to equilibrium: the timed-step
+    # default of the throughput workloads must not shorten them
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    args = argparse.Namespace(steps=2000)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "angles3d"])
+    assert bench.long_solve_steps(args) == 20000
+    for given in (["--steps", "2000"], ["--steps=2000"]):
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "angles3d"] + given)
+        assert bench.long_solve_steps(args) == 2000
