@@ -19,7 +19,7 @@ import time
 from . import pflbm
 
 CANDIDATES = [dict(ctas_per_sm=c, tiles_per_item=g, order=o, use_graph=1)
-              for c in (0, 4, 2) for g in (1, 2, 4) for o in (0, 1)]
+              for c in (0, 4) for g in (1, 2, 4, 8) for o in (0, 1)]
 
 
 def cache_path():
