@@ -62,6 +62,7 @@ def lib():
         L.or_mass.argtypes = [ctypes.c_void_p]
         L.or_budget.argtypes = [ctypes.c_void_p, _dp]
         L.or_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+        L.or_set_state.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.or_steps.restype = ctypes.c_long
         L.or_steps.argtypes = [ctypes.c_void_p]
         L.or_contact_angle.restype = ctypes.c_int
@@ -253,6 +254,14 @@ class Oracle:
         sp = np.zeros((self.ny, self.nx))
         lib().or_state(self._h, _p(f), _p(g), _p(sp))
         return f, g, sp
+
+    def set_state(self, f, g):
+        """Overwrite the post-streaming f, g (arrays [9, ny, nx], paper order);
+        the u.grad(phi) history and the first-step flag are kept."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.shape == g.shape == (9, self.ny, self.nx)
+        lib().or_set_state(self._h, _p(f), _p(g))
 
     @property
     def steps(self):

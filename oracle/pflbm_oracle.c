@@ -770,6 +770,13 @@ void or_state(const or_solver* s, double* f, double* g, double* s_prev)
     if (s_prev) memcpy(s_prev, s->s_prev, (size_t)s->N * sizeof(double));
 }
 
+void or_set_state(or_solver* s, const double* f, const double* g)
+{
+    size_t n = (size_t)(Q * s->N) * sizeof(double);
+    memcpy(s->f, f, n);
+    memcpy(s->g, g, n);
+}
+
 long or_steps(const or_solver* s)
 {
     return s->steps;

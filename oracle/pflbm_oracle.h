@@ -18,8 +18,9 @@
  *   - the stored populations f_i, g_i are the post-streaming values (the
  *     state at the start of a time step).
  *
- * Parity pinning of each function is stated beside it; the functions marked
- * "parity unpinned" follow a reading of the paper that no closed form fixes.
+ * Each function is pinned by the tests against the paper's definitions; the
+ * readings where the paper is silent (ghost value, doubly-unknown bounce-back,
+ * the (1/2) dG/dt history) are pinned by hand-worked values.
  */
 #ifndef PFLBM_ORACLE_H
 #define PFLBM_ORACLE_H
@@ -104,6 +105,10 @@ double or_mass(const or_solver* s);
 void or_budget(const or_solver* s, double out[4]);
 /* Raw state access for tests: f, g as [9][ny*nx] in paper order, s_prev. */
 void or_state(const or_solver* s, double* f, double* g, double* s_prev);
+/* Raw state for tests: overwrite the post-streaming f and g ([9][ny*nx], paper
+ * order). The u.grad(phi) history and whether a step has been taken are kept,
+ * so a hand-set state can be stepped as the first or as a later step. */
+void or_set_state(or_solver* s, const double* f, const double* g);
 long or_steps(const or_solver* s);
 
 /* ---- contact-angle measurement (a reading; the paper does not say how) ---- */
