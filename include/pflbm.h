@@ -175,7 +175,9 @@ int pflbm_mass(pflbm_t* h, double* out);
  * [ny][nx] bytes or NULL; d_out: one double, written asynchronously on
  * `stream` (cudaStream_t, NULL = default stream) of the current device.
  * The first call on a device looks up the array's device address; make that
- * first call before any stream capture. Calls whose kernels overlap on the
+ * first call before any stream capture. The address is kept per CUDA context:
+ * after cudaDeviceReset the next call looks it up again, so it too belongs
+ * before any capture. Calls whose kernels overlap on the
  * GPU share the array and race. Errors: EINVAL for NULL phi/out, nx or
  * ny < 1, or nx * ny > 33,554,432 (the static limit); ECUDA. */
 int pflbm_phi_mass_noalloc(const double* d_phi, const uint8_t* d_zeta, int nx, int ny, double* d_out,
@@ -210,8 +212,13 @@ size_t pflbm_footprint_bytes(int nx, int ny, int precision);
 
 /* Checkpoint: *len in: capacity of buf, out: bytes needed/written. buf may be
  * NULL to query the size. The blob holds the populations, the u.grad(phi)
- * history, the step count and the parameters; load requires a handle of the
- * same size and precision. Both synchronous. */
+ * history, the step count, the parameters and flags (derived beta, kappa,
+ * alpha, tau_f, tau_g, rho_l, rho_g, W, sigma, M; nu_l, nu_g, gx, gy;
+ * dgdt_mode, chi_case) and a 64-bit fingerprint of the node bytes and
+ * wetting coefficients (so of the solid mask and the angle field where it
+ * acts). Load requires a handle of the same size and precision whose
+ * parameters, flags and fingerprint are equal; otherwise PFLBM_EINVAL and the
+ * handle is unchanged. Both synchronous. */
 int pflbm_save(pflbm_t* h, void* buf, size_t* len);
 int pflbm_load(pflbm_t* h, const void* buf, size_t len);
 
@@ -328,11 +335,13 @@ int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av);
 int pflbm3d_check(pflbm3d_t* h);
 /* Steps taken since the last initialisation (-1 for a NULL handle). */
 int64_t pflbm3d_steps(const pflbm3d_t* h);
-/* Checkpoint of the state (populations, u.grad(phi) history, step count)
- * into a caller buffer; buf == NULL returns the size in *len. pflbm3d_load
- * restores it into a handle of the same size and precision, after which the
- * steps continue bit for bit as if uninterrupted. Synchronous. Errors:
- * EINVAL (buffer too small, not a checkpoint, size or precision differs). */
+/* Checkpoint of the state (populations, u.grad(phi) history, step count,
+ * the derived parameters, dgdt_mode and a fingerprint of the node bytes and
+ * wetting coefficients) into a caller buffer; buf == NULL returns the size in
+ * *len. pflbm3d_load restores it into a handle of the same size, precision,
+ * parameters and geometry, after which the steps continue bit for bit as if
+ * uninterrupted. Synchronous. Errors: EINVAL (buffer too small, not a
+ * checkpoint, or any of those differs; the handle is then unchanged). */
 int pflbm3d_save(pflbm3d_t* h, void* buf, size_t* len);
 int pflbm3d_load(pflbm3d_t* h, const void* buf, size_t len);
 

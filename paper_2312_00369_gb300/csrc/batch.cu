@@ -46,21 +46,6 @@ struct pflbm_batch {
 
 namespace {
 
-struct Guard {
-    int prev = -1;
-    explicit Guard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~Guard()
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 int balloc(pflbm_batch_t* b, void** p, size_t bytes)
 {
     *p = nullptr;
@@ -243,7 +228,7 @@ int pflbm_batch_create(pflbm_batch_t** out, pflbm_t* const* hs, int count, const
     if (b->sched.tiles_per_item < 1) b->sched.tiles_per_item = 1;
     b->args_bytes = step_args_bytes(b->precision);
     b->hs.assign(hs, hs + count);
-    Guard g(b->device);
+    DeviceGuard g(b->device);
     if (int rc = upload(b)) {
         pflbm_batch_destroy(b);
         return rc;
@@ -256,7 +241,7 @@ int pflbm_batch_set(pflbm_batch_t* b, pflbm_t* const* hs, int count)
 {
     if (!b || !hs || count < 1) return set_error(PFLBM_EINVAL, "batch: invalid arguments");
     if (int rc = check_members(hs, count, b->precision, b->device, b->stream)) return rc;
-    Guard g(b->device);
+    DeviceGuard g(b->device);
     b->hs.assign(hs, hs + count);
     return upload(b);
 }
@@ -266,7 +251,7 @@ int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
     if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
     if (n < 0) return set_error(PFLBM_EINVAL, "batch: negative step count");
     if (n == 0) return PFLBM_OK;
-    Guard g(b->device);
+    DeviceGuard g(b->device);
     bool stale = false;
     for (size_t i = 0; i < b->hs.size(); ++i) {
         pflbm_t* h = b->hs[i];
@@ -322,7 +307,7 @@ int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* no
 void pflbm_batch_destroy(pflbm_batch_t* b)
 {
     if (!b) return;
-    Guard g(b->device);
+    DeviceGuard g(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
     for (int k = 0; k < 2; ++k) bfree(b, b->d_args[k], b->args_bytes * b->cap_lattices);

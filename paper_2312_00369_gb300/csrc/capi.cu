@@ -39,21 +39,6 @@ int cuda_fail(cudaError_t e, const char* where)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 int dalloc(pflbm_t* h, void** p, size_t bytes)
 {
     *p = nullptr;
@@ -614,14 +599,40 @@ int pflbm_status(const pflbm_t* h)
 }
 
 namespace {
+// Checkpoint header. A state is only meaningful with the parameters, flags
+// and geometry that produced it, so all of them are recorded and compared.
 struct Blob {
     uint64_t magic;
     int32_t version, nx, ny, precision;
     int64_t steps;
-    int32_t replace_phi, pad;
-    double params[10];
+    int32_t replace_phi, dgdt_mode;
+    double params[10];    // beta, kappa, alpha, tau_f, tau_g, rho_l, rho_g, W, sigma, M
+    double extra[4];      // nu_l, nu_g, gx, gy
+    int32_t chi_case, pad;
+    uint64_t geometry;    // fingerprint of the node bytes and wetting coefficients
 };
 constexpr uint64_t kMagic = 0x4d424c4650ULL;  // "PFLBM"
+constexpr int32_t kBlobVersion = 2;
+
+void fill_params(const Params& q, double pv[10], double ex[4])
+{
+    const double a[10] = {q.beta, q.kappa, q.alpha, q.tau_f, q.tau_g, q.rho_l, q.rho_g, q.W, q.sigma, q.M};
+    const double b[4] = {q.nu_l, q.nu_g, q.gx, q.gy};
+    std::memcpy(pv, a, sizeof(a));
+    std::memcpy(ex, b, sizeof(b));
+}
+
+// Geometry fingerprint of the handle (synchronous).
+int geometry_fingerprint(pflbm_t* h, uint64_t* out)
+{
+    unsigned long long* d = (unsigned long long*)(h->red + mass_scratch_doubles() - 16);
+    CK(launch_fingerprint(h->cls, h->wet, h->precision == PFLBM_FP64, h->nx, h->ny, h->pitch, d, h->stream));
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *out = v;
+    return PFLBM_OK;
+}
 }  // namespace
 
 int pflbm_save(pflbm_t* h, void* buf, size_t* len)
@@ -636,15 +647,16 @@ int pflbm_save(pflbm_t* h, void* buf, size_t* len)
     if (int rc = materialize(h)) return rc;
     Blob b{};
     b.magic = kMagic;
-    b.version = 1;
+    b.version = kBlobVersion;
     b.nx = h->nx;
     b.ny = h->ny;
     b.precision = h->precision;
     b.steps = h->steps;
     b.replace_phi = h->replace_phi;
-    const Params& q = h->prm;
-    double pv[10] = {q.beta, q.kappa, q.alpha, q.tau_f, q.tau_g, q.rho_l, q.rho_g, q.W, q.sigma, q.M};
-    std::memcpy(b.params, pv, sizeof(pv));
+    b.dgdt_mode = h->prm.dgdt_mode;
+    b.chi_case = h->prm.chi_case;
+    fill_params(h->prm, b.params, b.extra);
+    if (int rc = geometry_fingerprint(h, &b.geometry)) return rc;
     std::memcpy(buf, &b, sizeof(b));
     char* dst = (char*)buf + sizeof(Blob);
     CK(cudaMemcpyAsync(dst, h->pop[h->cur], s.pop, cudaMemcpyDeviceToHost, h->stream));
@@ -661,11 +673,19 @@ int pflbm_load(pflbm_t* h, const void* buf, size_t len)
     Blob b;
     std::memcpy(&b, buf, sizeof(b));
     Sizes s = sizes_of(h->nx, h->ny, h->precision);
-    if (b.magic != kMagic || b.version != 1) return fail(PFLBM_EINVAL, "not a pflbm checkpoint");
+    if (b.magic != kMagic || b.version != kBlobVersion) return fail(PFLBM_EINVAL, "not a pflbm checkpoint");
     if (b.nx != h->nx || b.ny != h->ny || b.precision != h->precision)
         return fail(PFLBM_EINVAL, "checkpoint size or precision differs from the handle");
     if (len < sizeof(Blob) + s.pop + s.sprev) return fail(PFLBM_EINVAL, "blob truncated");
+    double pv[10], ex[4];
+    fill_params(h->prm, pv, ex);
+    if (std::memcmp(pv, b.params, sizeof(pv)) != 0 || std::memcmp(ex, b.extra, sizeof(ex)) != 0 ||
+        b.dgdt_mode != h->prm.dgdt_mode || b.chi_case != h->prm.chi_case)
+        return fail(PFLBM_EINVAL, "checkpoint parameters differ from the handle's");
     DeviceGuard g(h->device);
+    uint64_t geo = 0;
+    if (int rc = geometry_fingerprint(h, &geo)) return rc;
+    if (geo != b.geometry) return fail(PFLBM_EINVAL, "checkpoint geometry or angle field differs from the handle's");
     const char* src = (const char*)buf + sizeof(Blob);
     CK(cudaMemcpyAsync(h->pop[h->cur], src, s.pop, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->sprev, src + s.pop, s.sprev, cudaMemcpyHostToDevice, h->stream));

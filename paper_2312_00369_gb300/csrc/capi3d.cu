@@ -37,7 +37,16 @@ int materialize3(pflbm3d_t* h)
     if (!h->init_pending) return PFLBM_OK;
     CK3(launch_init(h));
     CK3(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+    if (h->hstatus) h->hstatus[0] = 0;
     h->init_pending = false;
+    return PFLBM_OK;
+}
+
+// The device status word as last copied to the host (after a step or a
+// check): a solve that reported NaN or |u| >= 0.3 is not stepped further.
+int read_status3(const pflbm3d_t* h)
+{
+    if (h->hstatus && h->hstatus[0] != 0) return fail3(PFLBM_ENUMERIC, "NaN or |u| >= 0.3 detected on the device");
     return PFLBM_OK;
 }
 
@@ -69,6 +78,7 @@ void release3(pflbm3d_t* h)
             cudaFree(a.first);
     }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->hstatus) cudaFreeHost(h->hstatus);
     delete h;
 }
 
@@ -125,7 +135,7 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
     int dev = p->device;
     if (dev < 0) cudaGetDevice(&dev);
     h->device = dev;
-    cudaSetDevice(dev);
+    DeviceGuard guard(dev);
     Params& q = h->prm;
     q.sigma = p->sigma;
     q.W = p->W;
@@ -157,6 +167,13 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
             return rc;
         }
     }
+    if (cudaMallocHost((void**)&h->hstatus, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        h->hstatus = nullptr;
+        release3(h);
+        return fail3(PFLBM_ENOMEM, "pinned status word");
+    }
+    h->hstatus[0] = 0;
     cudaMemsetAsync(h->pop[0], 0, pop3_bytes(p->precision, plane), h->stream);
     cudaMemsetAsync(h->pop[1], 0, pop3_bytes(p->precision, plane), h->stream);
     cudaMemsetAsync(h->phi, 0, plane * cs, h->stream);
@@ -221,11 +238,17 @@ int pflbm3d_create(pflbm3d_t** out, const pflbm3d_params_t* p)
     return PFLBM_OK;
 }
 
-void pflbm3d_destroy(pflbm3d_t* h) { release3(h); }
+void pflbm3d_destroy(pflbm3d_t* h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    release3(h);
+}
 
 int pflbm3d_init_droplet(pflbm3d_t* h, double x0, double y0, double z0, double R)
 {
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    DeviceGuard g(h->device);
     if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(z0) || !std::isfinite(R))
         return fail3(PFLBM_EINVAL, "non-finite droplet");
     if (h->replace_phi) CK3(cudaMemsetAsync(h->phi0, 0, (size_t)h->nz * h->ny * h->pitch * 8, h->stream));
@@ -255,6 +278,7 @@ int pflbm3d_init_droplet(pflbm3d_t* h, double x0, double y0, double z0, double R
 int pflbm3d_init_phi(pflbm3d_t* h, const double* phi)
 {
     if (!h || !phi) return fail3(PFLBM_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
     CK3(cudaMemcpy2DAsync(h->phi0, h->pitch * 8, phi, h->nx * 8, h->nx * 8, (size_t)h->ny * h->nz,
                           cudaMemcpyHostToDevice, h->stream));
     CK3(cudaStreamSynchronize(h->stream));
@@ -267,19 +291,26 @@ int pflbm3d_init_phi(pflbm3d_t* h, const double* phi)
 int pflbm3d_step(pflbm3d_t* h, int64_t n)
 {
     if (!h || n < 0) return fail3(PFLBM_EINVAL, "invalid arguments");
+    if (int rc = read_status3(h)) return rc;
+    DeviceGuard g(h->device);
     if (int rc = materialize3(h)) return rc;
     for (int64_t t = 0; t < n; ++t) {
         CK3(launch_step(h));
         h->cur ^= 1;
         h->steps += 1;
     }
-    if (n > 0) h->replace_phi = true;
+    if (n > 0) {
+        h->replace_phi = true;
+        // refreshed without waiting; read by the next step
+        CK3(cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    }
     return PFLBM_OK;
 }
 
 int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p)
 {
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    DeviceGuard g(h->device);
     if (int rc = materialize3(h)) return rc;
     const size_t N = (size_t)h->nx * h->ny * h->nz;
     if (!h->out)
@@ -296,6 +327,7 @@ int pflbm3d_get(pflbm3d_t* h, double* phi, double* u, double* p)
 int pflbm3d_get_f32(pflbm3d_t* h, float* phi, float* u, float* p)
 {
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    DeviceGuard g(h->device);
     if (int rc = materialize3(h)) return rc;
     const size_t N = (size_t)h->nx * h->ny * h->nz;
     if (!h->out_f)
@@ -313,6 +345,7 @@ int pflbm3d_get_f32(pflbm3d_t* h, float* phi, float* u, float* p)
 int pflbm3d_mass(pflbm3d_t* h, double* out)
 {
     if (!h || !out) return fail3(PFLBM_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
     if (int rc = materialize3(h)) return rc;
     double* d = h->red + kMassBlocks + 4;
     CK3(launch_mass(h, d));
@@ -324,6 +357,7 @@ int pflbm3d_mass(pflbm3d_t* h, double* out)
 int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av)
 {
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    DeviceGuard g(h->device);
     if (cls) {
         CK3(cudaMemcpy2DAsync(cls, h->nx, h->cls, h->pitch, h->nx, (size_t)h->ny * h->nz, cudaMemcpyDeviceToHost,
                               h->stream));
@@ -340,6 +374,7 @@ int pflbm3d_geometry(pflbm3d_t* h, uint8_t* cls, double* av)
 int pflbm3d_contact_angle(pflbm3d_t* h, const pflbm3d_wall_t* wall, double* theta_deg, double* sphere, int* npoints)
 {
     if (!h || !wall || !theta_deg) return fail3(PFLBM_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
     if (wall->type != 0 && wall->type != 1) return fail3(PFLBM_EINVAL, "wall type must be 0 or 1");
     if (int rc = materialize3(h)) return rc;
     const size_t N = (size_t)h->nx * h->ny * h->nz;
@@ -370,12 +405,34 @@ int pflbm3d_contact_angle(pflbm3d_t* h, const pflbm3d_wall_t* wall, double* thet
 
 namespace {
 constexpr uint64_t kMagic3 = 0x33444d424c46504bULL;   // checkpoint tag of the 3D state
+// Checkpoint header: the parameters, flags and geometry that produced the
+// state are recorded and compared on load.
 struct Blob3 {
     uint64_t magic;
-    int32_t version, nx, ny, nz, precision, replace_phi;
+    int32_t version, nx, ny, nz, precision, replace_phi, dgdt_mode;
     int64_t steps;
-    double params[10];
+    double params[10];    // beta, kappa, alpha, tau_f, tau_g, rho_l, rho_g, W, sigma, M
+    uint64_t geometry;    // fingerprint of the node bytes and wetting coefficients
 };
+constexpr int32_t kBlob3Version = 2;
+
+void params3(const Params& q, double pv[10])
+{
+    const double a[10] = {q.beta, q.kappa, q.alpha, q.tau_f, q.tau_g, q.rho_l, q.rho_g, q.W, q.sigma, q.M};
+    std::memcpy(pv, a, sizeof(a));
+}
+
+int fingerprint3(pflbm3d_t* h, uint64_t* out)
+{
+    unsigned long long* d = (unsigned long long*)(h->red + kMassBlocks + 2);
+    CK3(launch_fingerprint(h->cls, h->wet, h->precision == PFLBM_FP64, h->nx, (long long)h->ny * h->nz, h->pitch, d,
+                           h->stream));
+    unsigned long long v = 0;
+    CK3(cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+    *out = v;
+    return PFLBM_OK;
+}
 size_t sprev3_bytes(const pflbm3d_t* h)
 {
     return (size_t)h->nz * h->ny * h->pitch * (h->precision == PFLBM_FP64 ? 8 : 4);
@@ -390,19 +447,20 @@ int pflbm3d_save(pflbm3d_t* h, void* buf, size_t* len)
     const size_t need = sizeof(Blob3) + pop + sp;
     if (!buf) { *len = need; return PFLBM_OK; }
     if (*len < need) { *len = need; return fail3(PFLBM_EINVAL, "buffer too small"); }
+    DeviceGuard g(h->device);
     if (int rc = materialize3(h)) return rc;
     Blob3 b{};
     b.magic = kMagic3;
-    b.version = 1;
+    b.version = kBlob3Version;
+    b.dgdt_mode = h->prm.dgdt_mode;
+    if (int rc = fingerprint3(h, &b.geometry)) return rc;
     b.nx = h->nx;
     b.ny = h->ny;
     b.nz = h->nz;
     b.precision = h->precision;
     b.replace_phi = h->replace_phi;
     b.steps = h->steps;
-    const Params& q = h->prm;
-    const double pv[10] = {q.beta, q.kappa, q.alpha, q.tau_f, q.tau_g, q.rho_l, q.rho_g, q.W, q.sigma, q.M};
-    std::memcpy(b.params, pv, sizeof(pv));
+    params3(h->prm, b.params);
     std::memcpy(buf, &b, sizeof(b));
     char* dst = (char*)buf + sizeof(Blob3);
     CK3(cudaMemcpyAsync(dst, h->pop[h->cur], pop, cudaMemcpyDeviceToHost, h->stream));
@@ -417,17 +475,26 @@ int pflbm3d_load(pflbm3d_t* h, const void* buf, size_t len)
     if (!h || !buf || len < sizeof(Blob3)) return fail3(PFLBM_EINVAL, "blob too small");
     Blob3 b;
     std::memcpy(&b, buf, sizeof(b));
-    if (b.magic != kMagic3 || b.version != 1) return fail3(PFLBM_EINVAL, "not a pflbm3d checkpoint");
+    if (b.magic != kMagic3 || b.version != kBlob3Version) return fail3(PFLBM_EINVAL, "not a pflbm3d checkpoint");
     if (b.nx != h->nx || b.ny != h->ny || b.nz != h->nz || b.precision != h->precision)
         return fail3(PFLBM_EINVAL, "checkpoint size or precision differs from the handle");
     const size_t plane = (size_t)h->nz * h->ny * h->pitch;
     const size_t pop = pop3_bytes(h->precision, plane), sp = sprev3_bytes(h);
     if (len < sizeof(Blob3) + pop + sp) return fail3(PFLBM_EINVAL, "blob truncated");
+    double pv[10];
+    params3(h->prm, pv);
+    if (std::memcmp(pv, b.params, sizeof(pv)) != 0 || b.dgdt_mode != h->prm.dgdt_mode)
+        return fail3(PFLBM_EINVAL, "checkpoint parameters differ from the handle's");
+    DeviceGuard g(h->device);
+    uint64_t geo = 0;
+    if (int rc = fingerprint3(h, &geo)) return rc;
+    if (geo != b.geometry) return fail3(PFLBM_EINVAL, "checkpoint geometry differs from the handle's");
     const char* src = (const char*)buf + sizeof(Blob3);
     CK3(cudaMemcpyAsync(h->pop[h->cur], src, pop, cudaMemcpyHostToDevice, h->stream));
     CK3(cudaMemcpyAsync(h->sprev, src + pop, sp, cudaMemcpyHostToDevice, h->stream));
     CK3(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
     CK3(cudaStreamSynchronize(h->stream));
+    if (h->hstatus) h->hstatus[0] = 0;
     h->init_pending = false;
     h->steps = b.steps;
     h->replace_phi = b.replace_phi != 0;
@@ -439,9 +506,11 @@ int64_t pflbm3d_steps(const pflbm3d_t* h) { return h ? h->steps : -1; }
 int pflbm3d_check(pflbm3d_t* h)
 {
     if (!h) return fail3(PFLBM_EINVAL, "NULL handle");
+    DeviceGuard g(h->device);
     CK3(cudaStreamSynchronize(h->stream));
     int st = 0;
     CK3(cudaMemcpy(&st, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h->hstatus) h->hstatus[0] = st;
     return st ? fail3(PFLBM_ENUMERIC, "NaN or |u| >= 0.3 detected on the device") : PFLBM_OK;
 }
 

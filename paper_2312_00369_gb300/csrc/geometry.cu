@@ -170,7 +170,54 @@ __global__ void k_tile_flags(const uint8_t* __restrict__ cls, uint8_t* __restric
 
 dim3 grid2d(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
+// SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014): a bijective
+// mixing of 64 bits.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Fingerprint of a geometry: the sum (mod 2^64) over the nodes of a hash of
+// (node index, node byte, bit pattern of the wetting coefficient). Integer
+// addition is order-free, so the result does not depend on the launch.
+template <typename C>
+__global__ void k_fingerprint(const uint8_t* __restrict__ cls, const C* __restrict__ wet, int nx, long long rows,
+                              int pitch, unsigned long long* out)
+{
+    unsigned long long acc = 0;
+    const long long n = rows * nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / nx, x = i - r * nx;
+        const size_t k = (size_t)r * pitch + x;
+        unsigned long long wb;
+        if constexpr (sizeof(C) == 8) wb = (unsigned long long)__double_as_longlong((double)wet[k]);
+        else wb = (unsigned long long)(unsigned)__float_as_int((float)wet[k]);
+        acc += mix64(mix64(((unsigned long long)i << 8) | cls[k]) ^ wb);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 }  // namespace
+
+cudaError_t launch_fingerprint(const uint8_t* cls, const void* wet, bool wet_fp64, int nx, long long rows, int pitch,
+                               unsigned long long* d_out, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    long long n = rows * nx, blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    if (wet_fp64)
+        k_fingerprint<double><<<(int)blocks, 256, 0, stream>>>(cls, (const double*)wet, nx, rows, pitch, d_out);
+    else
+        k_fingerprint<float><<<(int)blocks, 256, 0, stream>>>(cls, (const float*)wet, nx, rows, pitch, d_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tile_flags(pflbm_t* h)
 {

@@ -13,9 +13,15 @@
 // keeps until the process exits. Host code may not use the array's name as a
 // device address, so the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should therefore come before any stream capture. All calls share the
-// one array: calls whose kernels overlap on the GPU race on it. No element
-// needs clearing: every call writes each partial it later reads.
+// call should therefore come before any stream capture. The cache is keyed on
+// the unique id of the current CUDA context, so after cudaDeviceReset (which
+// unloads the module: the array then lives at a new address) the next call
+// looks the address up again, and that call too should come before any
+// capture. All calls share the one array: calls whose kernels overlap on the
+// GPU race on it. No element needs clearing: every call writes each partial
+// it later reads.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "pflbm_internal.cuh"
@@ -32,7 +38,17 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) double g_mass_scratch[kStaticBlocks];
 
 std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchEntry {
+    unsigned long long ctx_id;   // id of the context the address belongs to (0: none yet)
+    double* ptr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
+
+// Driver entry points, reached through the runtime (no link against libcuda).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -81,7 +97,32 @@ __global__ void __launch_bounds__(kThreads) k_phi_mass_final(const double* __res
     if (threadIdx.x == 0) *out = r;
 }
 
-// Device address of the static scratch for the current device (looked up once).
+// Unique id of the calling thread's current context; 0 when none is current.
+cudaError_t current_context_id(unsigned long long* id)
+{
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess) return e;
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return cudaErrorNotSupported;
+        g_ctx_get_current = (CtxGetCurrentFn)a;
+        g_ctx_get_id = (CtxGetIdFn)b;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (!ctx) return cudaSuccess;
+    if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
+// Device address of the static scratch for the current device, looked up once
+// per context with cudaGetSymbolAddress.
 cudaError_t scratch_for_current_device(double** out)
 {
     int dev = -1;
@@ -89,13 +130,21 @@ cudaError_t scratch_for_current_device(double** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_mass_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = (double*)p;
+    unsigned long long id = 0;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    if (id != 0 && g_scratch[dev].ctx_id == id && g_scratch[dev].ptr) {
+        *out = g_scratch[dev].ptr;
+        return cudaSuccess;
     }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_mass_scratch);   // makes the device's context current
+    if (e != cudaSuccess) return e;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    g_scratch[dev].ctx_id = id;
+    g_scratch[dev].ptr = (double*)p;
+    *out = (double*)p;
     return cudaSuccess;
 }
 

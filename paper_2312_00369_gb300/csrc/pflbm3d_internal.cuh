@@ -27,6 +27,7 @@ struct pflbm3d {
     double* out = nullptr;
     float* out_f = nullptr;     // FP32 read-back scratch (5 dense fields), on first use
     int* dstatus = nullptr;
+    int* hstatus = nullptr;     // pinned host mirror of dstatus[0], refreshed after each pflbm3d_step
     double* pts = nullptr;      // contact-angle crossings (3 doubles each)
     int pts_cap = 0;
     int* ghosts = nullptr;      // indices of the ghost nodes

@@ -65,6 +65,27 @@ __device__ __forceinline__ C cdot(C vx, C vy, C vz)
     else return cdot<X, Z>(vx, vz);
 }
 
+// Makes `dev` the current device for the life of the guard and restores the
+// caller's device on return: every entry point that touches the device
+// takes one, so a caller that switched devices after creating a handle still
+// runs that handle's work on the handle's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Tile of the fused step: TX x TY nodes per CTA, one node per thread.
 constexpr int TX = 32;
 constexpr int TY = 8;
@@ -139,6 +160,11 @@ cudaError_t launch_classify(pflbm_t* h);
 cudaError_t launch_wet(pflbm_t* h);
 cudaError_t launch_links(pflbm_t* h, uint16_t* unknown, uint16_t* doubly);
 cudaError_t launch_tile_flags(pflbm_t* h);
+// Order-free 64-bit fingerprint of the node bytes and wetting coefficients of
+// a [rows][pitch] lattice (first nx columns) into *d_out: checkpoints record
+// it so that a state is only loaded into a handle of the same geometry.
+cudaError_t launch_fingerprint(const uint8_t* cls, const void* wet, bool wet_fp64, int nx, long long rows, int pitch,
+                               unsigned long long* d_out, cudaStream_t stream);
 __host__ __device__ inline int tiles_x(int nx) { return (nx + TX - 1) / TX; }
 __host__ __device__ inline int tiles_y(int ny) { return (ny + TY - 1) / TY; }
 

@@ -170,13 +170,38 @@ def test_checkpoint_resume_3d(precision):
     for x, y in zip(a.get(), b.get()):
         assert np.array_equal(x, y)
     assert a.mass() == b.mass() and b.steps == 55
-    # a checkpoint of another size is refused
+    # a checkpoint of another size, other parameters or another wall is refused
     s2, _ = __import__("paper_2312_00369_gb300.workloads", fromlist=["box3d"]).box3d(40, 20, 20)
-    other = pflbm.Solver3D(s2, precision=precision)
-    with pytest.raises(pflbm.PflbmError):
-        other.load(blob)
-    for s in (a, b, other):
+    bump = c.solid.copy()
+    bump[2, 3:6, 3:6] = 1
+    others = [pflbm.Solver3D(s2, precision=precision),
+              pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision=precision, **{**c.physical(), "tau_f": 0.9}),
+              pflbm.Solver3D(c.solid, theta_deg=c.theta_deg + 1.0, precision=precision, **c.physical()),
+              pflbm.Solver3D(bump, theta_deg=c.theta_deg, precision=precision, **c.physical())]
+    for other in others:
+        with pytest.raises(pflbm.PflbmError) as e:
+            other.load(blob)
+        assert e.value.code == pflbm.EINVAL
+    for s in [a, b] + others:
         s.close()
+
+
+def test_nan_stops_stepping_3d():
+    # a NaN in the initial field trips the device status word; the next step
+    # after the status has reached the host is refused with ENUMERIC
+    from paper_2312_00369_gb300 import pflbm
+    c = oj.case3d_by_name("flat3d")
+    s = pflbm.Solver3D(c.solid, theta_deg=c.theta_deg, precision="fp32", **c.physical())
+    phi = np.zeros((c.solid.shape))
+    phi[10, 10, 20] = np.nan
+    s.init_phi(phi)
+    s.step(3)
+    torch.cuda.synchronize()
+    with pytest.raises(pflbm.PflbmError) as e:
+        s.step(1)
+    assert e.value.code == pflbm.ENUMERIC
+    assert s.steps == 3
+    s.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -273,6 +273,35 @@ def test_save_load_continues_bit_exact():
     assert np.array_equal(pa, pb) and np.array_equal(ua, ub) and np.array_equal(qa, qb)
 
 
+def test_load_refuses_other_parameters_or_geometry():
+    # a checkpoint carries the parameters, flags and geometry that produced it
+    from paper_2312_00369_gb300.pflbm import PflbmError, Solver, EINVAL
+    case = oj.case_by_name("flat60_short")
+    a = solver(case, "fp32")
+    a.step(20)
+    blob = a.save()
+    kw = dict(theta_deg=case.theta_deg, precision="fp32", **case.physical())
+    bump = case.solid.copy()
+    bump[2, 10:14] = 1                     # a different wall, same size
+    others = {
+        "tau_f": Solver(case.solid, **{**kw, "tau_f": 0.9}),
+        "theta": Solver(case.solid, **{**kw, "theta_deg": 61.0}),
+        "mask": Solver(bump, **kw),
+        "dgdt": Solver(case.solid, dgdt_mode=1, **kw),
+        "body_force": Solver(case.solid, gx=1e-6, **kw),
+    }
+    for name, b in others.items():
+        with pytest.raises(PflbmError) as e:
+            b.load(blob)
+        assert e.value.code == EINVAL, name
+        b.close()
+    same = Solver(case.solid, **kw)
+    same.load(blob)
+    assert same.steps == 20
+    same.close()
+    a.close()
+
+
 def test_nan_is_reported():
     from paper_2312_00369_gb300.pflbm import PflbmError, ENUMERIC
     case = oj.case_by_name("flat60_short")
