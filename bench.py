@@ -522,6 +522,7 @@ def run_3d(args, torch, rank, world, local):
             s.init_droplet(*d)
         s.step(args.warmup)
         s.check()
+        step_kernel_used = s.step_kernel
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -624,6 +625,9 @@ def main():
     ap.add_argument("--size3d", default="512x512x128", help="nx x ny x nz of many_flat3d")
     ap.add_argument("--path3d", default="auto", choices=["auto", "fused", "three_pass"],
                     help="3D step: one fused launch or three launches")
+    ap.add_argument("--kernel", default="default", choices=["default", "global", "staged32x8", "staged64x4"],
+                    help="2D step kernel (results identical; speed differs)")
+    ap.add_argument("--chunk", type=int, default=0, help="staged kernel: tiles per work item (0: library default)")
     ap.add_argument("--dgdt", type=int, default=0, choices=[0, 1],
                     help="(1/2) dG/dt: 0 backward difference, 1 omitted")
     args = ap.parse_args()
@@ -662,11 +666,13 @@ def main():
     # ---------------- device-resident throughput ----------------
     with torch.cuda.stream(stream):
         s = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
-                   precision=args.precision, device=local, stream=stream, **case.physical())
+                   precision=args.precision, device=local, stream=stream, step_kernel=args.kernel,
+                   step_chunk=args.chunk, **case.physical())
         for d in case.droplets:
             s.init_droplet(*d)
         s.step(args.warmup)
         s.check()
+        step_kernel_used = s.step_kernel
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -722,7 +728,8 @@ def main():
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         s2 = Solver(solid_h, theta_deg=case.theta_deg, theta_field=theta_h,
-                    precision=args.precision, device=local, stream=stream, **case.physical())
+                    precision=args.precision, device=local, stream=stream, step_kernel=args.kernel,
+                    step_chunk=args.chunk, **case.physical())
         for d in case.droplets:
             s2.init_droplet(*d)
         s2.step(e2e_steps)
@@ -748,6 +755,7 @@ def main():
                       "fp16": "f16 storage, f32 arithmetic"}[args.precision], "data": "synthetic",
             "config": {"workload": case.name, "nx": case.nx, "ny": case.ny,
                        "droplets": len(case.droplets), "precision": args.precision,
+                       "step_kernel": step_kernel_used,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state 1.2 GB > L2, no flush needed" if case.name == "many_flat"
                        else "small lattice: L2-resident"},

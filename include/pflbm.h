@@ -44,7 +44,8 @@ enum pflbm_status {
     PFLBM_ENOMEM = -2,   /* device allocation failed                         */
     PFLBM_EBADMASK = -3, /* rows 0, 1, ny-2, ny-1 of the mask are not solid  */
     PFLBM_ENUMERIC = -4, /* NaN or |u| >= 0.3 seen on the device             */
-    PFLBM_ETIMEOUT = -5, /* reserved: no kernel of this library waits on another */
+    PFLBM_ETIMEOUT = -5, /* a bounded wait of the staged step kernel for its
+                            TMA data gave up (the kernel then returns)       */
     PFLBM_ECUDA = -6     /* a CUDA runtime call failed                       */
 };
 
@@ -95,6 +96,14 @@ typedef struct {
      * or below; other ghosts keep the mean), with mu carrying the a_v wall
      * term 0 times (case 1) or twice (case 3). */
     int chi_case;
+    /* Step kernel (results are identical bit for bit; only the speed
+     * differs). 0: the library's default (1); 1: populations pulled from
+     * global memory, 32 x 8 tiles; 2: populations staged in shared memory
+     * by TMA, 32 x 8 tiles; 3: staged, 64 x 4 tiles. FP64 handles always
+     * use 1. step_chunk: tiles a CTA of the staged kernel marches down one
+     * tile column per work item (<= 0: 16). */
+    int step_kernel;
+    int step_chunk;
 } pflbm_params_t;
 
 /* Flat, inclined or circular wall for the contact-angle fit. type 0: the
@@ -127,6 +136,13 @@ int pflbm_create(pflbm_t** out, int nx, int ny, const uint8_t* solid_mask, doubl
 int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* p);
 /* Release every device buffer of the handle (NULL is ignored). */
 void pflbm_destroy(pflbm_t* h);
+
+/* Switch the step kernel of a handle (values as pflbm_params_t.step_kernel
+ * and step_chunk). EINVAL for a staged kernel on an FP64 handle or when the
+ * handle's tensor maps could not be built. */
+int pflbm_set_step_kernel(pflbm_t* h, int step_kernel, int step_chunk);
+/* The step kernel a handle uses (1, 2 or 3 as above). */
+int pflbm_get_step_kernel(const pflbm_t* h);
 
 /* Replace the contact-angle field (degrees, [ny][nx], copied). Takes effect
  * from the next step. */
@@ -232,13 +248,26 @@ int pflbm_load(pflbm_t* h, const void* buf, size_t len);
 typedef struct pflbm_batch pflbm_batch_t;
 typedef struct {
     int ctas_per_sm;     /* persistent CTAs per SM; <= 0: as many as fit      */
-    int tiles_per_item;  /* 32 x 8 tiles of one tile column per work item     */
+    int tiles_per_item;  /* tiles of one tile column per work item (lattices
+                            no size class below covers)                       */
     int order;           /* 0: lattice by lattice; 1: largest lattices first,
                             items interleaved across lattices                 */
     int use_graph;       /* replay step pairs from a captured CUDA graph      */
+    int kernel;          /* 0 or 1: global-load kernel, 32 x 8 tiles; 2:
+                            staged kernel (TMA ring) with the size classes
+                            below. FP64 batches always use 1.                */
+    /* Staged kernel, per size class: a lattice with nx * ny <=
+     * class_max_nodes[k] (first such k < n_classes) runs with tile shape
+     * class_shape[k] (0: 32 x 8, 1: 64 x 4) and class_tiles[k] tiles per
+     * work item; other lattices with 32 x 8 and tiles_per_item. */
+    int n_classes;
+    int64_t class_max_nodes[8];
+    int class_shape[8];
+    int class_tiles[8];
 } pflbm_schedule_t;
 
-/* Defaults: as many CTAs as fit, 1 tile per item, order 0, graphs on. */
+/* Defaults: as many CTAs as fit, 1 tile per item, order 0, graphs on,
+ * default kernel, no size classes. */
 void pflbm_schedule_default(pflbm_schedule_t* s);
 /* Build a batch over hs[0..count-1] (schedule NULL: defaults). Allocates the
  * device work list and descriptors with cudaMalloc. EINVAL if the handles
@@ -253,6 +282,8 @@ int pflbm_batch_set(pflbm_batch_t* b, pflbm_t* const* hs, int count);
  * in between are picked up (descriptors are rewritten). ENUMERIC if a member
  * reported a NaN or |u| >= 0.3 earlier. */
 int pflbm_batch_step(pflbm_batch_t* b, int64_t n);
+/* The step kernel the batch runs (1 global loads, 2 staged). */
+int pflbm_batch_kernel(const pflbm_batch_t* b);
 /* Work items, persistent grid size and total nodes of the batch. */
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes);
 void pflbm_batch_destroy(pflbm_batch_t* b);

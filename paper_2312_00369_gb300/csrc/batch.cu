@@ -32,7 +32,8 @@ struct pflbm_batch {
     size_t args_bytes = 0;
     int cap_lattices = 0, cap_work = 0;
     void* d_args[2] = {nullptr, nullptr};
-    int2* d_work = nullptr;
+    bool staged = false;          // staged (TMA ring) kernel, int4 items; else int2 items
+    void* d_work = nullptr;
     int n_work = 0;
     int grid = 0;
     long long nodes = 0;
@@ -80,19 +81,14 @@ void drop_graph(pflbm_batch_t* b)
     b->graph_n_work = -1;
 }
 
-std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s)
+// Interleave per-lattice item lists: lattice by lattice (order 0), or the
+// largest lattices first with items interleaved across lattices (order 1).
+template <typename I>
+std::vector<I> order_items(std::vector<std::vector<I>>& per, int order)
 {
-    const int G = std::max(1, s.tiles_per_item);
-    std::vector<std::vector<int2>> per(hs.size());
-    for (size_t i = 0; i < hs.size(); ++i) {
-        int ntx = tiles_x(hs[i]->nx), nty = tiles_y(hs[i]->ny);
-        for (int by = 0; by < nty; by += G)
-            for (int bx = 0; bx < ntx; ++bx) per[i].push_back(make_int2((int)i, by * ntx + bx));
-    }
-    std::vector<int2> w;
-    if (s.order == 1) {
-        // largest lattices first, items interleaved across lattices
-        std::vector<size_t> idx(hs.size());
+    std::vector<I> w;
+    if (order == 1) {
+        std::vector<size_t> idx(per.size());
         for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
         std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return per[a].size() > per[b].size(); });
         size_t longest = idx.empty() ? 0 : per[idx[0]].size();
@@ -103,6 +99,43 @@ std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedu
         for (auto& v : per) w.insert(w.end(), v.begin(), v.end());
     }
     return w;
+}
+
+// Global-load kernel: (lattice, first tile) items of tiles_per_item tiles.
+std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s)
+{
+    const int G = std::max(1, s.tiles_per_item);
+    std::vector<std::vector<int2>> per(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) {
+        int ntx = tiles_x(hs[i]->nx), nty = tiles_y(hs[i]->ny);
+        for (int by = 0; by < nty; by += G)
+            for (int bx = 0; bx < ntx; ++bx) per[i].push_back(make_int2((int)i, by * ntx + bx));
+    }
+    return order_items(per, s.order);
+}
+
+// Staged kernel: (lattice, strip, first block, blocks | shape << 16) items,
+// shape and blocks per item by size class.
+std::vector<int4> build_work_staged(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s)
+{
+    std::vector<std::vector<int4>> per(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) {
+        const long long nodes = (long long)hs[i]->nx * hs[i]->ny;
+        int shape = 0, L = std::max(1, s.tiles_per_item);
+        for (int k = 0; k < std::min(8, s.n_classes); ++k)
+            if (nodes <= s.class_max_nodes[k]) {
+                shape = s.class_shape[k] == 1 ? 1 : 0;
+                L = std::max(1, s.class_tiles[k]);
+                break;
+            }
+        const int TXs = shape ? 64 : 32, TYs = shape ? 4 : 8;
+        const int nsx = (hs[i]->nx + TXs - 1) / TXs, nby = (hs[i]->ny + TYs - 1) / TYs;
+        L = std::min(L, std::min(nby, 0xffff));
+        for (int b0 = 0; b0 < nby; b0 += L)
+            for (int sx = 0; sx < nsx; ++sx)
+                per[i].push_back(make_int4((int)i, sx, b0, std::min(L, nby - b0) | (shape << 16)));
+    }
+    return order_items(per, s.order);
 }
 
 int upload(pflbm_batch_t* b)
@@ -118,7 +151,21 @@ int upload(pflbm_batch_t* b)
         b->cur0[i] = h->cur;
         b->nodes += (long long)h->nx * h->ny;
     }
-    std::vector<int2> w = build_work(b->hs, b->sched);
+    b->staged = b->precision != PFLBM_FP64 && b->sched.kernel == 2;
+    for (pflbm_t* h : b->hs)
+        if (!h->tma) b->staged = false;
+    std::vector<unsigned char> wbytes;
+    size_t item = b->staged ? sizeof(int4) : sizeof(int2);
+    if (b->staged) {
+        std::vector<int4> w4 = build_work_staged(b->hs, b->sched);
+        wbytes.resize(w4.size() * item);
+        if (!w4.empty()) std::memcpy(wbytes.data(), w4.data(), wbytes.size());
+    } else {
+        std::vector<int2> w2 = build_work(b->hs, b->sched);
+        wbytes.resize(w2.size() * item);
+        if (!w2.empty()) std::memcpy(wbytes.data(), w2.data(), wbytes.size());
+    }
+    const int n_items = (int)(wbytes.size() / item);
     if (n > b->cap_lattices) {
         int cap = std::max(n, 2 * b->cap_lattices);
         for (int k = 0; k < 2; ++k) {
@@ -130,26 +177,27 @@ int upload(pflbm_batch_t* b)
         b->cap_lattices = cap;
         drop_graph(b);
     }
-    if ((int)w.size() > b->cap_work) {
-        int cap = std::max((int)w.size(), 2 * b->cap_work);
-        bfree(b, b->d_work, sizeof(int2) * b->cap_work);
+    if (n_items > b->cap_work) {
+        int cap = std::max(n_items, 2 * b->cap_work);
+        bfree(b, b->d_work, sizeof(int4) * b->cap_work);
         b->d_work = nullptr;
         void* p;
-        if (int rc = balloc(b, &p, sizeof(int2) * cap)) return rc;
-        b->d_work = (int2*)p;
+        if (int rc = balloc(b, &p, sizeof(int4) * cap)) return rc;
+        b->d_work = p;
         b->cap_work = cap;
         drop_graph(b);
     }
     cudaError_t e = cudaMemcpyAsync(b->d_args[0], a0.data(), a0.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_args[1], a1.data(), a1.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && !w.empty())
-        e = cudaMemcpyAsync(b->d_work, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !wbytes.empty())
+        e = cudaMemcpyAsync(b->d_work, wbytes.data(), wbytes.size(), cudaMemcpyHostToDevice, b->stream);
     // the host vectors go out of scope on return: finish the copies first
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
-    b->n_work = (int)w.size();
+    drop_graph(b);   // kernel, work list or grid may differ from the captured ones
+    b->n_work = n_items;
     b->phase = 0;
-    int per_sm = batch_max_ctas_per_sm(b->precision);
+    int per_sm = b->staged ? staged_batch_ctas_per_sm(b->precision) : batch_max_ctas_per_sm(b->precision);
     if (b->sched.ctas_per_sm > 0) per_sm = std::min(per_sm, b->sched.ctas_per_sm);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -171,8 +219,11 @@ int check_members(pflbm_t* const* hs, int count, int precision, int device, cuda
 
 cudaError_t launch_set(pflbm_batch_t* b, int set)
 {
-    return launch_step_batch(b->precision, b->d_args[set], b->d_work, b->n_work, std::max(1, b->sched.tiles_per_item),
-                             b->grid, b->stream);
+    if (b->staged)
+        return launch_step_staged_batch(b->precision, b->d_args[set], (const int4*)b->d_work, b->n_work, b->grid,
+                                        b->stream);
+    return launch_step_batch(b->precision, b->d_args[set], (const int2*)b->d_work, b->n_work,
+                             std::max(1, b->sched.tiles_per_item), b->grid, b->stream);
 }
 
 int ensure_graph(pflbm_batch_t* b)
@@ -204,10 +255,13 @@ extern "C" {
 void pflbm_schedule_default(pflbm_schedule_t* s)
 {
     if (!s) return;
+    std::memset(s, 0, sizeof(*s));
     s->ctas_per_sm = 0;
     s->tiles_per_item = 1;
     s->order = 0;
     s->use_graph = 1;
+    s->kernel = 0;
+    s->n_classes = 0;
 }
 
 int pflbm_batch_create(pflbm_batch_t** out, pflbm_t* const* hs, int count, const pflbm_schedule_t* sched)
@@ -255,6 +309,8 @@ int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
     bool stale = false;
     for (size_t i = 0; i < b->hs.size(); ++i) {
         pflbm_t* h = b->hs[i];
+        if (h->hstatus && (h->hstatus[0] & 4))
+            return set_error(PFLBM_ETIMEOUT, "batch: a wait for staged data in the step kernel gave up");
         if (h->hstatus && h->hstatus[0] != 0)
             return set_error(PFLBM_ENUMERIC, "batch: NaN or |u| >= 0.3 detected on the device");
         if (h->init_pending) {
@@ -295,6 +351,12 @@ int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
     return PFLBM_OK;
 }
 
+int pflbm_batch_kernel(const pflbm_batch_t* b)
+{
+    if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
+    return b->staged ? 2 : 1;
+}
+
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes)
 {
     if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
@@ -311,7 +373,7 @@ void pflbm_batch_destroy(pflbm_batch_t* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
     for (int k = 0; k < 2; ++k) bfree(b, b->d_args[k], b->args_bytes * b->cap_lattices);
-    bfree(b, b->d_work, sizeof(int2) * b->cap_work);
+    bfree(b, b->d_work, sizeof(int4) * b->cap_work);
     delete b;
 }
 

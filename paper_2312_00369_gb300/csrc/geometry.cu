@@ -202,7 +202,55 @@ __global__ void k_fingerprint(const uint8_t* __restrict__ cls, const C* __restri
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+// Per TXT x TYT tile of the staged step (tile column sx, block b): bit 0 when
+// every node within two of the tile's nodes lies in the lattice and is a
+// fluid node (no class reads, no bounce-back checks, no ghosts: the fluid
+// path), bit 1 when a node of the tile is a ghost or a zeta = 1 node next to
+// a ghost (the phi tile then needs a ring of two and the ghost values).
+template <int TXT, int TYT>
+__global__ void k_staged_flags(const uint8_t* __restrict__ cls, uint8_t* __restrict__ flags, int nx, int ny, int pitch,
+                               int nsx, int nby)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nsx * nby) return;
+    const int sx = t % nsx, b = t / nsx;
+    const int x0 = sx * TXT, y0 = b * TYT, nreal = min(TXT, nx - x0);
+    auto at = [&](int x, int y) {
+        int xx = x % nx;
+        if (xx < 0) xx += nx;
+        return cls[(size_t)y * pitch + xx];
+    };
+    bool fluid = true;
+    for (int y = y0 - 2; fluid && y < y0 + TYT + 2; ++y) {
+        if (y < 0 || y >= ny) { fluid = false; break; }
+        for (int x = x0 - 2; x < x0 + nreal + 2; ++x)
+            if ((at(x, y) & CLS_MASK) != CLS_FLUID) { fluid = false; break; }
+    }
+    bool halo2 = false;
+    for (int y = y0; y < min(y0 + TYT, ny); ++y)
+        for (int x = x0; x < x0 + nreal; ++x) {
+            const uint8_t c = at(x, y);
+            if ((zeta_of(c) && (c & F_NEARGHOST)) || (c & CLS_MASK) == CLS_GHOST) halo2 = true;
+        }
+    flags[t] = (fluid ? 1 : 0) | (halo2 ? 2 : 0);
+}
+
 }  // namespace
+
+size_t staged_flags_bytes(int nx, int ny)
+{
+    return (size_t)((nx + 31) / 32) * ((ny + 7) / 8) + (size_t)((nx + 63) / 64) * ((ny + 3) / 4);
+}
+
+cudaError_t launch_staged_flags(pflbm_t* h)
+{
+    const int n0 = ((h->nx + 31) / 32) * ((h->ny + 7) / 8), n1 = ((h->nx + 63) / 64) * ((h->ny + 3) / 4);
+    k_staged_flags<32, 8><<<(n0 + 127) / 128, 128, 0, h->stream>>>(h->cls, h->sflags, h->nx, h->ny, h->pitch,
+                                                                  (h->nx + 31) / 32, (h->ny + 7) / 8);
+    k_staged_flags<64, 4><<<(n1 + 127) / 128, 128, 0, h->stream>>>(h->cls, h->sflags + n0, h->nx, h->ny, h->pitch,
+                                                                  (h->nx + 63) / 64, (h->ny + 3) / 4);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fingerprint(const uint8_t* cls, const void* wet, bool wet_fp64, int nx, long long rows, int pitch,
                                unsigned long long* d_out, cudaStream_t stream)

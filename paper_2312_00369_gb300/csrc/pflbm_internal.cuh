@@ -108,6 +108,8 @@ struct Params {           // derived parameters (Sec. 2.1-2.2), in FP64
     int chi_case;         // Appendix A, Table 2: 1, 2 (the paper's method) or 3
 };
 
+struct TmaSet;            // tensor maps of the staged step (step_core.cuh)
+
 }  // namespace pfk
 
 // The handle.
@@ -148,6 +150,11 @@ struct pflbm {
     int64_t steps = 0;
     size_t bytes_allocated = 0;
     cudaEvent_t status_ev = nullptr;
+    // staged step (FP32 and 16-bit): tensor maps [shape][copy] in device memory
+    pfk::TmaSet* tma = nullptr;
+    uint8_t* sflags = nullptr;    // staged step: per-tile flags of both shapes
+    int step_shape = -1;          // -1: global-load step kernel; 0: 32 x 8; 1: 64 x 4 staged
+    int step_chunk = 16;          // staged step: tiles per work item (blocks a CTA marches)
 };
 
 namespace pfk {
@@ -160,6 +167,10 @@ cudaError_t launch_classify(pflbm_t* h);
 cudaError_t launch_wet(pflbm_t* h);
 cudaError_t launch_links(pflbm_t* h, uint16_t* unknown, uint16_t* doubly);
 cudaError_t launch_tile_flags(pflbm_t* h);
+// tile flags of the staged step for both tile shapes (h->sflags: the 32 x 8
+// tiles, then the 64 x 4 tiles, tile column fastest)
+size_t staged_flags_bytes(int nx, int ny);
+cudaError_t launch_staged_flags(pflbm_t* h);
 // Order-free 64-bit fingerprint of the node bytes and wetting coefficients of
 // a [rows][pitch] lattice (first nx columns) into *d_out: checkpoints record
 // it so that a state is only loaded into a handle of the same geometry.
@@ -179,6 +190,16 @@ void write_step_args(pflbm_t* h, int flip, void* dst);   // flip: in/out swapped
 cudaError_t launch_step_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,
                               int grid, cudaStream_t stream);
 int batch_max_ctas_per_sm(int precision);
+
+// step_tma.cu: the staged step (TMA ring, tile shapes 0: 32 x 8, 1: 64 x 4)
+constexpr int kStagedShapes = 2;
+struct TmaSet;
+size_t tma_sets_bytes();                                    // kStagedShapes x 2 copies
+bool encode_tma_sets(const pflbm_t* h, TmaSet* host);      // false: staged step unavailable
+cudaError_t launch_step_staged(pflbm_t* h, int shape, int blocks_per_item, int ctas_per_sm);
+cudaError_t launch_step_staged_batch(int precision, const void* d_args, const int4* d_work, int n_work, int grid,
+                                     cudaStream_t stream);
+int staged_batch_ctas_per_sm(int precision);
 
 // diag.cu
 cudaError_t launch_mass(pflbm_t* h, double* d_out);

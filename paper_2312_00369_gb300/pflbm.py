@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
                 ("alloc_ctx", ctypes.c_void_p), ("nu_l", ctypes.c_double), ("nu_g", ctypes.c_double),
                 ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("dgdt_mode", ctypes.c_int),
-                ("chi_case", ctypes.c_int)]
+                ("chi_case", ctypes.c_int), ("step_kernel", ctypes.c_int), ("step_chunk", ctypes.c_int)]
 
 
 class Params3D(ctypes.Structure):
@@ -67,7 +67,13 @@ class Wall3D(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int), ("tiles_per_item", ctypes.c_int),
-                ("order", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("order", ctypes.c_int), ("use_graph", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("n_classes", ctypes.c_int), ("class_max_nodes", ctypes.c_int64 * 8),
+                ("class_shape", ctypes.c_int * 8), ("class_tiles", ctypes.c_int * 8)]
+
+
+# step kernels (pflbm_params_t.step_kernel)
+STEP_KERNELS = {"default": 0, "global": 1, "staged32x8": 2, "staged64x4": 3}
 
 
 class Wall(ctypes.Structure):
@@ -110,6 +116,8 @@ _SIGS = {
     "pflbm_create_ex": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(Params)]),
     "pflbm_destroy": (None, [_H]),
     "pflbm_set_theta_field": (ctypes.c_int, [_H, _fp]),
+    "pflbm_set_step_kernel": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    "pflbm_get_step_kernel": (ctypes.c_int, [_H]),
     "pflbm_init_droplet": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "pflbm_init_phi": (ctypes.c_int, [_H, _dp]),
     "pflbm_step": (ctypes.c_int, [_H, ctypes.c_int64]),
@@ -135,6 +143,7 @@ _SIGS = {
     "pflbm_batch_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_H), ctypes.c_int]),
     "pflbm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "pflbm_batch_info": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, ctypes.POINTER(ctypes.c_int64)]),
+    "pflbm_batch_kernel": (ctypes.c_int, [ctypes.c_void_p]),
     "pflbm_batch_destroy": (None, [ctypes.c_void_p]),
     "pflbm3d_params_default": (None, [ctypes.POINTER(Params3D)]),
     "pflbm3d_create": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(Params3D)]),
@@ -256,7 +265,7 @@ class Solver:
     def __init__(self, solid, theta_deg=90.0, sigma=0.01, W=4.0, M=0.1, tau_f=0.8,
                  rho_l=1.0, rho_g=0.1, tau_g=0.0, theta_field=None, precision="fp32",
                  device=None, stream=None, torch_memory=True, nu_l=0.0, nu_g=0.0, gx=0.0, gy=0.0,
-                 dgdt_mode=0, chi_case=2):
+                 dgdt_mode=0, chi_case=2, step_kernel="default", step_chunk=0):
         import torch
         L = lib()
         solid = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -282,6 +291,9 @@ class Solver:
         p.nu_l, p.nu_g, p.gx, p.gy = float(nu_l), float(nu_g), float(gx), float(gy)
         p.dgdt_mode = int(dgdt_mode)
         p.chi_case = int(chi_case)
+        p.step_kernel = STEP_KERNELS.get(step_kernel, step_kernel) if isinstance(step_kernel, str) \
+            else int(step_kernel)
+        p.step_chunk = int(step_chunk)
         p.device = dev
         p.stream = ctypes.c_void_p(stream.cuda_stream)
         if torch_memory:
@@ -319,6 +331,16 @@ class Solver:
         phi = np.ascontiguousarray(phi, dtype=np.float64)
         assert phi.shape == (self.ny, self.nx)
         _check(lib().pflbm_init_phi(self._h, _p(phi)))
+
+    def set_step_kernel(self, step_kernel, step_chunk=0):
+        """Switch the step kernel ("default", "global", "staged32x8",
+        "staged64x4" or 0..3); results are the same bit for bit."""
+        k = STEP_KERNELS.get(step_kernel, step_kernel) if isinstance(step_kernel, str) else int(step_kernel)
+        _check(lib().pflbm_set_step_kernel(self._h, int(k), int(step_chunk)))
+
+    @property
+    def step_kernel(self):
+        return {v: k for k, v in STEP_KERNELS.items()}[lib().pflbm_get_step_kernel(self._h)]
 
     def set_theta_field(self, theta):
         theta = np.ascontiguousarray(theta, dtype=np.float32)
@@ -409,11 +431,18 @@ class Solver:
         _check(lib().pflbm_load(self._h, buf, len(blob)))
 
 
-def schedule(ctas_per_sm=0, tiles_per_item=1, order=0, use_graph=1):
+def schedule(ctas_per_sm=0, tiles_per_item=1, order=0, use_graph=1, kernel=0, classes=()):
+    """A ``pflbm_schedule_t``. ``classes``: up to 8 (max_nodes, shape,
+    tiles_per_item) entries of the staged kernel, by lattice size."""
     s = Schedule()
     lib().pflbm_schedule_default(ctypes.byref(s))
     s.ctas_per_sm, s.tiles_per_item, s.order, s.use_graph = (int(ctas_per_sm), int(tiles_per_item),
                                                              int(order), int(use_graph))
+    s.kernel = int(kernel)
+    classes = list(classes)[:8]
+    s.n_classes = len(classes)
+    for k, (mx, shape, tiles) in enumerate(classes):
+        s.class_max_nodes[k], s.class_shape[k], s.class_tiles[k] = int(mx), int(shape), int(tiles)
     return s
 
 
@@ -440,6 +469,11 @@ class Batch:
 
     def step(self, n=1):
         _check(lib().pflbm_batch_step(self._b, int(n)))
+
+    @property
+    def kernel(self):
+        """1: global-load kernel, 2: staged kernel."""
+        return lib().pflbm_batch_kernel(self._b)
 
     def info(self):
         nw, grid, nodes = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()

@@ -1,0 +1,109 @@
+"""The staged step kernel (populations brought to shared memory by TMA, two
+tile shapes) against the global-load kernel: the arithmetic is shared, so the
+fields must agree bit for bit after any number of steps, for every storage
+precision that has the staged path, every geometry class (fluid-only tiles,
+walls, ghosts, bounce-back corners, lattices narrower than a tile, ragged
+edges) and in batches whose lattices run with different tile shapes.
+"""
+import numpy as np
+import pytest
+
+from tests import oracle_jobs as oj
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CASES = ["flat60_short", "incline45_ragged", "block", "tiny", "cylinder", "crop", "flat_visc_force", "flat_chi1",
+         "incline_nodgdt"]
+KERNELS = [("staged32x8", 16), ("staged64x4", 16), ("staged32x8", 3), ("staged64x4", 1)]
+
+
+def _solver(case, precision, kernel, chunk=0):
+    from paper_2312_00369_gb300.pflbm import Solver
+    s = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field, precision=precision,
+               step_kernel=kernel, step_chunk=chunk, **case.physical(), **oj.solver_options(case))
+    for d in case.droplets:
+        s.init_droplet(*d)
+    return s
+
+
+def _state(s):
+    phi, u, p = s.get()
+    return phi, u, p, s.mass()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("name", CASES)
+def test_staged_equals_global(name, precision):
+    case = oj.case_by_name(name)
+    steps = 37   # odd: both population copies serve as input
+    ref = _solver(case, precision, "global")
+    assert ref.step_kernel == "global"
+    ref.step(steps)
+    want = _state(ref)
+    ref.close()
+    for kernel, chunk in KERNELS:
+        s = _solver(case, precision, kernel, chunk)
+        assert s.step_kernel == kernel
+        s.step(steps)
+        got = _state(s)
+        s.close()
+        for a, b, what in zip(want, got, ("phi", "u", "p", "mass")):
+            assert np.array_equal(a, b), (name, precision, kernel, chunk, what, np.max(np.abs(np.asarray(a) - b)))
+
+
+def test_kernel_is_switchable_between_steps():
+    from paper_2312_00369_gb300.pflbm import PflbmError, EINVAL
+    case = oj.case_by_name("flat60_short")
+    s = _solver(case, "fp32", "default")
+    assert s.step_kernel == "global"
+    s.step(10)
+    s.set_step_kernel("staged32x8")
+    s.step(10)
+    s.set_step_kernel("staged64x4", 2)
+    s.step(11)
+    got = _state(s)
+    r = _solver(case, "fp32", "global")
+    r.step(31)
+    want = _state(r)
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
+    f64 = _solver(case, "fp64", "default")
+    assert f64.step_kernel == "global"
+    with pytest.raises(PflbmError) as e:
+        f64.set_step_kernel("staged32x8")
+    assert e.value.code == EINVAL
+    for x in (s, r, f64):
+        x.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_staged_batch_with_mixed_shapes_equals_single(precision):
+    # lattices of several sizes, the small ones with 64 x 4 tiles and short
+    # items, the others with 32 x 8 tiles: each member equals its own
+    # single-lattice run with the global-load kernel
+    from paper_2312_00369_gb300 import pflbm, workloads as wl
+    cases = wl.batched_instances(count=12, seed=7)
+    classes = [(64 * 32, 1, 2), (128 * 64, 1, 5), (256 * 128, 0, 3)]
+    stream = torch.cuda.Stream()
+    members = []
+    for c in cases:
+        s = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision=precision, stream=stream, **c.physical())
+        for d in c.droplets:
+            s.init_droplet(*d)
+        members.append(s)
+    b = pflbm.Batch(members, pflbm.schedule(tiles_per_item=4, kernel=2, classes=classes))
+    assert b.kernel == 2
+    b.step(23)
+    for c, s in zip(cases, members):
+        r = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision=precision, step_kernel="global",
+                         **c.physical())
+        for d in c.droplets:
+            r.init_droplet(*d)
+        r.step(23)
+        for x, y in zip(_state(r), _state(s)):
+            assert np.array_equal(x, y), (c.nx, c.ny)
+        r.close()
+    b.close()
+    for s in members:
+        s.close()
