@@ -45,13 +45,23 @@ namespace {
 
 // Pull of direction I at node (gx, gy), whose class byte sits at s_cls[sy][sx].
 // CHECK = false: every neighbour is a zeta = 1 node (s_cls is not read).
-template <int I, int PREC, bool CHECK>
+// WRAP = false: the neighbours x +- 1 lie inside 0..nx-1 (a tile away from the
+// periodic seam), so every source is the node's own index plus a fixed offset.
+template <int I, int PREC, bool CHECK, bool WRAP>
 __device__ __forceinline__ typename Store<PREC>::C pull(const typename Store<PREC>::S* __restrict__ base,
                                                         const uint8_t (*s_cls)[TX + 6], int sy, int sx, int gx,
                                                         int gy, int nx, int pitch, int plane)
 {
     using T = Store<PREC>;
     constexpr int X = cx(I), Y = cy(I), O = opp(I);
+    if constexpr (!WRAP) {
+        const int k = gy * pitch + gx;
+        if (!CHECK) return T::template ldp<I>(base[k + (I * plane - Y * pitch - X)]);
+        int src = k + O * plane;
+        if (zeta_of(s_cls[sy + Y][sx + X])) src = k + (O * plane + Y * pitch + X);
+        if (zeta_of(s_cls[sy - Y][sx - X])) src = k + (I * plane - Y * pitch - X);
+        return T::template ldp<I>(base[src]);
+    }
     if (!CHECK) return T::template ldp<I>(base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)]);
     // one load from the selected source, no branch (a warp whose lanes pick
     // different sources still issues one load); I and O share a storage unit
@@ -62,25 +72,25 @@ __device__ __forceinline__ typename Store<PREC>::C pull(const typename Store<PRE
     return T::template ldp<I>(base[src]);
 }
 
-template <int PREC, bool CHECK>
+template <int PREC, bool CHECK, bool WRAP>
 __device__ __forceinline__ void pull_f(typename Store<PREC>::C v[9], const typename Store<PREC>::S* __restrict__ f,
                                        const uint8_t (*s_cls)[TX + 6], int sy, int sx, int gx, int gy, int nx,
                                        int pitch, int plane)
 {
     using T = Store<PREC>;
     v[0] = T::template ldp<0>(f[gy * pitch + gx]);
-    v[1] = pull<1, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[2] = pull<2, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[3] = pull<3, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[4] = pull<4, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[5] = pull<5, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[6] = pull<6, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[7] = pull<7, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[8] = pull<8, PREC, CHECK>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[1] = pull<1, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[2] = pull<2, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[3] = pull<3, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[4] = pull<4, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[5] = pull<5, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[6] = pull<6, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[7] = pull<7, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[8] = pull<8, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
 }
 
 // Pulled g at a node: g_0 raw (storage form) and its value, g_1..g_8.
-template <int PREC, bool CHECK>
+template <int PREC, bool CHECK, bool WRAP>
 __device__ __forceinline__ void pull_g(typename Store<PREC>::C v[9], typename Store<PREC>::G0T& raw0,
                                        const Planes<PREC>& P, const uint8_t (*s_cls)[TX + 6], int sy, int sx,
                                        int gx, int gy, int nx, int pitch, int plane)
@@ -88,30 +98,30 @@ __device__ __forceinline__ void pull_g(typename Store<PREC>::C v[9], typename St
     using T = Store<PREC>;
     raw0 = P.g0[gy * pitch + gx];
     v[0] = T::g0(raw0);
-    v[1] = pull<1, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[2] = pull<2, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[3] = pull<3, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[4] = pull<4, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[5] = pull<5, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[6] = pull<6, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[7] = pull<7, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[8] = pull<8, PREC, CHECK>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[1] = pull<1, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[2] = pull<2, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[3] = pull<3, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[4] = pull<4, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[5] = pull<5, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[6] = pull<6, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[7] = pull<7, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    v[8] = pull<8, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
 }
 
-template <int PREC, bool CHECK>
+template <int PREC, bool CHECK, bool WRAP>
 __device__ __forceinline__ typename Store<PREC>::C pulled_phi(const Planes<PREC>& P, const uint8_t (*s_cls)[TX + 6],
                                                               int sy, int sx, int gx, int gy, int nx, int pitch,
                                                               int plane)
 {
     typename Store<PREC>::C v[9];
     typename Store<PREC>::G0T raw0;
-    pull_g<PREC, CHECK>(v, raw0, P, s_cls, sy, sx, gx, gy, nx, pitch, plane);
+    pull_g<PREC, CHECK, WRAP>(v, raw0, P, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     return phi_of<PREC>(v);
 }
 
 // Prologue of a tile whose nodes within two of it are all fluid: no class
 // tile, no bounce-back checks, no ghosts, phi on a one-node ring.
-template <int PREC>
+template <int PREC, bool WRAP>
 __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
                                                     typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0,
                                                     typename Store<PREC>::C gown[9],
@@ -122,10 +132,10 @@ __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
     const int tid = ty * TX + tx;
     const int nx = a.nx, pitch = a.pitch, plane = a.plane;
     {
-        const int gx = wrap1(x0 + tx, nx), gy = y0 + ty;
-        pull_g<PREC, false>(gown, raw0, a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
+        const int gx = WRAP ? wrap1(x0 + tx, nx) : x0 + tx, gy = y0 + ty;
+        pull_g<PREC, false, WRAP>(gown, raw0, a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
         // the f pulls do not depend on phi: issue them before the barrier
-        if (PFLBM_PREFETCH_F) pull_f<PREC, false>(fown, a.in.f, nullptr, 0, 0, gx, gy, nx, pitch, plane);
+        if (PFLBM_PREFETCH_F) pull_f<PREC, false, WRAP>(fown, a.in.f, nullptr, 0, 0, gx, gy, nx, pitch, plane);
         s_phi[ty + 2][tx + 2] = phi_of<PREC>(gown);
     }
     // ring: top row, bottom row (TX + 2 each), left and right columns (TY each)
@@ -136,14 +146,14 @@ __device__ __forceinline__ void tile_prologue_fluid(const StepArgs<PREC>& a,
         else if (tid < 2 * RT) { py = TY + 2; px = 1 + tid - RT; }
         else if (tid < 2 * RT + TY) { py = 2 + tid - 2 * RT; px = 1; }
         else { py = 2 + tid - 2 * RT - TY; px = TX + 2; }
-        const int gy = y0 - 2 + py, gx = wrap1(x0 - 2 + px, nx);
-        s_phi[py][px] = pulled_phi<PREC, false>(a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
+        const int gy = y0 - 2 + py, gx = WRAP ? wrap1(x0 - 2 + px, nx) : x0 - 2 + px;
+        s_phi[py][px] = pulled_phi<PREC, false, WRAP>(a.in, nullptr, 0, 0, gx, gy, nx, pitch, plane);
     }
     __syncthreads();
 }
 
 // phi on the ring of width H around the tile (one position per thread).
-template <int PREC, int H>
+template <int PREC, int H, bool WRAP>
 __device__ __forceinline__ void ring_phi(const StepArgs<PREC>& a, const uint8_t (*s_cls)[TX + 6],
                                          typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0, int tid,
                                          bool tiny)
@@ -174,11 +184,11 @@ __device__ __forceinline__ void ring_phi(const StepArgs<PREC>& a, const uint8_t 
     const uint8_t c = s_cls[sy][sx];
     if (zeta_of(c)) {
         const int gy = y0 - 2 + py, xr = x0 - 2 + px;
-        const int gx = tiny ? wrapn(xr, a.nx) : wrap1(xr, a.nx);
+        const int gx = !WRAP ? xr : (tiny ? wrapn(xr, a.nx) : wrap1(xr, a.nx));
         if (has_link(c))
-            ph = pulled_phi<PREC, true>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
+            ph = pulled_phi<PREC, true, WRAP>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
         else
-            ph = pulled_phi<PREC, false>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
+            ph = pulled_phi<PREC, false, WRAP>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
     }
     s_phi[py][px] = ph;
 }
@@ -187,7 +197,7 @@ __device__ __forceinline__ void ring_phi(const StepArgs<PREC>& a, const uint8_t 
 // tile needs phi two nodes out only when a ghost node lies next to one of its
 // nodes (the ghost average reaches one node further); otherwise one ring.
 // Returns the own node's pulled g (and raw g_0) when it is a zeta = 1 node.
-template <int PREC>
+template <int PREC, bool WRAP>
 __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (*s_cls)[TX + 6],
                                               typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0,
                                               typename Store<PREC>::C gown[9], typename Store<PREC>::G0T& raw0)
@@ -199,7 +209,7 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
 
     // one conditional wrap covers the tile and its halo unless nx is tiny
     const bool tiny = nx < TX + 8;
-    auto wx = [&](int x) { return tiny ? wrapn(x, nx) : wrap1(x, nx); };
+    auto wx = [&](int x) { return !WRAP ? x : (tiny ? wrapn(x, nx) : wrap1(x, nx)); };
     for (int p = tid; p < (TY + 6) * (TX + 6); p += TX * TY) {
         int py = p / (TX + 6), px = p - py * (TX + 6);
         int gy = y0 - 3 + py, gx = wx(x0 - 3 + px);
@@ -220,18 +230,18 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
         C ph = C(0);
         if (gy < ny && zeta_of(own)) {
             if (has_link(own))
-                pull_g<PREC, true>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+                pull_g<PREC, true, WRAP>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
             else
-                pull_g<PREC, false>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+                pull_g<PREC, false, WRAP>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
             ph = phi_of<PREC>(gown);
         }
         s_phi[ty + 2][tx + 2] = ph;
     }
     // halo ring of width 1 or 2: top rows, bottom rows, left and right columns
     if (halo == 1)
-        ring_phi<PREC, 1>(a, s_cls, s_phi, x0, y0, tid, tiny);
+        ring_phi<PREC, 1, WRAP>(a, s_cls, s_phi, x0, y0, tid, tiny);
     else
-        ring_phi<PREC, 2>(a, s_cls, s_phi, x0, y0, tid, tiny);
+        ring_phi<PREC, 2, WRAP>(a, s_cls, s_phi, x0, y0, tid, tiny);
     __syncthreads();
     if (halo == 1) return;
 
@@ -246,9 +256,10 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
 // One tile (bx, by) of one lattice: the whole time step for its nodes.
 // Called by every thread of the CTA; the shared tiles are the caller's.
 // VV: 0 uniform tau_f, 1 variable viscosity, 2 decided by a.varvisc.
-template <int PREC, bool COLLIDE, int VV>
-__device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int by, int ntx,
-                                          uint8_t (*s_cls)[TX + 6], typename Store<PREC>::C (*s_phi)[TX + 4])
+// WRAP: the tile or its halo of three crosses the periodic seam in x.
+template <int PREC, bool COLLIDE, int VV, bool WRAP>
+__device__ __forceinline__ void step_tile_w(const StepArgs<PREC>& a, int bx, int by, int ntx,
+                                            uint8_t (*s_cls)[TX + 6], typename Store<PREC>::C (*s_phi)[TX + 4])
 {
     using T = Store<PREC>;
     using C = typename T::C;
@@ -257,9 +268,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     typename T::G0T g0raw;
     const bool fluid_tile = a.tiles[by * ntx + bx] != 0;
     if (fluid_tile)
-        tile_prologue_fluid<PREC>(a, s_phi, x0, y0, g, g0raw, f);
+        tile_prologue_fluid<PREC, WRAP>(a, s_phi, x0, y0, g, g0raw, f);
     else
-        tile_prologue<PREC>(a, s_cls, s_phi, x0, y0, g, g0raw);
+        tile_prologue<PREC, WRAP>(a, s_cls, s_phi, x0, y0, g, g0raw);
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int gx = x0 + tx, gy = y0 + ty;
@@ -267,13 +278,25 @@ __device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int b
     const uint8_t code = fluid_tile ? (uint8_t)CLS_FLUID : s_cls[ty + 3][tx + 3];
     node_step<PREC, COLLIDE, VV, TX + 4>(a, code, s_phi, ty + 2, tx + 2, gx, gy, g, g0raw, [&](C fv[9]) {
         if (!fluid_tile && has_link(code))
-            pull_f<PREC, true>(fv, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
+            pull_f<PREC, true, WRAP>(fv, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
         else if (PFLBM_PREFETCH_F && fluid_tile) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) fv[i] = f[i];
         } else
-            pull_f<PREC, false>(fv, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
+            pull_f<PREC, false, WRAP>(fv, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
     }, [&](int k) { return (C)a.sprev[k]; });
+}
+
+template <int PREC, bool COLLIDE, int VV>
+__device__ __forceinline__ void step_tile(const StepArgs<PREC>& a, int bx, int by, int ntx,
+                                          uint8_t (*s_cls)[TX + 6], typename Store<PREC>::C (*s_phi)[TX + 4])
+{
+    // every x the tile touches (class tile: three out) lies inside the lattice
+    const int x0 = bx * TX;
+    if (x0 >= 3 && x0 + TX + 3 <= a.nx)
+        step_tile_w<PREC, COLLIDE, VV, false>(a, bx, by, ntx, s_cls, s_phi);
+    else
+        step_tile_w<PREC, COLLIDE, VV, true>(a, bx, by, ntx, s_cls, s_phi);
 }
 
 // L2 prefetch of the rows that a later tile reads: the 18 population planes
