@@ -17,6 +17,7 @@ replica of the workload (the solver does not shard: replicas only).
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -61,7 +62,7 @@ def whole_job_mlups(world, nodes, steps, seconds):
     return world * nodes * steps / seconds / 1e6
 
 
-def step_source_sha256(files=("step.cu", "storage.cuh", "pflbm_internal.cuh")):
+def step_source_sha256(files=("step.cu", "step_core.cuh", "storage.cuh", "pflbm_internal.cuh")):
     import hashlib
     h = hashlib.sha256()
     for f in files:
@@ -119,6 +120,13 @@ class ClockSampler:
     def _read(self):
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
+
+    def wait_first(self, timeout=3.0):
+        """Block until nvidia-smi has printed its first sample (its start-up
+        takes longer than a short timed region)."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.02)
 
     def stop(self):
         if not self.proc:
@@ -225,13 +233,19 @@ def run_reference(args, rank, world):
 
 
 def run_batched(args, torch, rank, world, local):
+    line = batched_line(args, torch, world, local, args.steps, args.warmup, plain=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def batched_line(args, torch, world, local, steps, warmup, plain=True, precision=None):
     """256 uneven lattices (sizes from {64x32 .. 512x256}, flat / 30 deg
     incline / cylinder walls, theta ~ U[30, 150], seed 369), advanced by one
     persistent launch per step with the autotuned schedule, replayed from a
     CUDA graph. Also times the plain path: the same lattices in FP32, one
     launch per lattice per step."""
     from paper_2312_00369_gb300 import autotune, workloads as wl
-    from paper_2312_00369_gb300.pflbm import Batch, Solver, schedule
+    from paper_2312_00369_gb300.pflbm import Batch, Solver
     cases = wl.batched_instances(256, seed=369, steps=5000)
     nodes = sum(c.nx * c.ny for c in cases)
     stream = torch.cuda.Stream(device=local)
@@ -247,16 +261,18 @@ def run_batched(args, torch, rank, world, local):
                 out.append(sv)
         return out
 
-    sched, timings = autotune.tune(cases, args.precision, stream=stream)
-    solvers = build(args.precision)
-    b = Batch(solvers, schedule(**sched))
-    b.step(args.warmup)
+    precision = args.precision if precision is None else precision
+    sched, timings = autotune.tune(cases, precision, stream=stream)
+    solvers = build(precision)
+    b = Batch(solvers, autotune.to_schedule(sched))
+    b.step(warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.wait_first()
     e0.record(stream)
-    b.step(args.steps)
+    b.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -264,50 +280,57 @@ def run_batched(args, torch, rank, world, local):
     for sv in solvers:
         sv.check()
     info = b.info()
+    kernel = b.kernel
     b.close()
     for sv in solvers:
         sv.close()
-    value = nodes * args.steps / (ms * 1e-3) / 1e6
+    value = nodes * steps / (ms * 1e-3) / 1e6
 
-    # the plain path: FP32, one launch per lattice per step
-    plain = build("fp32")
-    k_plain = max(3, args.steps // 4)
-    for sv in plain:
-        sv.step(2)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(k_plain):
-        for sv in plain:
-            sv.step(1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_plain = e0.elapsed_time(e1)
-    for sv in plain:
-        sv.close()
-    plain_mlups = nodes * k_plain / (ms_plain * 1e-3) / 1e6
+    plain_mlups = None
+    if plain:
+        # the plain path: FP32, one launch per lattice per step
+        ps = build("fp32")
+        k_plain = max(3, steps // 4)
+        for sv in ps:
+            sv.step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k_plain):
+            for sv in ps:
+                sv.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = e0.elapsed_time(e1)
+        for sv in ps:
+            sv.close()
+        plain_mlups = nodes * k_plain / (ms_plain * 1e-3) / 1e6
     peak, peak_kind = load_peaks()
-    bpl = BYTES_PER_LU[args.precision]
-    achieved = bpl * nodes / (ms / args.steps * 1e-3) / 1e9
-    line = {
-        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.precision + " storage", "data": "synthetic",
+    bpl = BYTES_PER_LU[precision]
+    achieved = bpl * nodes / (ms / steps * 1e-3) / 1e9
+    return {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": precision + " storage", "data": "synthetic",
         "config": {"workload": "batched", "lattices": len(cases), "nodes": nodes,
-                   "precision": args.precision, "schedule": sched, "work_items": info["n_work"],
+                   "precision": precision, "schedule": sched, "kernel": kernel, "work_items": info["n_work"],
                    "grid": info["grid"], "l2": "state of all lattices > L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "bytes_per_lu": bpl},
         "plain_fp32_one_launch_per_lattice_mlups": plain_mlups,
-        "speedup_vs_plain": value / plain_mlups,
+        "speedup_vs_plain": (value / plain_mlups) if plain_mlups else None,
         "autotune_ms_per_step": timings,
-        "gpu_launches": args.steps, "clocks": clocks,
+        "gpu_launches": steps, "clocks": clocks,
     }
+
+
+def run_serving(args, torch, rank, world, local):
+    line = serving_line(args, torch, world, args.serve_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_serving(args, torch, rank, world, local):
+def serving_line(args, torch, world, T, prec=None, dgdt=None):
     """Poisson request stream (2000 requests/s, sizes 128x64 .. 1024x512
     log-uniform, steps U[1000, 20000], random wall and theta, seed 2024)
     served by continuous batching with 16-bit storage (FP16 unless --precision
@@ -320,13 +343,14 @@ def run_serving(args, torch, rank, world, local):
     from paper_2312_00369_gb300.serve import PlainServer, Server, requests_from_stream
     # FP16 (scaled) storage by default: as fast as BF16 and about 100x closer to
     # the FP64 oracle in phi, which keeps the served angles within 0.5 deg
-    prec = args.precision if "--precision" in sys.argv and args.precision in ("bf16", "fp16") else "fp16"
-    T = args.serve_seconds
+    if prec is None:
+        prec = args.precision if "--precision" in sys.argv and args.precision in ("bf16", "fp16") else "fp16"
     budget = int(args.hbm_budget_gb * (1 << 30))
     over = requests_from_stream(wl.request_stream(rate=2000.0, duration=T, seed=2024))
 
     def serve(cls, reqs, drain, **kw):
-        srv = cls(hbm_budget=budget, max_slots=args.max_slots, tick=args.tick, dgdt_mode=args.dgdt, **kw)
+        srv = cls(hbm_budget=budget, max_slots=args.max_slots, tick=args.tick,
+                  dgdt_mode=args.dgdt if dgdt is None else dgdt, **kw)
         try:
             st = srv.run(reqs, duration=T, drain=drain, max_wall=(4 * T if drain else T))
             return st.summary(), st.results
@@ -342,6 +366,11 @@ def run_serving(args, torch, rank, world, local):
     sus = requests_from_stream(wl.request_stream(rate=rate, duration=T, seed=2025))
     sb, rb = serve(Server, sus, True, precision=prec)
     sp, rp = serve(PlainServer, sus, True)
+    # the plain path at 70 % of its own capacity (its p99 without the queue
+    # the batched server's rate builds up)
+    rate_plain = 0.7 * s_over_plain["processed_mlups"] * 1e6 / mean_lu
+    sus_p = requests_from_stream(wl.request_stream(rate=rate_plain, duration=T, seed=2026))
+    spp, _ = serve(PlainServer, sus_p, True)
     # the same requests served both ways: contact angle of the batched 16-bit
     # result against the plain FP32 one
     tb = {r.rid: r.theta_fit for r in rb if not r.failed and np.isfinite(r.theta_fit)}
@@ -357,20 +386,21 @@ def run_serving(args, torch, rank, world, local):
         "dtype": prec + " storage", "data": "synthetic",
         "config": {"workload": "serving", "seconds": T, "hbm_budget_gb": args.hbm_budget_gb,
                    "max_slots": args.max_slots, "tick": args.tick, "precision": prec,
-                   "dgdt_mode": args.dgdt},
+                   "dgdt_mode": args.dgdt if dgdt is None else dgdt},
         "value_is": "lattice updates per second processed by the batched server under the stated stream",
         "overloaded_2000_per_s": s_over,
         "overloaded_2000_per_s_plain_fp32": s_over_plain,
         "sustainable_rate_per_s": rate,
         "sustainable_batched": sb,
         "sustainable_plain_fp32_one_launch_per_solve": sp,
+        "plain_fp32_rate_per_s_at_70pct_own_capacity": rate_plain,
+        "plain_fp32_at_70pct_own_capacity": spp,
         "sustainable_angle_batched_vs_plain": angle,
         "p99_ratio_plain_over_batched": sp["p99_s"] / sb["p99_s"] if sb["p99_s"] > 0 else None,
         "throughput_ratio_batched_over_plain_saturated":
             s_over["processed_mlups"] / max(s_over_plain["processed_mlups"], 1e-9),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_wsweep(args, torch, rank, world, local):
@@ -522,23 +552,37 @@ def run_3d(args, torch, rank, world, local):
             s.init_droplet(*d)
         s.step(args.warmup)
         s.check()
-        step_kernel_used = s.step_kernel
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        # the K-step region is repeated until it has run for at least 300 ms
+        # (clock samples need that long); each repeat is bracketed by a
+        # barrier and a synchronize, and the repeat count is the same on
+        # every rank (from the slowest rank's first region)
         sampler = ClockSampler(local)
         sampler.start()
+        sampler.wait_first()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        s.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
+
+        def region():
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e0.record(stream)
+            s.step(args.steps)          # K launches of the fused step kernel
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        times = [region()]
+        first = max_over_ranks(times[0], f"cuda:{local}", world)
+        repeats = max(1, min(1000, int(math.ceil(300.0 / max(first, 1e-3)))))
+        while len(times) < repeats:
+            times.append(region())
         clocks = sampler.stop()
-        ms = e0.elapsed_time(e1)
+        ms = sum(times) / len(times)
         s.check()
-        s.close()
     ms = max_over_ranks(ms, f"cuda:{local}", world)
     ms_per_step = ms / args.steps
     value = whole_job_mlups(world, N, args.steps, ms * 1e-3)
@@ -574,6 +618,10 @@ def run_3d(args, torch, rank, world, local):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, f"cuda:{local}", world)
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and case.name == "many_flat" and args.precision == "fp32":
+        extra = extra_block(args, torch, world, local, case, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = oracle_baseline("3d", "many_flat3d", 10.0)
@@ -608,6 +656,64 @@ def run_3d(args, torch, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def extra_block(args, torch, world, local, case, stream):
+    """The other paths, measured in the same run: the 16-bit step on the same
+    lattice, the batched config-3 workload with the autotuned schedule, and
+    short serving runs (capacity, a sustainable rate, each path at 70 % of its
+    own capacity)."""
+    from paper_2312_00369_gb300.pflbm import Solver
+    out = {}
+    N = case.nx * case.ny
+    with torch.cuda.stream(stream):
+        s = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field, precision="bf16",
+                   device=local, stream=stream, **case.physical())
+        for d in case.droplets:
+            s.init_droplet(*d)
+        s.step(20)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k = 1000
+        e0.record(stream)
+        s.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.check()
+        s.close()
+    ms = e0.elapsed_time(e1) / k
+    peak, peak_kind = load_peaks()
+    achieved = BYTES_PER_LU["bf16"] * N / (ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            t = json.load(open(tfile)).get("many_flat:bf16")
+            if t and t.get("step_source_sha256") == step_source_sha256():
+                traffic = t["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    out["bf16_many_flat"] = {"value": N / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": k,
+                             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                                          "bytes_per_lu": BYTES_PER_LU["bf16"]}}
+    b = batched_line(args, torch, world, local, 400, 5, plain=False, precision="bf16")
+    out["batched_bf16_config3"] = {kk: b[kk] for kk in ("value", "unit", "ms_per_step", "steps", "config",
+                                                        "roofline", "clocks")}
+    out["batched_bf16_config3"]["autotune_candidates"] = len(b["autotune_ms_per_step"])
+    # the serving defaults: FP16 storage, the (1/2) dG/dt term omitted (long
+    # solves at these parameters are not stable with the backward difference)
+    sv = serving_line(args, torch, world, 5.0, prec="fp16", dgdt=1)
+    keep = ("sustainable_rate_per_s", "sustainable_batched", "sustainable_plain_fp32_one_launch_per_solve",
+            "plain_fp32_rate_per_s_at_70pct_own_capacity", "plain_fp32_at_70pct_own_capacity",
+            "sustainable_angle_batched_vs_plain", "p99_ratio_plain_over_batched",
+            "throughput_ratio_batched_over_plain_saturated")
+    out["serving_fp16_5s"] = {kk: sv[kk] for kk in keep}
+    out["serving_fp16_5s"]["config"] = sv["config"]
+    out["serving_fp16_5s"]["capacity_mlups"] = {"batched": sv["overloaded_2000_per_s"]["processed_mlups"],
+                                                "plain_fp32": sv["overloaded_2000_per_s_plain_fp32"]["processed_mlups"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,6 +723,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"])
     ap.add_argument("--workload", default="many_flat")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra block (BF16 step, batched config 3, short serving runs)")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--hbm-budget-gb", type=float, default=64.0)
@@ -676,17 +784,33 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        # the K-step region is repeated until it has run for at least 300 ms
+        # (clock samples need that long); each repeat is bracketed by a
+        # barrier and a synchronize, and the repeat count is the same on
+        # every rank (from the slowest rank's first region)
         sampler = ClockSampler(local)
         sampler.start()
+        sampler.wait_first()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        s.step(args.steps)          # K launches of the fused step kernel
-        e1.record(stream)
-        torch.cuda.synchronize()
+
+        def region():
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e0.record(stream)
+            s.step(args.steps)          # K launches of the fused step kernel
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        times = [region()]
+        first = max_over_ranks(times[0], f"cuda:{local}", world)
+        repeats = max(1, min(1000, int(math.ceil(300.0 / max(first, 1e-3)))))
+        while len(times) < repeats:
+            times.append(region())
         clocks = sampler.stop()
-        ms = e0.elapsed_time(e1)
+        ms = sum(times) / len(times)
         s.check()
     ms = max_over_ranks(ms, f"cuda:{local}", world)
     ms_per_step = ms / args.steps
@@ -741,6 +865,10 @@ def main():
     h2d = case.solid.nbytes + (case.theta_field.nbytes if case.theta_field is not None else 0)
     d2h = phi.nbytes + u.nbytes + p.nbytes
 
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and case.name == "many_flat" and args.precision == "fp32":
+        extra = extra_block(args, torch, world, local, case, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups_cpu, cores, desc = oracle_baseline("2d", args.workload, 12.0)
@@ -770,9 +898,14 @@ def main():
                                 "FP64 solves, float32 otherwise)",
                     "host_buffers": "pinned"},
             "gpu_launches": args.steps,
+            "timing": {"repeats": len(times), "note": "each repeat times exactly K steps, bracketed by a "
+                       "barrier and synchronize; ms_per_step is the mean over repeats (max over ranks)",
+                       "ms_per_repeat": [round(t, 4) for t in times[:50]]},
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
+        if extra is not None:
+            line["extra"] = extra
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

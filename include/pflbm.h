@@ -288,6 +288,14 @@ int pflbm_batch_kernel(const pflbm_batch_t* b);
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes);
 void pflbm_batch_destroy(pflbm_batch_t* b);
 
+/* Index-checked debug build (compiled with -DPFLBM_BOUNDS, shipped as
+ * libpflbm_bounds.so beside the library): every global and staged
+ * shared-memory index of the 2D step kernels is checked against its buffer;
+ * an index outside is counted and the access skipped. *enabled: 1 in that
+ * build, 0 in the normal one; *violations: accesses refused so far on the
+ * current device (0 in the normal build). Not in the paper: a test aid. */
+int pflbm_debug_bounds(int* enabled, unsigned* violations);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* pflbm_last_error(void);
 

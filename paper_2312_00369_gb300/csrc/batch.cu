@@ -306,6 +306,7 @@ int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
     if (n < 0) return set_error(PFLBM_EINVAL, "batch: negative step count");
     if (n == 0) return PFLBM_OK;
     DeviceGuard g(b->device);
+    NvtxRange range("pflbm_batch_step");
     bool stale = false;
     for (size_t i = 0; i < b->hs.size(); ++i) {
         pflbm_t* h = b->hs[i];

@@ -439,6 +439,17 @@ int pflbm_create(pflbm_t** out, int nx, int ny, const uint8_t* solid_mask, doubl
 
 void pflbm_destroy(pflbm_t* h) { release(h); }
 
+int pflbm_debug_bounds(int* enabled, unsigned* violations)
+{
+#ifdef PFLBM_BOUNDS
+    if (enabled) *enabled = 1;
+#else
+    if (enabled) *enabled = 0;
+#endif
+    if (violations) *violations = bounds_violations_step() + bounds_violations_tma();
+    return PFLBM_OK;
+}
+
 int pflbm_set_step_kernel(pflbm_t* h, int step_kernel, int step_chunk)
 {
     if (int rc = check_handle(h)) return rc;
@@ -502,6 +513,7 @@ int pflbm_step(pflbm_t* h, int64_t n)
     if (n < 0) return fail(PFLBM_EINVAL, "negative step count");
     if (int rc = read_status(h)) return rc;
     DeviceGuard g(h->device);
+    NvtxRange range("pflbm_step");
     if (int rc = materialize(h)) return rc;
     for (int64_t t = 0; t < n; ++t) {
         CK(launch_step(h));

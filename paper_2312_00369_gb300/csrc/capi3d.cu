@@ -293,6 +293,7 @@ int pflbm3d_step(pflbm3d_t* h, int64_t n)
     if (!h || n < 0) return fail3(PFLBM_EINVAL, "invalid arguments");
     if (int rc = read_status3(h)) return rc;
     DeviceGuard g(h->device);
+    NvtxRange range("pflbm3d_step");
     if (int rc = materialize3(h)) return rc;
     for (int64_t t = 0; t < n; ++t) {
         CK3(launch_step(h));

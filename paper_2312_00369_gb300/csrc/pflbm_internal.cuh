@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -84,6 +86,15 @@ struct DeviceGuard {
     }
     DeviceGuard(const DeviceGuard&) = delete;
     DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// NVTX range around an entry point's device work (visible in Nsight tools;
+// a no-op without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // Tile of the fused step: TX x TY nodes per CTA, one node per thread.
@@ -200,6 +211,9 @@ cudaError_t launch_step_staged(pflbm_t* h, int shape, int blocks_per_item, int c
 cudaError_t launch_step_staged_batch(int precision, const void* d_args, const int4* d_work, int n_work, int grid,
                                      cudaStream_t stream);
 int staged_batch_ctas_per_sm(int precision);
+// index-checked build: out-of-range accesses counted in step.cu / step_tma.cu
+unsigned bounds_violations_step();
+unsigned bounds_violations_tma();
 
 // diag.cu
 cudaError_t launch_mass(pflbm_t* h, double* d_out);

@@ -56,20 +56,21 @@ __device__ __forceinline__ typename Store<PREC>::C pull(const typename Store<PRE
     constexpr int X = cx(I), Y = cy(I), O = opp(I);
     if constexpr (!WRAP) {
         const int k = gy * pitch + gx;
-        if (!CHECK) return T::template ldp<I>(base[k + (I * plane - Y * pitch - X)]);
+        if (!CHECK) return T::template ldp<I>(PFLBM_LD(base, k + (I * plane - Y * pitch - X), 9LL * plane));
         int src = k + O * plane;
         if (zeta_of(s_cls[sy + Y][sx + X])) src = k + (O * plane + Y * pitch + X);
         if (zeta_of(s_cls[sy - Y][sx - X])) src = k + (I * plane - Y * pitch - X);
-        return T::template ldp<I>(base[src]);
+        return T::template ldp<I>(PFLBM_LD(base, src, 9LL * plane));
     }
-    if (!CHECK) return T::template ldp<I>(base[I * plane + (gy - Y) * pitch + wrap1(gx - X, nx)]);
+    if (!CHECK)
+        return T::template ldp<I>(PFLBM_LD(base, I * plane + (gy - Y) * pitch + wrap1(gx - X, nx), 9LL * plane));
     // one load from the selected source, no branch (a warp whose lanes pick
     // different sources still issues one load); I and O share a storage unit
     static_assert(T::template unit<I>() == T::template unit<O>(), "opposite directions share a unit");
     int src = O * plane + gy * pitch + gx;
     if (zeta_of(s_cls[sy + Y][sx + X])) src = O * plane + (gy + Y) * pitch + wrap1(gx + X, nx);
     if (zeta_of(s_cls[sy - Y][sx - X])) src = I * plane + (gy - Y) * pitch + wrap1(gx - X, nx);
-    return T::template ldp<I>(base[src]);
+    return T::template ldp<I>(PFLBM_LD(base, src, 9LL * plane));
 }
 
 template <int PREC, bool CHECK, bool WRAP>
@@ -78,7 +79,7 @@ __device__ __forceinline__ void pull_f(typename Store<PREC>::C v[9], const typen
                                        int pitch, int plane)
 {
     using T = Store<PREC>;
-    v[0] = T::template ldp<0>(f[gy * pitch + gx]);
+    v[0] = T::template ldp<0>(PFLBM_LD(f, gy * pitch + gx, 9LL * plane));
     v[1] = pull<1, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     v[2] = pull<2, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     v[3] = pull<3, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
@@ -96,7 +97,7 @@ __device__ __forceinline__ void pull_g(typename Store<PREC>::C v[9], typename St
                                        int gx, int gy, int nx, int pitch, int plane)
 {
     using T = Store<PREC>;
-    raw0 = P.g0[gy * pitch + gx];
+    raw0 = PFLBM_LD(P.g0, gy * pitch + gx, plane);
     v[0] = T::g0(raw0);
     v[1] = pull<1, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
     v[2] = pull<2, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
@@ -213,7 +214,7 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
     for (int p = tid; p < (TY + 6) * (TX + 6); p += TX * TY) {
         int py = p / (TX + 6), px = p - py * (TX + 6);
         int gy = y0 - 3 + py, gx = wx(x0 - 3 + px);
-        s_cls[py][px] = (gy < 0 || gy >= ny) ? (uint8_t)CLS_OUT : a.cls[gy * pitch + gx];
+        s_cls[py][px] = (gy < 0 || gy >= ny) ? (uint8_t)CLS_OUT : PFLBM_LD(a.cls, gy * pitch + gx, a.plane);
     }
     __syncthreads();
     const uint8_t own = s_cls[ty + 3][tx + 3];
@@ -249,7 +250,7 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
     // the Robin value of Appendix A cases 1 and 3 on flat walls
     fill_ghosts<C, TX, TY, TX + 4>(
         s_phi, [&](int dy, int dx) { return s_cls[dy + 3][dx + 3]; },
-        [&](int dy, int dx) { return a.wet[(y0 + dy) * pitch + wx(x0 + dx)]; }, tid, TX * TY);
+        [&](int dy, int dx) { return PFLBM_LD(a.wet, (y0 + dy) * pitch + wx(x0 + dx), a.plane); }, tid, TX * TY);
     __syncthreads();
 }
 
@@ -284,7 +285,7 @@ __device__ __forceinline__ void step_tile_w(const StepArgs<PREC>& a, int bx, int
             for (int i = 0; i < 9; ++i) fv[i] = f[i];
         } else
             pull_f<PREC, false, WRAP>(fv, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
-    }, [&](int k) { return (C)a.sprev[k]; });
+    }, [&](int k) { return (C)PFLBM_LD(a.sprev, k, a.plane); });
 }
 
 template <int PREC, bool COLLIDE, int VV>
@@ -741,5 +742,16 @@ cudaError_t launch_macro_f32(pflbm_t* h, float* phi, float* u, float* p)
         default: return run_step_kernel<PFLBM_FP16, false>(h, nullptr, nullptr, nullptr, phi, u, p);
     }
 }
+
+#ifdef PFLBM_BOUNDS
+unsigned bounds_violations_step()
+{
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_bounds_viol, sizeof(v));
+    return v;
+}
+#else
+unsigned bounds_violations_step() { return 0; }
+#endif
 
 }  // namespace pfk

@@ -10,6 +10,39 @@
 
 namespace pfk {
 
+// Index-checked debug build (-DPFLBM_BOUNDS): every global and staged
+// shared-memory access of the step kernels goes through PFLBM_LD / PFLBM_ST,
+// which check the index against the size of the buffer it addresses; an
+// index outside is counted (per translation unit, read back by
+// pflbm_debug_bounds) and the access is skipped (a load returns zero). The
+// normal build compiles them to the plain access.
+#ifdef PFLBM_BOUNDS
+static __device__ unsigned g_bounds_viol = 0;
+template <typename T>
+__device__ __forceinline__ T bounds_load(const T* p, long long i, long long n)
+{
+    if (i < 0 || i >= n) {
+        atomicAdd(&g_bounds_viol, 1u);
+        return T();
+    }
+    return p[i];
+}
+template <typename T, typename V>
+__device__ __forceinline__ void bounds_store(T* p, long long i, long long n, V v)
+{
+    if (i < 0 || i >= n) {
+        atomicAdd(&g_bounds_viol, 1u);
+        return;
+    }
+    p[i] = v;
+}
+#define PFLBM_LD(p, i, n) ::pfk::bounds_load((p), (long long)(i), (long long)(n))
+#define PFLBM_ST(p, i, n, v) ::pfk::bounds_store((p), (long long)(i), (long long)(n), (v))
+#else
+#define PFLBM_LD(p, i, n) ((p)[i])
+#define PFLBM_ST(p, i, n, v) ((p)[i] = (v))
+#endif
+
 // Tensor maps (CUtensorMap, built on the host by cuTensorMapEncodeTiled) of
 // one population copy as the staged step reads it with one tile shape.
 struct alignas(64) TmaSet {
@@ -145,8 +178,8 @@ __device__ __forceinline__ void collide_f_pair(const StepArgs<PREC>& a, typename
         S = w * S;
         A = w * A;
     }
-    a.out.f[I * a.plane + k] = T::template stp<I>(fmadd(K.omf, fI, S + A));
-    a.out.f[O * a.plane + k] = T::template stp<O>(fmadd(K.omf, fO, S - A));
+    PFLBM_ST(a.out.f, I * a.plane + k, 9LL * a.plane, T::template stp<I>(fmadd(K.omf, fI, S + A)));
+    PFLBM_ST(a.out.f, O * a.plane + k, 9LL * a.plane, T::template stp<O>(fmadd(K.omf, fO, S - A)));
 }
 
 // g_i (i != 0) collision and store; returns the storage rounding residual
@@ -163,7 +196,7 @@ __device__ __forceinline__ typename Store<PREC>::C collide_g_dir(const StepArgs<
     // second term, the same for the four axes and for the four diagonals
     const C v = fmadd(omg, g_i, gadd);
     const typename T::S s = T::template stp<I>(v);
-    a.out.g[I * a.plane + k] = s;
+    PFLBM_ST(a.out.g, I * a.plane + k, 9LL * a.plane, s);
     if (T::kAbsorb) return v - T::template ldp<I>(s);   // in work units
     return C(0);
 }
@@ -190,12 +223,13 @@ __device__ __forceinline__ void node_step(const StepArgs<PREC>& a, uint8_t code,
     if (!zeta_of(code)) {
         if (!COLLIDE) {
             const size_t o = (size_t)gy * a.nx + gx;
-            if (a.o_phi) a.o_phi[o] = (double)s_phi[py][px];
-            if (a.o_u) { a.o_u[2 * o] = 0.0; a.o_u[2 * o + 1] = 0.0; }
-            if (a.o_p) a.o_p[o] = 0.0;
-            if (a.f_phi) a.f_phi[o] = (float)s_phi[py][px];
-            if (a.f_u) { a.f_u[2 * o] = 0.0f; a.f_u[2 * o + 1] = 0.0f; }
-            if (a.f_p) a.f_p[o] = 0.0f;
+            const long long no = (long long)a.nx * a.ny;
+            if (a.o_phi) PFLBM_ST(a.o_phi, o, no, (double)s_phi[py][px]);
+            if (a.o_u) { PFLBM_ST(a.o_u, 2 * o, 2 * no, 0.0); PFLBM_ST(a.o_u, 2 * o + 1, 2 * no, 0.0); }
+            if (a.o_p) PFLBM_ST(a.o_p, o, no, 0.0);
+            if (a.f_phi) PFLBM_ST(a.f_phi, o, no, (float)s_phi[py][px]);
+            if (a.f_u) { PFLBM_ST(a.f_u, 2 * o, 2 * no, 0.0f); PFLBM_ST(a.f_u, 2 * o + 1, 2 * no, 0.0f); }
+            if (a.f_p) PFLBM_ST(a.f_p, o, no, 0.0f);
         }
         return;
     }
@@ -204,7 +238,7 @@ __device__ __forceinline__ void node_step(const StepArgs<PREC>& a, uint8_t code,
     C gpx, gpy, lap;
     stencils<C, PW>(s_phi, py, px, gpx, gpy, lap);
     const C ph = s_phi[py][px];
-    const C wet = (code & F_WET) ? a.wet[k] : C(0);
+    const C wet = (code & F_WET) ? PFLBM_LD(a.wet, k, a.plane) : C(0);
     const C mu = fmadd(-wet, fmadd(-ph, ph, ph), fmadd(-a.kappa, lap, a.beta4 * ph * (ph - C(1)) * (ph - C(0.5))));
 
     // ---- coupling fields (Sec. 2.1.1): F = F_s + F_b, F_s = mu grad(phi), F_b = rho g ----
@@ -232,12 +266,13 @@ __device__ __forceinline__ void node_step(const StepArgs<PREC>& a, uint8_t code,
 
     if (!COLLIDE) {
         size_t o = (size_t)gy * a.nx + gx;
-        if (a.o_phi) a.o_phi[o] = (double)ph;
-        if (a.o_u) { a.o_u[2 * o] = (double)ux; a.o_u[2 * o + 1] = (double)uy; }
-        if (a.o_p) a.o_p[o] = (double)p;
-        if (a.f_phi) a.f_phi[o] = (float)ph;
-        if (a.f_u) { a.f_u[2 * o] = (float)ux; a.f_u[2 * o + 1] = (float)uy; }
-        if (a.f_p) a.f_p[o] = (float)p;
+        const long long no = (long long)a.nx * a.ny;
+        if (a.o_phi) PFLBM_ST(a.o_phi, o, no, (double)ph);
+        if (a.o_u) { PFLBM_ST(a.o_u, 2 * o, 2 * no, (double)ux); PFLBM_ST(a.o_u, 2 * o + 1, 2 * no, (double)uy); }
+        if (a.o_p) PFLBM_ST(a.o_p, o, no, (double)p);
+        if (a.f_phi) PFLBM_ST(a.f_phi, o, no, (float)ph);
+        if (a.f_u) { PFLBM_ST(a.f_u, 2 * o, 2 * no, (float)ux); PFLBM_ST(a.f_u, 2 * o + 1, 2 * no, (float)uy); }
+        if (a.f_p) PFLBM_ST(a.f_p, o, no, (float)p);
         return;
     }
     if (!(uu < C(0.09))) atomicOr(a.status, 1);
@@ -253,7 +288,7 @@ __device__ __forceinline__ void node_step(const StepArgs<PREC>& a, uint8_t code,
     {
         C feq0 = fmadd(-(rho * (wgt<C>(0) * C(1.5))), uu, (C(-5) / C(3)) * p);
         if constexpr (T::kNorm) feq0 = feq0 * (C(1) / T::template unit<0>());
-        a.out.f[k] = T::template stp<0>(fmadd(omega_f, feq0 - f[0], f[0]));
+        PFLBM_ST(a.out.f, k, 9LL * a.plane, T::template stp<0>(fmadd(omega_f, feq0 - f[0], f[0])));
     }
     {
         PairK<C> K;
@@ -297,9 +332,9 @@ __device__ __forceinline__ void node_step(const StepArgs<PREC>& a, uint8_t code,
         // g_0^eq - g_0 = sum_{i!=0} g_i - (1 - w_0) alpha mu (Eq. H_i); in the
         // 16-bit formats g_0 also takes back what rounding removed from g_1..g_8
         const C d0 = fmadd(a.omega_g, fmadd(-(C(1) - wgt<C>(0)), am, sum_pop<PREC>(g)), (wgt<C>(0) * C(-2)) * src);
-        a.out.g0[k] = T::g0_add(g0raw, T::kAbsorb ? d0 + resid : d0, a.status);
+        PFLBM_ST(a.out.g0, k, a.plane, T::g0_add(g0raw, T::kAbsorb ? d0 + resid : d0, a.status));
     }
-    if (!a.dgdt) a.sprev[k] = s_now;
+    if (!a.dgdt) PFLBM_ST(a.sprev, k, a.plane, s_now);
 }
 
 // Ghost values of the phi tile (halo 2): every ghost node within one node of

@@ -159,7 +159,10 @@ struct View {
         if (st >= Gm::NS) st -= Gm::NS;
         return st * (Gm::STAGE0 / 4) + ((d + 3) % TYT) * Gm::W0;
     }
-    __device__ __forceinline__ uint8_t c(int d, int dx) const { return cls[(d + 3) * Gm::WC + dx + Gm::AC]; }
+    __device__ __forceinline__ uint8_t c(int d, int dx) const
+    {
+        return PFLBM_LD(cls, (d + 3) * Gm::WC + dx + Gm::AC, Gm::CR * Gm::WC);
+    }
 };
 
 // Pulled populations of lattice P0 (0: f, 9: g) at window position (d, dx):
@@ -183,18 +186,19 @@ __device__ __forceinline__ void spull(typename Store<PREC>::C v[9], const View<P
             if (zeta_of(V.c(d + Y, dx + X))) src = row(Y) + (P0 + O) * Gm::PL + c + X;
             if (zeta_of(V.c(d - Y, dx - X))) src = srcs;
         }
+        constexpr long long NE = (long long)Gm::NS * (Gm::STAGE / Gm::ES);   // ring elements
         switch (i) {   // the unit of direction i is a template argument of the load
-            case 1: v[1] = T::template ldp<1>(V.pop[src]); break;
-            case 2: v[2] = T::template ldp<2>(V.pop[src]); break;
-            case 3: v[3] = T::template ldp<3>(V.pop[src]); break;
-            case 4: v[4] = T::template ldp<4>(V.pop[src]); break;
-            case 5: v[5] = T::template ldp<5>(V.pop[src]); break;
-            case 6: v[6] = T::template ldp<6>(V.pop[src]); break;
-            case 7: v[7] = T::template ldp<7>(V.pop[src]); break;
-            default: v[8] = T::template ldp<8>(V.pop[src]); break;
+            case 1: v[1] = T::template ldp<1>(PFLBM_LD(V.pop, src, NE)); break;
+            case 2: v[2] = T::template ldp<2>(PFLBM_LD(V.pop, src, NE)); break;
+            case 3: v[3] = T::template ldp<3>(PFLBM_LD(V.pop, src, NE)); break;
+            case 4: v[4] = T::template ldp<4>(PFLBM_LD(V.pop, src, NE)); break;
+            case 5: v[5] = T::template ldp<5>(PFLBM_LD(V.pop, src, NE)); break;
+            case 6: v[6] = T::template ldp<6>(PFLBM_LD(V.pop, src, NE)); break;
+            case 7: v[7] = T::template ldp<7>(PFLBM_LD(V.pop, src, NE)); break;
+            default: v[8] = T::template ldp<8>(PFLBM_LD(V.pop, src, NE)); break;
         }
     }
-    if (P0 == 0) v[0] = T::template ldp<0>(V.pop[r0 + c]);
+    if (P0 == 0) v[0] = T::template ldp<0>(PFLBM_LD(V.pop, r0 + c, (long long)Gm::NS * (Gm::STAGE / Gm::ES)));
 }
 
 template <int PREC, int TXT, int TYT, bool CHECK>
@@ -204,8 +208,8 @@ __device__ __forceinline__ void spull_g(typename Store<PREC>::C v[9], typename S
     using T = Store<PREC>;
     using Gm = Geo<PREC, TXT, TYT>;
     spull<PREC, TXT, TYT, CHECK, 9>(v, V, d, dx);
-    if constexpr (Gm::kG0) raw0 = V.g0[V.r0base(d) + dx + Gm::A0];
-    else raw0 = __float_as_int(V.pop[V.rbase(d) + 9 * Gm::PL + dx + Gm::A]);
+    if constexpr (Gm::kG0) raw0 = PFLBM_LD(V.g0, V.r0base(d) + dx + Gm::A0, Gm::NS * (Gm::STAGE0 / 4));
+    else raw0 = __float_as_int(PFLBM_LD(V.pop, V.rbase(d) + 9 * Gm::PL + dx + Gm::A, Gm::NS * (Gm::STAGE / Gm::ES)));
     v[0] = T::g0(raw0);
 }
 
@@ -263,7 +267,7 @@ __device__ __forceinline__ void fix_group(const StepArgs<PREC>& a, unsigned char
                 if (y < 0 || y >= ny || !((j < 3 && left) || (j >= 3 && right))) continue;
                 int xs = (x0 + dx) % nx;
                 if (xs < 0) xs += nx;
-                cw[r * Gm::WC + dx + Gm::AC] = a.cls[(size_t)y * a.pitch + xs];
+                PFLBM_ST(cw, r * Gm::WC + dx + Gm::AC, Gm::CR * Gm::WC, PFLBM_LD(a.cls, (size_t)y * a.pitch + xs, a.plane));
             }
         }
     }
@@ -280,12 +284,14 @@ __device__ __forceinline__ void fix_group(const StepArgs<PREC>& a, unsigned char
         if (xs < 0) xs += nx;
         const size_t k = (size_t)y * a.pitch + xs;
         if (pl < 9) {
-            pop[pl * Gm::PL + r * Gm::W + dx + Gm::A] = a.in.f[(size_t)pl * a.plane + k];
+            PFLBM_ST(pop, pl * Gm::PL + r * Gm::W + dx + Gm::A, 18 * Gm::PL,
+                     PFLBM_LD(a.in.f, (size_t)pl * a.plane + k, 18LL * a.plane));
         } else if (pl < 9 + Gm::NGP) {
             const int gp = Gm::GP0 + (pl - 9);   // plane index in the [18] layout
-            pop[gp * Gm::PL + r * Gm::W + dx + Gm::A] = a.in.f[(size_t)gp * a.plane + k];
+            PFLBM_ST(pop, gp * Gm::PL + r * Gm::W + dx + Gm::A, 18 * Gm::PL,
+                     PFLBM_LD(a.in.f, (size_t)gp * a.plane + k, 18LL * a.plane));
         } else {
-            g0r[r * Gm::W0 + dx + Gm::A0] = (int32_t)a.in.g0[k];
+            PFLBM_ST(g0r, r * Gm::W0 + dx + Gm::A0, TYT * Gm::W0, (int32_t)PFLBM_LD(a.in.g0, k, a.plane));
         }
     }
 }
@@ -406,7 +412,7 @@ __device__ __forceinline__ bool march(const StepArgs<PREC>& a, const TmaSet* ts,
         const int gx = x0 + tx, gy = y0 + ty;
         const bool mine = gx < a.nx && gy < a.ny;
         C sp = C(0);   // the u.grad(phi) history, loaded early
-        if (mine && !a.dgdt) sp = a.sprev[gy * a.pitch + gx];
+        if (mine && !a.dgdt) sp = PFLBM_LD(a.sprev, gy * a.pitch + gx, a.plane);
         const uint8_t tf = flags[b * nsx + sx];
         const bool fluid = (tf & 1) != 0;
         const int halo = (tf & 2) ? 2 : 1;
@@ -434,7 +440,7 @@ __device__ __forceinline__ bool march(const StepArgs<PREC>& a, const TmaSet* ts,
                 [&](int dy, int dxx) {
                     int xs = (x0 + dxx) % a.nx;
                     if (xs < 0) xs += a.nx;
-                    return a.wet[(y0 + dy) * a.pitch + xs];
+                    return PFLBM_LD(a.wet, (y0 + dy) * a.pitch + xs, a.plane);
                 },
                 tid, kThreads);
             __syncthreads();
@@ -767,6 +773,17 @@ cudaError_t launch_step_staged_batch(int precision, const void* d_args, const in
         default: return cudaErrorInvalidValue;
     }
 }
+
+#ifdef PFLBM_BOUNDS
+unsigned bounds_violations_tma()
+{
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_bounds_viol, sizeof(v));
+    return v;
+}
+#else
+unsigned bounds_violations_tma() { return 0; }
+#endif
 
 int staged_batch_ctas_per_sm(int precision)
 {

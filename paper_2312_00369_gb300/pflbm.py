@@ -16,7 +16,10 @@ import weakref
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpflbm.so")
+# PFLBM_LIBRARY selects another build of the same library (the index-checked
+# libpflbm_bounds.so beside it); the default is libpflbm.so
+LIB_PATH = os.environ.get("PFLBM_LIBRARY") or os.path.join(HERE, "libpflbm.so")
+BOUNDS_LIB_PATH = os.path.join(HERE, "libpflbm_bounds.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pflbm.h")
 
 OK, EINVAL, ENOMEM, EBADMASK, ENUMERIC, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
@@ -117,6 +120,7 @@ _SIGS = {
     "pflbm_destroy": (None, [_H]),
     "pflbm_set_theta_field": (ctypes.c_int, [_H, _fp]),
     "pflbm_set_step_kernel": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    "pflbm_debug_bounds": (ctypes.c_int, [_ip, ctypes.POINTER(ctypes.c_uint)]),
     "pflbm_get_step_kernel": (ctypes.c_int, [_H]),
     "pflbm_init_droplet": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "pflbm_init_phi": (ctypes.c_int, [_H, _dp]),
@@ -201,6 +205,13 @@ def pflbm_lattice():
     cy = (ctypes.c_int * 9)()
     lib().pflbm_lattice(cx, cy)
     return np.array(cx[:]), np.array(cy[:])
+
+
+def debug_bounds():
+    """(enabled, violations) of the index-checked build (see pflbm.h)."""
+    e, v = ctypes.c_int(), ctypes.c_uint()
+    _check(lib().pflbm_debug_bounds(ctypes.byref(e), ctypes.byref(v)))
+    return bool(e.value), int(v.value)
 
 
 def pflbm_footprint_bytes(nx, ny, precision="fp32"):

@@ -184,6 +184,10 @@ class Server:
         self.slots = [sl for sl in self.slots if sl not in failed]
 
     def step_tick(self, now_fn):
+        with self.torch.cuda.nvtx.range(f"serve tick ({len(self.slots)} solves)"):
+            return self._step_tick(now_fn)
+
+    def _step_tick(self, now_fn):
         out = []
         # solves that reported a NaN or |u| >= 0.3 leave as failed requests
         # (the flag is read without waiting; a refused step did no work)

@@ -244,3 +244,20 @@ def max2d_window_run(x_centre, half, steps):
     o.step(steps)
     phi, u, p = o.get()
     return dict(phi=phi[:, half], u=u[:, half], p=p[:, half])
+
+
+def run_instance(nx, ny, wall_type, theta, steps, dgdt=0):
+    """Oracle run of one batched / served instance (workloads.batch_instance):
+    the fitted contact angle (the same wall and exclusion band as the
+    library's fit), phi and the mass after ``steps``."""
+    c = wl.batch_instance(None, nx, ny, wall_type, theta, steps)
+    o = oracle.Oracle(c.solid, theta_deg=c.theta_deg, **c.physical())
+    if dgdt:
+        o.set_dgdt(dgdt)
+    for d in c.droplets:
+        o.init_droplet(*d)
+    o.step(steps)
+    phi, u, _ = o.get()
+    th, circ, n = oracle.contact_angle(phi, o.geometry()["cls"], dict(c.wall, exclude=1.5 * c.W))
+    return dict(theta=th, npts=n, phi=phi, mass=o.mass(), umax=float(np.abs(u).max()))
+

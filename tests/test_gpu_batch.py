@@ -6,11 +6,35 @@ bit. A member stepped on its own between batched steps, odd step counts and
 membership changes must keep that property. One member is also checked
 against the FP64 oracle.
 """
+import multiprocessing as mp
+
 import numpy as np
 import pytest
 
+from tests import oracle_jobs as oj
+
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+# config-3 instances in BF16 storage against the FP64 oracle: every wall
+# type, the three smaller batch sizes, 5000 steps (a 64 x 32 lattice's
+# droplet of radius 6.4 leaves too few contour points outside the exclusion
+# band for an angle fit: phi only)
+CFG3 = [(64, 32, 0, 45.0), (64, 32, 1, 120.0), (128, 64, 2, 75.0), (128, 64, 0, 140.0), (128, 64, 1, 95.0),
+        (256, 128, 1, 60.0), (256, 128, 2, 100.0), (256, 128, 0, 35.0)]
+CFG3_STEPS = 5000
+_pool = None
+_fut = []
+
+
+@pytest.fixture(scope="module", autouse=True)
+def oracle_pool():
+    global _pool
+    _pool = mp.get_context("spawn").Pool(processes=len(CFG3))
+    for (nx, ny, wt, th) in CFG3:
+        _fut.append(_pool.apply_async(oj.run_instance, (nx, ny, wt, th, CFG3_STEPS, 0)))
+    yield
+    _pool.terminate()
 
 
 def mix(seed=5, n=9):
@@ -103,3 +127,61 @@ def test_autotune_picks_a_measured_schedule(tmp_path, monkeypatch):
     assert best in cands and len(timings) == 2 and all(t > 0 for t in timings.values())
     again, _ = autotune.tune(cases, "bf16", candidates=cands)      # served from the cache
     assert again == best
+
+
+def test_autotune_tunes_staged_size_classes(tmp_path, monkeypatch):
+    # the default search: the global-load kernel's grid, then the staged
+    # kernel's shape and item length per size class; the chosen schedule
+    # steps every member exactly as it steps alone
+    from paper_2312_00369_gb300 import autotune
+    from paper_2312_00369_gb300.pflbm import Batch
+    monkeypatch.setenv("PFLBM_TUNE_CACHE", str(tmp_path / "sched.json"))
+    cases = mix(seed=3, n=6)
+    best, timings = autotune.tune(cases, "bf16", steps=3, warmup=1)
+    assert any(k.startswith("global_") for k in timings) and any(k.startswith("staged[") for k in timings)
+    assert timings[autotune.name_of(best)] == min(timings.values())
+    stream = torch.cuda.Stream()
+    alone = make(cases, "bf16", stream)
+    for s in alone:
+        s.step(13)
+    together = make(cases, "bf16", stream)
+    b = Batch(together, autotune.to_schedule(best))
+    b.step(13)
+    for a, t in zip(alone, together):
+        for x, y in zip(a.get(), t.get()):
+            assert np.array_equal(x, y)
+    b.close()
+
+
+def test_batched_bf16_members_match_oracle():
+    # config 3's precision pattern (BF16 storage, FP32 arithmetic) in one
+    # batch of uneven lattices: each member's contact angle within 0.5 deg of
+    # the FP64 oracle's, phi within the stated bound
+    from paper_2312_00369_gb300 import workloads as wl
+    from paper_2312_00369_gb300.pflbm import Batch, Solver, schedule
+    stream = torch.cuda.Stream()
+    cases = [wl.batch_instance(None, nx, ny, wt, th, CFG3_STEPS) for (nx, ny, wt, th) in CFG3]
+    members = []
+    for c in cases:
+        s = Solver(c.solid, theta_deg=c.theta_deg, precision="bf16", stream=stream, **c.physical())
+        for d in c.droplets:
+            s.init_droplet(*d)
+        members.append(s)
+    b = Batch(members, schedule(tiles_per_item=4))
+    b.step(CFG3_STEPS)
+    for c, s, f in zip(cases, members, _fut):
+        ref = f.get(timeout=1800)
+        phi, _, _ = s.get()
+        dphi = float(np.max(np.abs(phi - ref["phi"])))
+        if c.ny >= 64:
+            th, _, _ = s.contact_angle(dict(c.wall, exclude=1.5 * c.W))
+            print(f"{c.nx}x{c.ny} {c.name} theta {c.theta_deg:.0f}: bf16 {th:.4f} oracle {ref['theta']:.4f} "
+                  f"max|dphi| {dphi:.2e}")
+            assert abs(th - ref["theta"]) < 0.5
+        else:
+            print(f"{c.nx}x{c.ny} {c.name} theta {c.theta_deg:.0f}: max|dphi| {dphi:.2e}")
+        assert dphi < 2e-2
+    b.close()
+    for s in members:
+        s.close()
+

@@ -240,8 +240,10 @@ def test_contact_angle_fp32_within_half_degree():
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_16bit_storage_error_and_contact_angle(precision):
     # f_i and g_i (i != 0) in 16 bits, g_0 32-bit fixed point, FP32 arithmetic:
-    # the error against the FP64 oracle is reported; the bar is the contact
-    # angle within 0.5 deg of the oracle's (mass within 1e-4, phi within 5e-2).
+    # the error against the FP64 oracle is reported; the bars are the contact
+    # angle within 0.5 deg of the oracle's and about 3x the measured errors
+    # (BF16: max|dphi| 4.9e-4, mass 2.2e-5 relative, theta 0.011 deg; FP16:
+    # 5.4e-6, 1.1e-6, below 1e-4 deg), so a regression of a few times fails.
     case = oj.case_by_name("flat60")
     r = ref("flat60")
     s = solver(case, precision)
@@ -252,9 +254,10 @@ def test_16bit_storage_error_and_contact_angle(precision):
     th, _, _ = s.contact_angle(case.wall)
     print(f"{precision}: max|dphi|={dphi:.3e} max|du|={du:.3e} theta={th:.4f} "
           f"oracle={r['theta']:.4f} mass_rel={(s.mass() - r['mass']) / r['mass']:.3e}")
-    assert abs(th - r["theta"]) < 0.5
-    assert abs(s.mass() - r["mass"]) <= 1e-4 * abs(r["mass"])
-    assert dphi < 5e-2
+    bar = {"bf16": dict(phi=1.5e-3, mass=7e-5, theta=0.035), "fp16": dict(phi=2e-5, mass=4e-6, theta=1e-3)}[precision]
+    assert abs(th - r["theta"]) < min(0.5, bar["theta"])
+    assert abs(s.mass() - r["mass"]) <= bar["mass"] * abs(r["mass"])
+    assert dphi < bar["phi"]
 
 
 # ------------------------------------------------------------ host paths --

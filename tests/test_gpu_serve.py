@@ -1,11 +1,34 @@
 """Continuous batching: every request's result is the same alone and in the
-mix, admission respects the HBM budget, and reduced-precision storage stays
-within 0.5 deg of the FP32 contact angle."""
+mix, admission respects the HBM budget, reduced-precision storage stays
+within 0.5 deg of the FP32 contact angle, and the served FP16 results stay
+within 0.5 deg of the FP64 oracle's run of the same requests."""
+import multiprocessing as mp
+
 import numpy as np
 import pytest
 
+from tests import oracle_jobs as oj
+
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+# served requests checked against the oracle: 128 x 64 and 160 x 80 lattices
+# of every wall type, 2000-3000 steps, the serving default (the (1/2) dG/dt
+# term omitted)
+ORACLE_REQS = [(128, 64, 0, 55.0, 3000), (128, 64, 1, 100.0, 2500), (160, 80, 2, 80.0, 2000),
+               (128, 64, 0, 125.0, 2500), (160, 80, 1, 65.0, 2000), (128, 64, 2, 140.0, 3000)]
+_pool = None
+_fut = []
+
+
+@pytest.fixture(scope="module", autouse=True)
+def oracle_pool():
+    global _pool
+    _pool = mp.get_context("spawn").Pool(processes=len(ORACLE_REQS))
+    for (nx, ny, wt, th, st) in ORACLE_REQS:
+        _fut.append(_pool.apply_async(oj.run_instance, (nx, ny, wt, th, st, 1)))
+    yield
+    _pool.terminate()
 
 
 def small_stream(n=12, seed=4):
@@ -74,3 +97,28 @@ def test_plain_server_completes_same_requests():
     for r in stats.results:
         th, n, m = alone(reqs[r.rid], "fp32")
         assert r.mass == m and abs(r.theta_fit - th) < 1e-9
+
+
+def test_served_fp16_angles_match_oracle():
+    # the requests go through the continuous-batching server in FP16 (they
+    # overlap on the device); each fitted angle is compared with the FP64
+    # oracle's run of the same request
+    from paper_2312_00369_gb300 import pflbm
+    from paper_2312_00369_gb300.serve import Request, Server
+    reqs = [Request(i, 0.002 * i, nx, ny, wt, th, st) for i, (nx, ny, wt, th, st) in enumerate(ORACLE_REQS)]
+    biggest = max(pflbm.pflbm_footprint_bytes(r.nx, r.ny, "fp16") for r in reqs)
+    srv = Server(precision="fp16", hbm_budget=4 * biggest, tick=200, dgdt_mode=1)
+    stats = srv.run(reqs, duration=10.0, drain=True, max_wall=300.0)
+    srv.close()
+    assert len(stats.results) == len(reqs) and stats.peak_slots >= 2
+    worst = 0.0
+    for r in stats.results:
+        ref = _fut[r.rid].get(timeout=1800)
+        d = abs(r.theta_fit - ref["theta"])
+        worst = max(worst, d)
+        print(f"request {r.rid}: served {r.theta_fit:.4f} oracle {ref['theta']:.4f} |d| {d:.4f} deg")
+        assert not r.failed
+        assert d < 0.5
+        assert abs(r.mass - ref["mass"]) <= 1e-3 * abs(ref["mass"])
+    print(f"worst |theta_served - theta_oracle| = {worst:.4f} deg")
+
