@@ -733,7 +733,7 @@ def main():
     ap.add_argument("--size3d", default="512x512x128", help="nx x ny x nz of many_flat3d")
     ap.add_argument("--path3d", default="auto", choices=["auto", "fused", "three_pass"],
                     help="3D step: one fused launch or three launches")
-    ap.add_argument("--kernel", default="default", choices=["default", "global", "staged32x8", "staged64x4"],
+    ap.add_argument("--kernel", default="default", choices=["default", "global", "staged32x8", "staged64x4", "pair"],
                     help="2D step kernel (results identical; speed differs)")
     ap.add_argument("--chunk", type=int, default=0, help="staged kernel: tiles per work item (0: library default)")
     ap.add_argument("--dgdt", type=int, default=0, choices=[0, 1],

@@ -99,9 +99,10 @@ typedef struct {
     /* Step kernel (results are identical bit for bit; only the speed
      * differs). 0: the library's default (1); 1: populations pulled from
      * global memory, 32 x 8 tiles; 2: populations staged in shared memory
-     * by TMA, 32 x 8 tiles; 3: staged, 64 x 4 tiles. FP64 handles always
-     * use 1. step_chunk: tiles a CTA of the staged kernel marches down one
-     * tile column per work item (<= 0: 16). */
+     * by TMA, 32 x 8 tiles; 3: staged, 64 x 4 tiles; 4: global loads, two
+     * x-adjacent nodes per thread in packed FP32x2 arithmetic, 64 x 8
+     * tiles. FP64 handles always use 1. step_chunk: tiles a CTA of the
+     * staged kernel marches down one tile column per work item (<= 0: 16). */
     int step_kernel;
     int step_chunk;
 } pflbm_params_t;
@@ -141,7 +142,7 @@ void pflbm_destroy(pflbm_t* h);
  * and step_chunk). EINVAL for a staged kernel on an FP64 handle or when the
  * handle's tensor maps could not be built. */
 int pflbm_set_step_kernel(pflbm_t* h, int step_kernel, int step_chunk);
-/* The step kernel a handle uses (1, 2 or 3 as above). */
+/* The step kernel a handle uses (1 to 4 as above). */
 int pflbm_get_step_kernel(const pflbm_t* h);
 
 /* Replace the contact-angle field (degrees, [ny][nx], copied). Takes effect

@@ -206,8 +206,14 @@ int ensure_out(pflbm_t* h)
 // instructions per node and runs at 4 instead of 6 resident CTAs per SM).
 int select_step_kernel(pflbm_t* h, int kernel, int chunk)
 {
-    if (kernel < 0 || kernel > 3) return fail(PFLBM_EINVAL, "step_kernel must be 0, 1, 2 or 3");
+    if (kernel < 0 || kernel > 4) return fail(PFLBM_EINVAL, "step_kernel must be 0, 1, 2, 3 or 4");
     if (kernel == 0) kernel = 1;
+    if (kernel == 4) {
+        if (h->precision == PFLBM_FP64) return fail(PFLBM_EINVAL, "the two-node step kernel needs FP32 or 16-bit storage");
+        h->step_shape = -2;
+        h->step_chunk = chunk > 0 ? chunk : 16;
+        return PFLBM_OK;
+    }
     if (kernel >= 2 && (h->precision == PFLBM_FP64 || !h->tma))
         return fail(PFLBM_EINVAL, "the staged step kernel needs FP32 or 16-bit storage and its tensor maps");
     h->step_shape = kernel - 2;
@@ -459,7 +465,7 @@ int pflbm_set_step_kernel(pflbm_t* h, int step_kernel, int step_chunk)
 int pflbm_get_step_kernel(const pflbm_t* h)
 {
     if (!h) return PFLBM_EINVAL;
-    return h->step_shape + 2;
+    return h->step_shape == -2 ? 4 : h->step_shape + 2;
 }
 
 int pflbm_set_theta_field(pflbm_t* h, const float* theta_deg)

@@ -164,7 +164,8 @@ struct pflbm {
     // staged step (FP32 and 16-bit): tensor maps [shape][copy] in device memory
     pfk::TmaSet* tma = nullptr;
     uint8_t* sflags = nullptr;    // staged step: per-tile flags of both shapes
-    int step_shape = -1;          // -1: global-load step kernel; 0: 32 x 8; 1: 64 x 4 staged
+    int step_shape = -1;          // -1: global-load step kernel; 0: 32 x 8; 1: 64 x 4 staged;
+                                  // -2: global loads, two nodes per thread (packed FP32x2)
     int step_chunk = 16;          // staged step: tiles per work item (blocks a CTA marches)
 };
 
@@ -194,6 +195,8 @@ __host__ __device__ inline int tiles_y(int ny) { return (ny + TY - 1) / TY; }
 cudaError_t launch_init_phi_droplet(pflbm_t* h, double x0, double y0, double R, int replace);
 cudaError_t launch_init_populations(pflbm_t* h);
 cudaError_t launch_step(pflbm_t* h);
+// step2.cu: two x-adjacent nodes per thread in packed FP32x2 (FP32, 16-bit)
+cudaError_t launch_step2(pflbm_t* h);
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p);
 cudaError_t launch_macro_f32(pflbm_t* h, float* phi, float* u, float* p);   // rounded to nearest
 size_t step_args_bytes(int precision);

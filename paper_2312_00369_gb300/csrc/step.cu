@@ -25,6 +25,12 @@
 // no O(1) term.
 #include "step_core.cuh"
 
+#ifndef PFLBM_BATCH_MINB
+#define PFLBM_BATCH_MINB 5   // resident 256-thread CTAs per SM asked of k_step_batch (FP32, 16-bit)
+#endif
+#ifndef PFLBM_PREFETCH_F_WALL
+#define PFLBM_PREFETCH_F_WALL 0   // tiles with walls: pull f with g, before the phi-tile barriers
+#endif
 #ifndef PFLBM_PREFETCH_F
 #define PFLBM_PREFETCH_F 0   // fluid tiles: pull f before the phi-tile barrier
 #endif
@@ -42,83 +48,6 @@
 
 namespace pfk {
 namespace {
-
-// Pull of direction I at node (gx, gy), whose class byte sits at s_cls[sy][sx].
-// CHECK = false: every neighbour is a zeta = 1 node (s_cls is not read).
-// WRAP = false: the neighbours x +- 1 lie inside 0..nx-1 (a tile away from the
-// periodic seam), so every source is the node's own index plus a fixed offset.
-template <int I, int PREC, bool CHECK, bool WRAP>
-__device__ __forceinline__ typename Store<PREC>::C pull(const typename Store<PREC>::S* __restrict__ base,
-                                                        const uint8_t (*s_cls)[TX + 6], int sy, int sx, int gx,
-                                                        int gy, int nx, int pitch, int plane)
-{
-    using T = Store<PREC>;
-    constexpr int X = cx(I), Y = cy(I), O = opp(I);
-    if constexpr (!WRAP) {
-        const int k = gy * pitch + gx;
-        if (!CHECK) return T::template ldp<I>(PFLBM_LD(base, k + (I * plane - Y * pitch - X), 9LL * plane));
-        int src = k + O * plane;
-        if (zeta_of(s_cls[sy + Y][sx + X])) src = k + (O * plane + Y * pitch + X);
-        if (zeta_of(s_cls[sy - Y][sx - X])) src = k + (I * plane - Y * pitch - X);
-        return T::template ldp<I>(PFLBM_LD(base, src, 9LL * plane));
-    }
-    if (!CHECK)
-        return T::template ldp<I>(PFLBM_LD(base, I * plane + (gy - Y) * pitch + wrap1(gx - X, nx), 9LL * plane));
-    // one load from the selected source, no branch (a warp whose lanes pick
-    // different sources still issues one load); I and O share a storage unit
-    static_assert(T::template unit<I>() == T::template unit<O>(), "opposite directions share a unit");
-    int src = O * plane + gy * pitch + gx;
-    if (zeta_of(s_cls[sy + Y][sx + X])) src = O * plane + (gy + Y) * pitch + wrap1(gx + X, nx);
-    if (zeta_of(s_cls[sy - Y][sx - X])) src = I * plane + (gy - Y) * pitch + wrap1(gx - X, nx);
-    return T::template ldp<I>(PFLBM_LD(base, src, 9LL * plane));
-}
-
-template <int PREC, bool CHECK, bool WRAP>
-__device__ __forceinline__ void pull_f(typename Store<PREC>::C v[9], const typename Store<PREC>::S* __restrict__ f,
-                                       const uint8_t (*s_cls)[TX + 6], int sy, int sx, int gx, int gy, int nx,
-                                       int pitch, int plane)
-{
-    using T = Store<PREC>;
-    v[0] = T::template ldp<0>(PFLBM_LD(f, gy * pitch + gx, 9LL * plane));
-    v[1] = pull<1, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[2] = pull<2, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[3] = pull<3, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[4] = pull<4, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[5] = pull<5, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[6] = pull<6, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[7] = pull<7, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[8] = pull<8, PREC, CHECK, WRAP>(f, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-}
-
-// Pulled g at a node: g_0 raw (storage form) and its value, g_1..g_8.
-template <int PREC, bool CHECK, bool WRAP>
-__device__ __forceinline__ void pull_g(typename Store<PREC>::C v[9], typename Store<PREC>::G0T& raw0,
-                                       const Planes<PREC>& P, const uint8_t (*s_cls)[TX + 6], int sy, int sx,
-                                       int gx, int gy, int nx, int pitch, int plane)
-{
-    using T = Store<PREC>;
-    raw0 = PFLBM_LD(P.g0, gy * pitch + gx, plane);
-    v[0] = T::g0(raw0);
-    v[1] = pull<1, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[2] = pull<2, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[3] = pull<3, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[4] = pull<4, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[5] = pull<5, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[6] = pull<6, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[7] = pull<7, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    v[8] = pull<8, PREC, CHECK, WRAP>(P.g, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-}
-
-template <int PREC, bool CHECK, bool WRAP>
-__device__ __forceinline__ typename Store<PREC>::C pulled_phi(const Planes<PREC>& P, const uint8_t (*s_cls)[TX + 6],
-                                                              int sy, int sx, int gx, int gy, int nx, int pitch,
-                                                              int plane)
-{
-    typename Store<PREC>::C v[9];
-    typename Store<PREC>::G0T raw0;
-    pull_g<PREC, CHECK, WRAP>(v, raw0, P, s_cls, sy, sx, gx, gy, nx, pitch, plane);
-    return phi_of<PREC>(v);
-}
 
 // Prologue of a tile whose nodes within two of it are all fluid: no class
 // tile, no bounce-back checks, no ghosts, phi on a one-node ring.
@@ -201,7 +130,8 @@ __device__ __forceinline__ void ring_phi(const StepArgs<PREC>& a, const uint8_t 
 template <int PREC, bool WRAP>
 __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (*s_cls)[TX + 6],
                                               typename Store<PREC>::C (*s_phi)[TX + 4], int x0, int y0,
-                                              typename Store<PREC>::C gown[9], typename Store<PREC>::G0T& raw0)
+                                              typename Store<PREC>::C gown[9], typename Store<PREC>::G0T& raw0,
+                                              typename Store<PREC>::C fown[9])
 {
     using C = typename Store<PREC>::C;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -230,10 +160,15 @@ __device__ __forceinline__ void tile_prologue(const StepArgs<PREC>& a, uint8_t (
         int gx = wx(x0 + tx), gy = y0 + ty;
         C ph = C(0);
         if (gy < ny && zeta_of(own)) {
-            if (has_link(own))
+            if (has_link(own)) {
                 pull_g<PREC, true, WRAP>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
-            else
+                if (PFLBM_PREFETCH_F_WALL)
+                    pull_f<PREC, true, WRAP>(fown, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+            } else {
                 pull_g<PREC, false, WRAP>(gown, raw0, a.in, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+                if (PFLBM_PREFETCH_F_WALL)
+                    pull_f<PREC, false, WRAP>(fown, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, nx, pitch, a.plane);
+            }
             ph = phi_of<PREC>(gown);
         }
         s_phi[ty + 2][tx + 2] = ph;
@@ -271,14 +206,17 @@ __device__ __forceinline__ void step_tile_w(const StepArgs<PREC>& a, int bx, int
     if (fluid_tile)
         tile_prologue_fluid<PREC, WRAP>(a, s_phi, x0, y0, g, g0raw, f);
     else
-        tile_prologue<PREC, WRAP>(a, s_cls, s_phi, x0, y0, g, g0raw);
+        tile_prologue<PREC, WRAP>(a, s_cls, s_phi, x0, y0, g, g0raw, f);
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx >= a.nx || gy >= a.ny) return;
     const uint8_t code = fluid_tile ? (uint8_t)CLS_FLUID : s_cls[ty + 3][tx + 3];
     node_step<PREC, COLLIDE, VV, TX + 4>(a, code, s_phi, ty + 2, tx + 2, gx, gy, g, g0raw, [&](C fv[9]) {
-        if (!fluid_tile && has_link(code))
+        if (PFLBM_PREFETCH_F_WALL && !fluid_tile) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fv[i] = f[i];
+        } else if (!fluid_tile && has_link(code))
             pull_f<PREC, true, WRAP>(fv, a.in.f, s_cls, ty + 3, tx + 3, gx, gy, a.nx, a.pitch, a.plane);
         else if (PFLBM_PREFETCH_F && fluid_tile) {
 #pragma unroll
@@ -347,7 +285,7 @@ __global__ void __launch_bounds__(TX * TY, PREC == PFLBM_FP64 ? 1 : PFLBM_STEP_M
 // an item covers `group` tiles of one tile column, top to bottom. CTAs take
 // items w = blockIdx.x, blockIdx.x + gridDim.x, ...
 template <int PREC>
-__global__ void __launch_bounds__(TX * TY, PREC == PFLBM_FP64 ? 3 : 5) k_step_batch(const StepArgs<PREC>* __restrict__ args,
+__global__ void __launch_bounds__(TX * TY, PREC == PFLBM_FP64 ? 3 : PFLBM_BATCH_MINB) k_step_batch(const StepArgs<PREC>* __restrict__ args,
                                                         const int2* __restrict__ work, int n_work, int group)
 {
     __shared__ uint8_t s_cls[TY + 6][TX + 6];
@@ -641,6 +579,11 @@ cudaError_t launch_step(pflbm_t* h)
     cudaError_t e;
     if (h->tma && h->step_shape >= 0 && h->precision != PFLBM_FP64) {
         e = launch_step_staged(h, h->step_shape, h->step_chunk, 0);
+        if (e == cudaSuccess) h->cur ^= 1;
+        return e;
+    }
+    if (h->step_shape == -2 && h->precision != PFLBM_FP64) {
+        e = launch_step2(h);
         if (e == cudaSuccess) h->cur ^= 1;
         return e;
     }

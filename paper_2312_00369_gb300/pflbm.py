@@ -76,7 +76,7 @@ class Schedule(ctypes.Structure):
 
 
 # step kernels (pflbm_params_t.step_kernel)
-STEP_KERNELS = {"default": 0, "global": 1, "staged32x8": 2, "staged64x4": 3}
+STEP_KERNELS = {"default": 0, "global": 1, "staged32x8": 2, "staged64x4": 3, "pair": 4}
 
 
 class Wall(ctypes.Structure):

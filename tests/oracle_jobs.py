@@ -41,6 +41,8 @@ def case_by_name(name):
         c = wl.droplet_on_flat_wall(theta=55.0 if name == "flat_chi1" else 125.0, steps=700)
         c.meta = dict(chi_case=int(name[-1]))
         return c
+    if name == "odd_wide":            # odd width (the last node pair ends in the padding), fluid tiles inside
+        return wl.many_droplets_flat(nx=201, ny=96, n_drops=3, seed=5, r_lo=14.0, r_hi=20.0, steps=300)
     if name == "tiny":
         s = np.ones((6, 3), np.uint8)
         s[2:4] = 0

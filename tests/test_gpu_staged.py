@@ -1,9 +1,11 @@
-"""The staged step kernel (populations brought to shared memory by TMA, two
-tile shapes) against the global-load kernel: the arithmetic is shared, so the
-fields must agree bit for bit after any number of steps, for every storage
-precision that has the staged path, every geometry class (fluid-only tiles,
-walls, ghosts, bounce-back corners, lattices narrower than a tile, ragged
-edges) and in batches whose lattices run with different tile shapes.
+"""The other step kernels -- the staged kernel (populations brought to shared
+memory by TMA, two tile shapes) and the two-node kernel (two x-adjacent
+nodes per thread in packed FP32x2 arithmetic) -- against the global-load
+kernel: the arithmetic is shared, so the fields must agree bit for bit after
+any number of steps, for every storage precision that has these paths, every
+geometry class (fluid-only tiles, walls, ghosts, bounce-back corners,
+lattices narrower than a tile, ragged and odd widths) and in batches whose
+lattices run with different tile shapes.
 """
 import numpy as np
 import pytest
@@ -14,8 +16,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 CASES = ["flat60_short", "incline45_ragged", "block", "tiny", "cylinder", "crop", "flat_visc_force", "flat_chi1",
-         "incline_nodgdt"]
-KERNELS = [("staged32x8", 16), ("staged64x4", 16), ("staged32x8", 3), ("staged64x4", 1)]
+         "incline_nodgdt", "odd_wide"]
+KERNELS = [("staged32x8", 16), ("staged64x4", 16), ("staged32x8", 3), ("staged64x4", 1), ("pair", 0)]
 
 
 def _solver(case, precision, kernel, chunk=0):
