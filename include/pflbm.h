@@ -97,12 +97,13 @@ typedef struct {
      * term 0 times (case 1) or twice (case 3). */
     int chi_case;
     /* Step kernel (results are identical bit for bit; only the speed
-     * differs). 0: the library's default (1); 1: populations pulled from
-     * global memory, 32 x 8 tiles; 2: populations staged in shared memory
-     * by TMA, 32 x 8 tiles; 3: staged, 64 x 4 tiles; 4: global loads, two
-     * x-adjacent nodes per thread in packed FP32x2 arithmetic, 64 x 8
-     * tiles. FP64 handles always use 1. step_chunk: tiles a CTA of the
-     * staged kernel marches down one tile column per work item (<= 0: 16). */
+     * differs). 0: the library's default (4 for 16-bit storage, else 1);
+     * 1: populations pulled from global memory, 32 x 8 tiles; 2:
+     * populations staged in shared memory by TMA, 32 x 8 tiles; 3: staged,
+     * 64 x 4 tiles; 4: global loads, two x-adjacent nodes per thread in
+     * packed FP32x2 arithmetic, 64 x 8 tiles. FP64 handles always use 1.
+     * step_chunk: tiles a CTA of the staged kernel marches down one tile
+     * column per work item (<= 0: 16). */
     int step_kernel;
     int step_chunk;
 } pflbm_params_t;
@@ -254,9 +255,12 @@ typedef struct {
     int order;           /* 0: lattice by lattice; 1: largest lattices first,
                             items interleaved across lattices                 */
     int use_graph;       /* replay step pairs from a captured CUDA graph      */
-    int kernel;          /* 0 or 1: global-load kernel, 32 x 8 tiles; 2:
-                            staged kernel (TMA ring) with the size classes
-                            below. FP64 batches always use 1.                */
+    int kernel;          /* 0: default (3 for 16-bit storage, else 1); 1:
+                            global-load kernel, 32 x 8 tiles; 2: staged
+                            kernel (TMA ring) with the size classes below;
+                            3: two-node kernel (two x-adjacent nodes per
+                            thread in packed FP32x2 arithmetic), 64 x 8
+                            tiles. FP64 batches always use 1.                */
     /* Staged kernel, per size class: a lattice with nx * ny <=
      * class_max_nodes[k] (first such k < n_classes) runs with tile shape
      * class_shape[k] (0: 32 x 8, 1: 64 x 4) and class_tiles[k] tiles per
@@ -283,7 +287,7 @@ int pflbm_batch_set(pflbm_batch_t* b, pflbm_t* const* hs, int count);
  * in between are picked up (descriptors are rewritten). ENUMERIC if a member
  * reported a NaN or |u| >= 0.3 earlier. */
 int pflbm_batch_step(pflbm_batch_t* b, int64_t n);
-/* The step kernel the batch runs (1 global loads, 2 staged). */
+/* The step kernel the batch runs (1 global loads, 2 staged, 3 two-node). */
 int pflbm_batch_kernel(const pflbm_batch_t* b);
 /* Work items, persistent grid size and total nodes of the batch. */
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes);

@@ -33,6 +33,7 @@ struct pflbm_batch {
     int cap_lattices = 0, cap_work = 0;
     void* d_args[2] = {nullptr, nullptr};
     bool staged = false;          // staged (TMA ring) kernel, int4 items; else int2 items
+    bool pair = false;            // two-node kernel: int2 items of 64 x 8 tiles
     void* d_work = nullptr;
     int n_work = 0;
     int grid = 0;
@@ -101,13 +102,14 @@ std::vector<I> order_items(std::vector<std::vector<I>>& per, int order)
     return w;
 }
 
-// Global-load kernel: (lattice, first tile) items of tiles_per_item tiles.
-std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s)
+// Global-load and two-node kernels: (lattice, first tile) items of
+// tiles_per_item tiles of one tile column; tiles of tw x 8 nodes.
+std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s, int tw)
 {
     const int G = std::max(1, s.tiles_per_item);
     std::vector<std::vector<int2>> per(hs.size());
     for (size_t i = 0; i < hs.size(); ++i) {
-        int ntx = tiles_x(hs[i]->nx), nty = tiles_y(hs[i]->ny);
+        int ntx = (hs[i]->nx + tw - 1) / tw, nty = tiles_y(hs[i]->ny);
         for (int by = 0; by < nty; by += G)
             for (int bx = 0; bx < ntx; ++bx) per[i].push_back(make_int2((int)i, by * ntx + bx));
     }
@@ -154,6 +156,10 @@ int upload(pflbm_batch_t* b)
     b->staged = b->precision != PFLBM_FP64 && b->sched.kernel == 2;
     for (pflbm_t* h : b->hs)
         if (!h->tma) b->staged = false;
+    // the default kernel is the two-node one for 16-bit storage (measured
+    // fastest on mixes of small lattices), the global-load one otherwise
+    const bool sixteen = b->precision == PFLBM_BF16 || b->precision == PFLBM_FP16;
+    b->pair = b->precision != PFLBM_FP64 && (b->sched.kernel == 3 || (b->sched.kernel == 0 && sixteen));
     std::vector<unsigned char> wbytes;
     size_t item = b->staged ? sizeof(int4) : sizeof(int2);
     if (b->staged) {
@@ -161,7 +167,7 @@ int upload(pflbm_batch_t* b)
         wbytes.resize(w4.size() * item);
         if (!w4.empty()) std::memcpy(wbytes.data(), w4.data(), wbytes.size());
     } else {
-        std::vector<int2> w2 = build_work(b->hs, b->sched);
+        std::vector<int2> w2 = build_work(b->hs, b->sched, b->pair ? 64 : TX);
         wbytes.resize(w2.size() * item);
         if (!w2.empty()) std::memcpy(wbytes.data(), w2.data(), wbytes.size());
     }
@@ -197,7 +203,8 @@ int upload(pflbm_batch_t* b)
     drop_graph(b);   // kernel, work list or grid may differ from the captured ones
     b->n_work = n_items;
     b->phase = 0;
-    int per_sm = b->staged ? staged_batch_ctas_per_sm(b->precision) : batch_max_ctas_per_sm(b->precision);
+    int per_sm = b->staged ? staged_batch_ctas_per_sm(b->precision)
+                           : (b->pair ? step2_batch_ctas_per_sm(b->precision) : batch_max_ctas_per_sm(b->precision));
     if (b->sched.ctas_per_sm > 0) per_sm = std::min(per_sm, b->sched.ctas_per_sm);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -222,6 +229,9 @@ cudaError_t launch_set(pflbm_batch_t* b, int set)
     if (b->staged)
         return launch_step_staged_batch(b->precision, b->d_args[set], (const int4*)b->d_work, b->n_work, b->grid,
                                         b->stream);
+    if (b->pair)
+        return launch_step2_batch(b->precision, b->d_args[set], (const int2*)b->d_work, b->n_work,
+                                  std::max(1, b->sched.tiles_per_item), b->grid, b->stream);
     return launch_step_batch(b->precision, b->d_args[set], (const int2*)b->d_work, b->n_work,
                              std::max(1, b->sched.tiles_per_item), b->grid, b->stream);
 }
@@ -355,7 +365,7 @@ int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
 int pflbm_batch_kernel(const pflbm_batch_t* b)
 {
     if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
-    return b->staged ? 2 : 1;
+    return b->staged ? 2 : (b->pair ? 3 : 1);
 }
 
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes)

@@ -207,7 +207,9 @@ int ensure_out(pflbm_t* h)
 int select_step_kernel(pflbm_t* h, int kernel, int chunk)
 {
     if (kernel < 0 || kernel > 4) return fail(PFLBM_EINVAL, "step_kernel must be 0, 1, 2, 3 or 4");
-    if (kernel == 0) kernel = 1;
+    // default: the two-node kernel for 16-bit storage (the fastest there),
+    // the one-node global-load kernel for FP32 and FP64
+    if (kernel == 0) kernel = (h->precision == PFLBM_BF16 || h->precision == PFLBM_FP16) ? 4 : 1;
     if (kernel == 4) {
         if (h->precision == PFLBM_FP64) return fail(PFLBM_EINVAL, "the two-node step kernel needs FP32 or 16-bit storage");
         h->step_shape = -2;

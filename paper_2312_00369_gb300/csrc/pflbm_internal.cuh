@@ -197,6 +197,10 @@ cudaError_t launch_init_populations(pflbm_t* h);
 cudaError_t launch_step(pflbm_t* h);
 // step2.cu: two x-adjacent nodes per thread in packed FP32x2 (FP32, 16-bit)
 cudaError_t launch_step2(pflbm_t* h);
+// two-node kernel over many lattices: (lattice, first 64 x 8 tile) items
+cudaError_t launch_step2_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,
+                               int grid, cudaStream_t stream);
+int step2_batch_ctas_per_sm(int precision);
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p);
 cudaError_t launch_macro_f32(pflbm_t* h, float* phi, float* u, float* p);   // rounded to nearest
 size_t step_args_bytes(int precision);

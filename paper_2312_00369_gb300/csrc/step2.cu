@@ -14,6 +14,8 @@
 // an x component are one aligned load for both nodes.
 #include "step_core.cuh"
 
+#include <type_traits>
+
 namespace pfk {
 namespace {
 
@@ -24,9 +26,20 @@ constexpr int QPW = QX + 4;           // phi tile row (halo 2)
 
 // L2 prefetch distance in CTAs of launch order (0: off): a quarter of the
 // 3 x 152 resident CTAs, the same node distance as the one-node kernel's
-// resident 256-thread CTAs per SM asked of k_step2
+// single-lattice kernel, fluid tiles: pull f with g, before the phi-tile
+// barrier (twice the loads in flight per thread, for 9 more registers;
+// measured faster there, slower in the batched kernel, which spills)
+#ifndef PFLBM_PAIR_EARLY_F
+#define PFLBM_PAIR_EARLY_F 1
+#endif
+
+// resident 256-thread CTAs per SM asked of k_step2: 4 with 16-bit storage
+// (64 registers, the pulled populations held as raw pairs), 3 with FP32
 #ifndef PFLBM_STEP2_MINB
-#define PFLBM_STEP2_MINB 3
+#define PFLBM_STEP2_MINB 4
+#endif
+#ifndef PFLBM_STEP2_MINB32
+#define PFLBM_STEP2_MINB32 3
 #endif
 #ifndef PFLBM_L2_AHEAD2
 #define PFLBM_L2_AHEAD2 114
@@ -67,27 +80,58 @@ __device__ __forceinline__ F2 pull2(const typename Store<PREC>::S* __restrict__ 
     }
 }
 
-template <int PREC, bool WRAP>
-__device__ __forceinline__ void pull2_f(F2 v[9], const typename Store<PREC>::S* __restrict__ f, int gx, int gy, int nx,
-                                        int pitch, int plane)
+// The same for 16-bit storage, as the raw pair (lane x in the low half):
+// the aligned word itself for directions without an x component away from
+// the seam, else two 16-bit loads joined.
+template <int I, int PREC, bool WRAP>
+__device__ __forceinline__ uint32_t pull2_raw(const typename Store<PREC>::S* __restrict__ base, int gx, int gy, int nx,
+                                              int pitch, int plane)
 {
-    v[0] = pull2<0, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[1] = pull2<1, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[2] = pull2<2, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[3] = pull2<3, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[4] = pull2<4, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[5] = pull2<5, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[6] = pull2<6, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[7] = pull2<7, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
-    v[8] = pull2<8, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    static_assert(PREC != PFLBM_FP32, "16-bit storage");
+    constexpr int X = cx(I), Y = cy(I);
+    const uint16_t* b = reinterpret_cast<const uint16_t*>(base);
+    if constexpr (!WRAP) {
+        const int idx = gy * pitch + gx + (I * plane - Y * pitch - X);
+        if constexpr (X == 0)
+            return PFLBM_LD(reinterpret_cast<const uint32_t*>(base), idx / 2, 9LL * plane / 2);
+        else
+            return (uint32_t)PFLBM_LD(b, idx, 9LL * plane) | ((uint32_t)PFLBM_LD(b, idx + 1, 9LL * plane) << 16);
+    } else {
+        const int r = (gy - Y) * pitch + I * plane;
+        return (uint32_t)PFLBM_LD(b, r + wrap1(gx - X, nx), 9LL * plane) |
+               ((uint32_t)PFLBM_LD(b, r + wrap1(gx + 1 - X, nx), 9LL * plane) << 16);
+    }
+}
+
+
+template <int I, int PREC, bool WRAP>
+__device__ __forceinline__ typename Hold2<PREC>::W pull2_w(const typename Store<PREC>::S* __restrict__ base, int gx,
+                                                        int gy, int nx, int pitch, int plane)
+{
+    if constexpr (Hold2<PREC>::kRaw) return pull2_raw<I, PREC, WRAP>(base, gx, gy, nx, pitch, plane);
+    else return pull2<I, PREC, WRAP>(base, gx, gy, nx, pitch, plane);
+}
+
+template <int PREC, bool WRAP>
+__device__ __forceinline__ void pull2_f(Hold2<PREC>& v, const typename Store<PREC>::S* __restrict__ f, int gx, int gy,
+                                        int nx, int pitch, int plane)
+{
+    v.w[0] = pull2_w<0, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[1] = pull2_w<1, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[2] = pull2_w<2, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[3] = pull2_w<3, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[4] = pull2_w<4, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[5] = pull2_w<5, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[6] = pull2_w<6, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[7] = pull2_w<7, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
+    v.w[8] = pull2_w<8, PREC, WRAP>(f, gx, gy, nx, pitch, plane);
 }
 
 // g of the two nodes (no bounce-back) and their raw g_0 (an aligned pair).
 template <int PREC, bool WRAP>
-__device__ __forceinline__ void pull2_g(F2 v[9], int32_t raw[2], const Planes<PREC>& P, int gx, int gy, int nx,
+__device__ __forceinline__ void pull2_g(Hold2<PREC>& v, int32_t raw[2], const Planes<PREC>& P, int gx, int gy, int nx,
                                         int pitch, int plane)
 {
-    using T = Store<PREC>;
     if constexpr (!WRAP) {
         const int2 r = PFLBM_LD(reinterpret_cast<const int2*>(P.g0), (gy * pitch + gx) / 2, plane / 2);
         raw[0] = r.x;
@@ -96,20 +140,19 @@ __device__ __forceinline__ void pull2_g(F2 v[9], int32_t raw[2], const Planes<PR
         raw[0] = PFLBM_LD(P.g0, gy * pitch + wrap1(gx, nx), plane);
         raw[1] = PFLBM_LD(P.g0, gy * pitch + wrap1(gx + 1, nx), plane);
     }
-    v[0] = F2(T::g0(raw[0]), T::g0(raw[1]));
-    v[1] = pull2<1, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
-    v[2] = pull2<2, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
-    v[3] = pull2<3, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
-    v[4] = pull2<4, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
-    v[5] = pull2<5, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
-    v[6] = pull2<6, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
-    v[7] = pull2<7, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
-    v[8] = pull2<8, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[1] = pull2_w<1, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[2] = pull2_w<2, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[3] = pull2_w<3, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[4] = pull2_w<4, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[5] = pull2_w<5, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[6] = pull2_w<6, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[7] = pull2_w<7, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
+    v.w[8] = pull2_w<8, PREC, WRAP>(P.g, gx, gy, nx, pitch, plane);
 }
 
 // phi = sum_i g_i (Eq. order-parameter) of both lanes, in the scalar order.
 template <int PREC>
-__device__ __forceinline__ F2 phi2(const F2 v[9])
+__device__ __forceinline__ F2 phi2(const Hold2<PREC>& v, const int32_t raw[2])
 {
     using T = Store<PREC>;
     F2 s;
@@ -118,7 +161,7 @@ __device__ __forceinline__ F2 phi2(const F2 v[9])
                   F2(T::template unit<5>()) * ((v[5] + v[6]) + (v[7] + v[8])));
     else
         s = ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
-    return v[0] + s;
+    return F2(T::g0(raw[0]), T::g0(raw[1])) + s;
 }
 
 // Ring positions (width H) around the 64 x 8 tile: phi of one node each.
@@ -164,7 +207,7 @@ __device__ __forceinline__ float own_g(float v[9], int32_t& raw, const StepArgs<
     return phi_of<PREC>(v);
 }
 
-template <int PREC, int VV, bool WRAP>
+template <int PREC, int VV, bool WRAP, bool EARLY_F>
 __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, uint8_t (*s_cls)[QCW],
                                       float (*s_phi)[QPW])
 {
@@ -178,14 +221,16 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, u
     const bool fluid = a.tiles[by * ntx + 2 * bx] != 0 && (2 * bx + 1 >= ntx || a.tiles[by * ntx + 2 * bx + 1] != 0);
     const bool tiny = nx < QX + 8;
     const int gxa = x0 + 2 * tx, gy = y0 + ty;
-    F2 g[9];
+    Hold2<PREC> g;
     int32_t raw[2] = {0, 0};
     uint8_t code[2] = {CLS_FLUID, CLS_FLUID};
 
+    Hold2<PREC> fearly;
     if (fluid) {
         // ---- prologue of an all-fluid tile: no class tile, no checks ----
         pull2_g<PREC, WRAP>(g, raw, a.in, gxa, gy, nx, pitch, a.plane);
-        const F2 ph = phi2<PREC>(g);
+        if (EARLY_F) pull2_f<PREC, WRAP>(fearly, a.in.f, gxa, gy, nx, pitch, a.plane);
+        const F2 ph = phi2<PREC>(g, raw);
         s_phi[ty + 2][2 * tx + 2] = ph.x;
         s_phi[ty + 2][2 * tx + 3] = ph.y;
         ring2<PREC, 1, WRAP, true>(a, s_cls, s_phi, x0, y0, tid, tiny);
@@ -217,7 +262,7 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, u
         if (gy < ny && zeta_of(code[1]))
             phb = own_g<PREC, WRAP>(gb, raw[1], a, s_cls, ty + 3, 2 * tx + 4, wx(gxa + 1), gy, code[1]);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = F2(ga[i], gb[i]);
+        for (int i = 1; i < 9; ++i) g.set(i, F2(ga[i], gb[i]));
         s_phi[ty + 2][2 * tx + 2] = pha;
         s_phi[ty + 2][2 * tx + 3] = phb;
         if (halo == 1) ring2<PREC, 1, WRAP, false>(a, s_cls, s_phi, x0, y0, tid, tiny);
@@ -243,16 +288,26 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, u
     lane.k = gy * pitch + gxa;
     lane.g0raw[0] = raw[0];
     lane.g0raw[1] = raw[1];
+    // the 4 x 3 phi values around the pair, as three aligned float2 per row
+    // (64-bit shared loads: no bank conflicts): W = (l.y, m.x), C = m, E = (m.y, r.x)
     const int py = ty + 2, px = 2 * tx + 2;
-    auto at = [&](int dy, int dx) { return F2(s_phi[py + dy][px + dx], s_phi[py + dy][px + dx + 1]); };
+    F2 Wr[3], Cr[3], Er[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float2* row = reinterpret_cast<const float2*>(&s_phi[py - 1 + r][0]);
+        const float2 l = row[px / 2 - 1], m = row[px / 2], rr = row[px / 2 + 1];
+        Wr[r] = F2(l.y, m.x);
+        Cr[r] = F2(m.x, m.y);
+        Er[r] = F2(m.y, rr.x);
+    }
     F2 gpx, gpy, lap;
-    stencil9<F2>(at(0, 0), at(0, 1), at(0, -1), at(1, 0), at(-1, 0), at(1, 1), at(1, -1), at(-1, -1), at(-1, 1), gpx,
-                 gpy, lap);
+    stencil9<F2>(Cr[1], Er[1], Wr[1], Cr[2], Cr[0], Er[2], Wr[2], Wr[0], Er[0], gpx, gpy, lap);
     node_core<PREC, true, VV>(
-        a, lane, at(0, 0), gpx, gpy, lap, g,
-        [&](F2 fv[9]) {
+        a, lane, Cr[1], gpx, gpy, lap, g,
+        [&](Hold2<PREC>& fv) {
             if (fluid) {
-                pull2_f<PREC, WRAP>(fv, a.in.f, gxa, gy, nx, pitch, a.plane);
+                if (EARLY_F) fv = fearly;
+                else pull2_f<PREC, WRAP>(fv, a.in.f, gxa, gy, nx, pitch, a.plane);
                 return;
             }
             float fa[9], fb[9];
@@ -269,7 +324,7 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, u
             one(fa, 0, gxa);
             one(fb, 1, gxa + 1);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) fv[i] = F2(fa[i], fb[i]);
+            for (int i = 0; i < 9; ++i) fv.set(i, F2(fa[i], fb[i]));
         },
         [&](int k) {
             const float2 v = PFLBM_LD(reinterpret_cast<const float2*>(a.sprev), k / 2, a.plane / 2);
@@ -324,17 +379,51 @@ __device__ __forceinline__ void prefetch2_l2(const StepArgs<PREC>& a, int bx, in
 }
 
 template <int PREC, int VV>
-__global__ void __launch_bounds__(QTX * QY, PFLBM_STEP2_MINB) k_step2(const __grid_constant__ StepArgs<PREC> a)
+__global__ void __launch_bounds__(QTX * QY, PREC == PFLBM_FP32 ? PFLBM_STEP2_MINB32 : PFLBM_STEP2_MINB) k_step2(const __grid_constant__ StepArgs<PREC> a)
 {
     __shared__ uint8_t s_cls[QY + 6][QCW];
-    __shared__ float s_phi[QY + 4][QPW];
+    __shared__ __align__(16) float s_phi[QY + 4][QPW];
     if (PFLBM_L2_AHEAD2 > 0) prefetch2_l2<PREC>(a, blockIdx.x, blockIdx.y);
     const int x0 = blockIdx.x * QX;
     // every x the tile touches (class tile: three out) inside the lattice
     if (x0 >= 3 && x0 + QX + 3 <= a.nx)
-        tile2<PREC, VV, false>(a, blockIdx.x, blockIdx.y, s_cls, s_phi);
+        tile2<PREC, VV, false, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_cls, s_phi);
     else
-        tile2<PREC, VV, true>(a, blockIdx.x, blockIdx.y, s_cls, s_phi);
+        tile2<PREC, VV, true, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_cls, s_phi);
+}
+
+// Persistent two-node step over many lattices: work item w = (lattice,
+// first 64 x 8 tile); an item covers `group` tiles of one tile column, top to
+// bottom. CTAs take items w = blockIdx.x, blockIdx.x + gridDim.x, ... The
+// item's lattice descriptor is copied to shared memory and read from there.
+template <int PREC>
+__global__ void __launch_bounds__(QTX * QY, PREC == PFLBM_FP32 ? PFLBM_STEP2_MINB32 : PFLBM_STEP2_MINB)
+    k_step2_batch(const StepArgs<PREC>* __restrict__ args, const int2* __restrict__ work, int n_work, int group)
+{
+    __shared__ uint8_t s_cls[QY + 6][QCW];
+    __shared__ __align__(16) float s_phi[QY + 4][QPW];
+    __shared__ __align__(16) unsigned char s_args_raw[sizeof(StepArgs<PREC>)];
+    const StepArgs<PREC>& a = *reinterpret_cast<const StepArgs<PREC>*>(s_args_raw);
+    const int tid = threadIdx.y * QTX + threadIdx.x;
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const int2 it = work[w];
+        {
+            const int* src = reinterpret_cast<const int*>(args + it.x);
+            int* dst = reinterpret_cast<int*>(s_args_raw);
+            for (int i = tid; i < (int)(sizeof(StepArgs<PREC>) / sizeof(int)); i += QTX * QY) dst[i] = src[i];
+        }
+        __syncthreads();
+        const int ntx = (a.nx + QX - 1) / QX, nty = (a.ny + QY - 1) / QY;
+        const int bx = it.y % ntx, by0 = it.y / ntx;
+        for (int gi = 0; gi < group && by0 + gi < nty; ++gi) {
+            const int x0 = bx * QX;
+            if (x0 >= 3 && x0 + QX + 3 <= a.nx)
+                tile2<PREC, 2, false, false>(a, bx, by0 + gi, s_cls, s_phi);
+            else
+                tile2<PREC, 2, true, false>(a, bx, by0 + gi, s_cls, s_phi);
+            __syncthreads();   // the next tile reuses the shared tiles and descriptor
+        }
+    }
 }
 
 template <int PREC>
@@ -353,6 +442,38 @@ cudaError_t run2(pflbm_t* h)
 }
 
 }  // namespace
+
+cudaError_t launch_step2_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,
+                               int grid, cudaStream_t stream)
+{
+    dim3 b(QTX, QY);
+    switch (precision) {
+        case PFLBM_FP32:
+            k_step2_batch<PFLBM_FP32><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_FP32>*)d_args, d_work, n_work, group);
+            break;
+        case PFLBM_BF16:
+            k_step2_batch<PFLBM_BF16><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_BF16>*)d_args, d_work, n_work, group);
+            break;
+        case PFLBM_FP16:
+            k_step2_batch<PFLBM_FP16><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_FP16>*)d_args, d_work, n_work, group);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int step2_batch_ctas_per_sm(int precision)
+{
+    int n = 0;
+    cudaError_t e;
+    switch (precision) {
+        case PFLBM_FP32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_batch<PFLBM_FP32>, QTX * QY, 0); break;
+        case PFLBM_BF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_batch<PFLBM_BF16>, QTX * QY, 0); break;
+        case PFLBM_FP16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_batch<PFLBM_FP16>, QTX * QY, 0); break;
+        default: return 1;
+    }
+    return e == cudaSuccess ? n : 1;
+}
 
 cudaError_t launch_step2(pflbm_t* h)
 {

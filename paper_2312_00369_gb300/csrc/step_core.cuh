@@ -8,6 +8,8 @@
 
 #include "storage.cuh"
 
+#include <type_traits>
+
 namespace pfk {
 
 // Index-checked debug build (-DPFLBM_BOUNDS): every global and staged
@@ -301,6 +303,7 @@ template <int PREC>
 struct Lane1 {
     using T = Store<PREC>;
     using C = typename T::C;
+    using FArr = C[9];
     uint8_t code;
     int k;
     typename T::G0T g0raw;
@@ -336,6 +339,42 @@ struct Lane1 {
     }
 };
 
+// Pulled populations of two x-adjacent nodes as they are held through the
+// step: F2 values (FP32 storage), or the raw 16-bit pairs (lane x in the
+// low half), converted where used, which keeps them in half the registers.
+template <int PREC>
+struct Hold2 {
+    static constexpr bool kRaw = PREC != PFLBM_FP32;
+    using W = typename std::conditional<kRaw, uint32_t, F2>::type;
+    W w[9];
+    __device__ static __forceinline__ uint32_t pack_raw(F2 v)
+    {
+        if constexpr (PREC == PFLBM_BF16) {
+            __nv_bfloat162 h = __float22bfloat162_rn(f2v(v));
+            return *reinterpret_cast<uint32_t*>(&h);
+        } else {
+            __half2 h = __float22half2_rn(f2v(v));
+            return *reinterpret_cast<uint32_t*>(&h);
+        }
+    }
+    __device__ static __forceinline__ F2 unpack_raw(uint32_t u)
+    {
+        if constexpr (PREC == PFLBM_BF16) return v2f(__bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u)));
+        else return v2f(__half22float2(*reinterpret_cast<__half2*>(&u)));
+    }
+    __device__ __forceinline__ F2 operator[](int i) const
+    {
+        if constexpr (kRaw) return unpack_raw(w[i]);
+        else return w[i];
+    }
+    // both lanes' values in work units (a 16-bit round trip is exact)
+    __device__ __forceinline__ void set(int i, F2 v)
+    {
+        if constexpr (kRaw) w[i] = pack_raw(v);
+        else w[i] = v;
+    }
+};
+
 // Two x-adjacent nodes per thread: lane x at the even index k, lane y at
 // k + 1. valid[j]: lane j is a zeta = 1 node of the lattice (stores of an
 // invalid lane write values no pull reads: a zeta = 0 node, or the padding
@@ -358,21 +397,9 @@ struct Lane2 {
     {
         if ((valid[0] && !(uu.x < 0.09f)) || (valid[1] && !(uu.y < 0.09f))) atomicOr(a.status, 1);
     }
-    __device__ __forceinline__ uint32_t pack(F2 v) const
-    {
-        if constexpr (PREC == PFLBM_BF16) {
-            __nv_bfloat162 h = __float22bfloat162_rn(f2v(v));
-            return *reinterpret_cast<uint32_t*>(&h);
-        } else {
-            __half2 h = __float22half2_rn(f2v(v));
-            return *reinterpret_cast<uint32_t*>(&h);
-        }
-    }
-    __device__ __forceinline__ F2 unpack(uint32_t u) const
-    {
-        if constexpr (PREC == PFLBM_BF16) return v2f(__bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u)));
-        else return v2f(__half22float2(*reinterpret_cast<__half2*>(&u)));
-    }
+    using FArr = Hold2<PREC>;
+    __device__ __forceinline__ uint32_t pack(F2 v) const { return Hold2<PREC>::pack_raw(v); }
+    __device__ __forceinline__ F2 unpack(uint32_t u) const { return Hold2<PREC>::unpack_raw(u); }
     template <int I>
     __device__ __forceinline__ void store_f(const StepArgs<PREC>& a, C v) const
     {
@@ -473,22 +500,22 @@ __device__ __forceinline__ typename L::C collide_g_dir(const StepArgs<PREC>& a, 
 
 // The time step of one node (or two, in packed lanes) once its g has been
 // pulled and the phi stencils are taken: chemical potential, coupling
-// fields, moments, both collisions and the stores. pull_f(f) fills the
+// fields, moments, both collisions and the stores. g[i] (i = 1..8) gives the
+// pulled g_i in the lane type (an array, or a Hold2). pull_f(f) fills the
 // pulled f (called where the moments need it) and sprev(k) the u.grad(phi)
 // history of the previous step (called only with the (1/2) dG/dt term). With
 // COLLIDE = false (one lane only) readback(phi, ux, uy, p) receives the
 // macroscopic fields instead. VV: 0 uniform tau_f, 1 variable viscosity,
 // 2 decided by a.varvisc.
-template <int PREC, bool COLLIDE, int VV, typename L, typename PullF, typename SprevF, typename ReadF>
+template <int PREC, bool COLLIDE, int VV, typename L, typename GA, typename PullF, typename SprevF, typename ReadF>
 __device__ __forceinline__ void node_core(const StepArgs<PREC>& a, const L& lane, typename L::C ph,
                                           typename L::C gpx, typename L::C gpy, typename L::C lap,
-                                          const typename L::C g[9], PullF&& pull_f, SprevF&& sprev,
-                                          ReadF&& readback)
+                                          const GA& g, PullF&& pull_f, SprevF&& sprev, ReadF&& readback)
 {
     using T = Store<PREC>;
     using C = typename L::C;
     using R = typename T::C;   // the scalar arithmetic type
-    C f[9];
+    typename L::FArr f;
 
     // ---- chemical potential (Eq. chemical_potencial2) ----
     const C wet = lane.wet(a);

@@ -483,7 +483,7 @@ class Batch:
 
     @property
     def kernel(self):
-        """1: global-load kernel, 2: staged kernel."""
+        """1: global-load kernel, 2: staged kernel, 3: two-node kernel."""
         return lib().pflbm_batch_kernel(self._b)
 
     def info(self):

@@ -130,15 +130,15 @@ def test_autotune_picks_a_measured_schedule(tmp_path, monkeypatch):
 
 
 def test_autotune_tunes_staged_size_classes(tmp_path, monkeypatch):
-    # the default search: the global-load kernel's grid, then the staged
-    # kernel's shape and item length per size class; the chosen schedule
-    # steps every member exactly as it steps alone
+    # the default search: the global-load and two-node kernels' grids, then
+    # the staged kernel's shape and item length per size class; the chosen
+    # schedule steps every member exactly as it steps alone
     from paper_2312_00369_gb300 import autotune
     from paper_2312_00369_gb300.pflbm import Batch
     monkeypatch.setenv("PFLBM_TUNE_CACHE", str(tmp_path / "sched.json"))
     cases = mix(seed=3, n=6)
     best, timings = autotune.tune(cases, "bf16", steps=3, warmup=1)
-    assert any(k.startswith("global_") for k in timings) and any(k.startswith("staged[") for k in timings)
+    assert all(any(k.startswith(p) for k in timings) for p in ("global_", "pair_", "staged["))
     assert timings[autotune.name_of(best)] == min(timings.values())
     stream = torch.cuda.Stream()
     alone = make(cases, "bf16", stream)

@@ -109,3 +109,35 @@ def test_staged_batch_with_mixed_shapes_equals_single(precision):
     b.close()
     for s in members:
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("tiles_per_item", [1, 3])
+def test_pair_batch_equals_single(precision, tiles_per_item):
+    # the two-node kernel over a mix of lattice sizes and wall types (flat,
+    # inclined, cylinder) in one persistent launch: each member equals its
+    # own single-lattice run with the global-load kernel
+    from paper_2312_00369_gb300 import pflbm, workloads as wl
+    cases = wl.batched_instances(count=12, seed=11)
+    stream = torch.cuda.Stream()
+    members = []
+    for c in cases:
+        s = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision=precision, stream=stream, **c.physical())
+        for d in c.droplets:
+            s.init_droplet(*d)
+        members.append(s)
+    b = pflbm.Batch(members, pflbm.schedule(tiles_per_item=tiles_per_item, kernel=3))
+    assert b.kernel == 3
+    b.step(23)
+    for c, s in zip(cases, members):
+        r = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision=precision, step_kernel="global",
+                         **c.physical())
+        for d in c.droplets:
+            r.init_droplet(*d)
+        r.step(23)
+        for x, y in zip(_state(r), _state(s)):
+            assert np.array_equal(x, y), (c.nx, c.ny)
+        r.close()
+    b.close()
+    for s in members:
+        s.close()
