@@ -62,7 +62,7 @@ def whole_job_mlups(world, nodes, steps, seconds):
     return world * nodes * steps / seconds / 1e6
 
 
-def step_source_sha256(files=("step.cu", "step_core.cuh", "storage.cuh", "pflbm_internal.cuh")):
+def step_source_sha256(files=("step.cu", "step2.cu", "step_core.cuh", "storage.cuh", "pflbm_internal.cuh")):
     import hashlib
     h = hashlib.sha256()
     for f in files:

@@ -260,7 +260,8 @@ typedef struct {
                             kernel (TMA ring) with the size classes below;
                             3: two-node kernel (two x-adjacent nodes per
                             thread in packed FP32x2 arithmetic), 64 x 8
-                            tiles. FP64 batches always use 1.                */
+                            tiles, all-fluid tiles and tiles with walls in
+                            two launches. FP64 batches always use 1.        */
     /* Staged kernel, per size class: a lattice with nx * ny <=
      * class_max_nodes[k] (first such k < n_classes) runs with tile shape
      * class_shape[k] (0: 32 x 8, 1: 64 x 4) and class_tiles[k] tiles per

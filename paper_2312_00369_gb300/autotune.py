@@ -5,7 +5,8 @@ The batched step has three kernels and several knobs (``pflbm_schedule_t``):
 * the global-load kernel (32 x 8 tiles): persistent CTAs per SM, tiles of one
   tile column per work item, item order;
 * the two-node kernel (64 x 8 tiles, two x-adjacent nodes per thread in
-  packed FP32x2 arithmetic): tiles per work item, item order;
+  packed FP32x2 arithmetic; all-fluid tiles and tiles with walls in two
+  launches): tiles per work item, item order;
 * the staged kernel (TMA ring): per size class of the mix, the tile shape
   (32 x 8 or 64 x 4) and the tiles a CTA marches down per work item.
 

@@ -3,9 +3,13 @@
 //
 // A batch holds, in device memory, one step descriptor per lattice for each
 // parity of the ping-pong state (set 0: in = current copy, out = the other;
-// set 1: swapped) and a work list of (lattice, first tile) items. Each step
-// is one launch of k_step_batch over the work list; with use_graph the pair
-// of launches (set p, set 1 - p) is captured once in a CUDA graph and replayed.
+// set 1: swapped) and a work list. Each step is one launch over the work
+// list: k_step_batch over (lattice, first tile) items; or the staged kernel;
+// or (the default for 16-bit storage) two launches of the two-node kernel,
+// one over the items of all-fluid 64 x 8 tiles and one over the items of
+// tiles with walls, each compiled for its own path. With use_graph the
+// launches of two steps (set p, set 1 - p) are captured once in a CUDA graph
+// and replayed.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -33,7 +37,9 @@ struct pflbm_batch {
     int cap_lattices = 0, cap_work = 0;
     void* d_args[2] = {nullptr, nullptr};
     bool staged = false;          // staged (TMA ring) kernel, int4 items; else int2 items
-    bool pair = false;            // two-node kernel: int2 items of 64 x 8 tiles
+    bool split = false;           // two-node kernels split by tile kind: int4 items, fluid first
+    int n_fluid = 0;              // split: items of all-fluid tiles (the rest have walls)
+    int grid_w = 0;               // split: grid of the wall-tile kernel (grid: the fluid one's)
     void* d_work = nullptr;
     int n_work = 0;
     int grid = 0;
@@ -102,18 +108,65 @@ std::vector<I> order_items(std::vector<std::vector<I>>& per, int order)
     return w;
 }
 
-// Global-load and two-node kernels: (lattice, first tile) items of
-// tiles_per_item tiles of one tile column; tiles of tw x 8 nodes.
-std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s, int tw)
+// Global-load kernel: (lattice, first tile) items of tiles_per_item tiles.
+std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s)
 {
     const int G = std::max(1, s.tiles_per_item);
     std::vector<std::vector<int2>> per(hs.size());
     for (size_t i = 0; i < hs.size(); ++i) {
-        int ntx = (hs[i]->nx + tw - 1) / tw, nty = tiles_y(hs[i]->ny);
+        int ntx = tiles_x(hs[i]->nx), nty = tiles_y(hs[i]->ny);
         for (int by = 0; by < nty; by += G)
             for (int bx = 0; bx < ntx; ++bx) per[i].push_back(make_int2((int)i, by * ntx + bx));
     }
     return order_items(per, s.order);
+}
+
+// Host copy of a lattice's tile flags (computed on the device at create;
+// the geometry does not change afterwards).
+int host_tiles(pflbm_t* h)
+{
+    if (!h->htiles.empty()) return PFLBM_OK;
+    const size_t n = (size_t)tiles_x(h->nx) * tiles_y(h->ny);
+    std::vector<uint8_t> t(n);
+    cudaError_t e = cudaMemcpyAsync(t.data(), h->tiles, n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
+    h->htiles.swap(t);
+    return PFLBM_OK;
+}
+
+// Two-node kernels split by tile kind: per 64-wide tile column, runs of
+// all-fluid tiles and runs of tiles with walls, each cut into items of at
+// most tiles_per_item tiles: (lattice, tile column, first tile row, tiles).
+// The fluid items come first; *n_fluid counts them.
+int build_work_split(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s, std::vector<int4>& w, int* n_fluid)
+{
+    const int G = std::max(1, s.tiles_per_item);
+    std::vector<std::vector<int4>> per_f(hs.size()), per_w(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) {
+        pflbm_t* h = hs[i];
+        if (int rc = host_tiles(h)) return rc;
+        const int ntx = tiles_x(h->nx), nty = tiles_y(h->ny), ntx2 = (h->nx + 63) / 64;
+        for (int bx = 0; bx < ntx2; ++bx) {
+            int by = 0;
+            while (by < nty) {
+                auto fluid = [&](int y) {
+                    return h->htiles[(size_t)y * ntx + 2 * bx] != 0 &&
+                           (2 * bx + 1 >= ntx || h->htiles[(size_t)y * ntx + 2 * bx + 1] != 0);
+                };
+                const bool f = fluid(by);
+                int n = 1;
+                while (by + n < nty && n < G && fluid(by + n) == f) ++n;
+                (f ? per_f : per_w)[i].push_back(make_int4((int)i, bx, by, n));
+                by += n;
+            }
+        }
+    }
+    w = order_items(per_f, s.order);
+    *n_fluid = (int)w.size();
+    std::vector<int4> ww = order_items(per_w, s.order);
+    w.insert(w.end(), ww.begin(), ww.end());
+    return PFLBM_OK;
 }
 
 // Staged kernel: (lattice, strip, first block, blocks | shape << 16) items,
@@ -159,15 +212,21 @@ int upload(pflbm_batch_t* b)
     // the default kernel is the two-node one for 16-bit storage (measured
     // fastest on mixes of small lattices), the global-load one otherwise
     const bool sixteen = b->precision == PFLBM_BF16 || b->precision == PFLBM_FP16;
-    b->pair = b->precision != PFLBM_FP64 && (b->sched.kernel == 3 || (b->sched.kernel == 0 && sixteen));
+    b->split = b->precision != PFLBM_FP64 && (b->sched.kernel == 3 || (b->sched.kernel == 0 && sixteen));
     std::vector<unsigned char> wbytes;
-    size_t item = b->staged ? sizeof(int4) : sizeof(int2);
-    if (b->staged) {
+    size_t item = (b->staged || b->split) ? sizeof(int4) : sizeof(int2);
+    b->n_fluid = 0;
+    if (b->split) {
+        std::vector<int4> w4;
+        if (int rc = build_work_split(b->hs, b->sched, w4, &b->n_fluid)) return rc;
+        wbytes.resize(w4.size() * item);
+        if (!w4.empty()) std::memcpy(wbytes.data(), w4.data(), wbytes.size());
+    } else if (b->staged) {
         std::vector<int4> w4 = build_work_staged(b->hs, b->sched);
         wbytes.resize(w4.size() * item);
         if (!w4.empty()) std::memcpy(wbytes.data(), w4.data(), wbytes.size());
     } else {
-        std::vector<int2> w2 = build_work(b->hs, b->sched, b->pair ? 64 : TX);
+        std::vector<int2> w2 = build_work(b->hs, b->sched);
         wbytes.resize(w2.size() * item);
         if (!w2.empty()) std::memcpy(wbytes.data(), w2.data(), wbytes.size());
     }
@@ -203,12 +262,20 @@ int upload(pflbm_batch_t* b)
     drop_graph(b);   // kernel, work list or grid may differ from the captured ones
     b->n_work = n_items;
     b->phase = 0;
-    int per_sm = b->staged ? staged_batch_ctas_per_sm(b->precision)
-                           : (b->pair ? step2_batch_ctas_per_sm(b->precision) : batch_max_ctas_per_sm(b->precision));
+    int per_sm = b->staged ? staged_batch_ctas_per_sm(b->precision) : batch_max_ctas_per_sm(b->precision);
     if (b->sched.ctas_per_sm > 0) per_sm = std::min(per_sm, b->sched.ctas_per_sm);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     b->grid = std::max(1, std::min(b->n_work, std::max(1, per_sm) * std::max(1, sms)));
+    if (b->split) {
+        int pf = step2_split_ctas_per_sm(b->precision, 1), pw = step2_split_ctas_per_sm(b->precision, 2);
+        if (b->sched.ctas_per_sm > 0) {
+            pf = std::min(pf, b->sched.ctas_per_sm);
+            pw = std::min(pw, b->sched.ctas_per_sm);
+        }
+        b->grid = std::max(1, std::min(b->n_fluid, std::max(1, pf) * std::max(1, sms)));
+        b->grid_w = std::max(1, std::min(b->n_work - b->n_fluid, std::max(1, pw) * std::max(1, sms)));
+    }
     return PFLBM_OK;
 }
 
@@ -229,9 +296,13 @@ cudaError_t launch_set(pflbm_batch_t* b, int set)
     if (b->staged)
         return launch_step_staged_batch(b->precision, b->d_args[set], (const int4*)b->d_work, b->n_work, b->grid,
                                         b->stream);
-    if (b->pair)
-        return launch_step2_batch(b->precision, b->d_args[set], (const int2*)b->d_work, b->n_work,
-                                  std::max(1, b->sched.tiles_per_item), b->grid, b->stream);
+    if (b->split) {
+        const int4* w = (const int4*)b->d_work;
+        cudaError_t e = launch_step2_split(b->precision, 1, b->d_args[set], w, b->n_fluid, b->grid, b->stream);
+        if (e != cudaSuccess) return e;
+        return launch_step2_split(b->precision, 2, b->d_args[set], w + b->n_fluid, b->n_work - b->n_fluid, b->grid_w,
+                                  b->stream);
+    }
     return launch_step_batch(b->precision, b->d_args[set], (const int2*)b->d_work, b->n_work,
                              std::max(1, b->sched.tiles_per_item), b->grid, b->stream);
 }
@@ -365,7 +436,7 @@ int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
 int pflbm_batch_kernel(const pflbm_batch_t* b)
 {
     if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
-    return b->staged ? 2 : (b->pair ? 3 : 1);
+    return b->staged ? 2 : (b->split ? 3 : 1);
 }
 
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes)

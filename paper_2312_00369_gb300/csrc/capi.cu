@@ -150,6 +150,8 @@ void release(pflbm_t* h)
     dfree(h, h->dstatus, sizeof(int) * 4);
     dfree(h, h->tma, tma_sets_bytes());
     dfree(h, h->sflags, staged_flags_bytes(h->nx, h->ny));
+    dfree(h, h->nword, node_words_bytes(h->nx, h->ny));
+    dfree(h, h->tiles2, tile2_flags_bytes(h->nx, h->ny));
     if (h->hstatus) cudaFreeHost(h->hstatus);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -283,7 +285,9 @@ size_t pflbm_footprint_bytes(int nx, int ny, int precision)
     Sizes s = sizes_of(nx, ny, precision);
     return 2 * s.pop + s.sprev + s.wet + s.N * (1 + 1 + 8 + 8 + 8) + s.red + s.pts + s.tiles + 16 +
            (size_t)nx * ny * 4 * sizeof(double) +
-           (precision != PFLBM_FP64 ? tma_sets_bytes() + staged_flags_bytes(nx, ny) : 0);
+           (precision != PFLBM_FP64 ? tma_sets_bytes() + staged_flags_bytes(nx, ny) + node_words_bytes(nx, ny) +
+                                          tile2_flags_bytes(nx, ny)
+                                    : 0);
 }
 
 int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
@@ -412,6 +416,12 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
             h->sflags = (uint8_t*)p;
             CKR(launch_staged_flags(h));
         }
+        // node words and 64 x 8 tile flags of the two-node step
+        if ((rc = dalloc(h, &p, node_words_bytes(nx, ny)))) { release(h); return rc; }
+        h->nword = (uint16_t*)p;
+        if ((rc = dalloc(h, &p, tile2_flags_bytes(nx, ny)))) { release(h); return rc; }
+        h->tiles2 = (uint8_t*)p;
+        CKR(launch_node_words(h));
     }
     CKR(cudaStreamSynchronize(h->stream));
 #undef CKR

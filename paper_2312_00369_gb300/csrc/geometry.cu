@@ -237,6 +237,59 @@ __global__ void k_staged_flags(const uint8_t* __restrict__ cls, uint8_t* __restr
 
 }  // namespace
 
+// Node words of the two-node step: the node byte in the low byte and, in the
+// high byte, bit j - 1 = zeta(x + c_j) for j = 1..8 (x periodic; rows outside
+// the lattice are not zeta = 1 nodes). With it a node's bounce-back sources
+// (Sec. 2.2.2) and a ghost node's zeta-weighted neighbour mean need no class
+// tile. Padding columns hold CLS_OUT.
+__global__ void k_node_words(const uint8_t* __restrict__ cls, uint16_t* __restrict__ words, int nx, int ny, int pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= pitch || y >= ny) return;
+    if (x >= nx) {
+        words[(size_t)y * pitch + x] = CLS_OUT;
+        return;
+    }
+    unsigned m = 0;
+    for (int j = 1; j < 9; ++j) {
+        const int yy = y + cy(j), xx = ((x + cx(j)) % nx + nx) % nx;
+        if (yy >= 0 && yy < ny && zeta_of(cls[(size_t)yy * pitch + xx])) m |= 1u << (j - 1);
+    }
+    words[(size_t)y * pitch + x] = (uint16_t)(cls[(size_t)y * pitch + x] | (m << 8));
+}
+
+// Flags of the two-node step's 64 x 8 tiles: bit 0 both 32 x 8 halves are
+// all-fluid tiles (a right half past the lattice counts as fluid); bit 1 the
+// tile needs phi two nodes out (a zeta = 1 node next to a ghost, or a ghost
+// node, among its nodes, a column past nx - 1 standing for its periodic image).
+__global__ void k_tile2_flags(const uint8_t* __restrict__ cls, const uint8_t* __restrict__ tiles,
+                              uint8_t* __restrict__ tiles2, int nx, int ny, int pitch)
+{
+    const int ntx = (nx + 31) / 32, ntx2 = (nx + 63) / 64, nty = (ny + 7) / 8;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntx2 * nty) return;
+    const int bx = t % ntx2, by = t / ntx2;
+    uint8_t f = (tiles[by * ntx + 2 * bx] != 0 && (2 * bx + 1 >= ntx || tiles[by * ntx + 2 * bx + 1] != 0)) ? 1 : 0;
+    for (int y = by * 8; y < by * 8 + 8 && y < ny; ++y)
+        for (int x = bx * 64; x < bx * 64 + 64; ++x) {
+            const uint8_t c = cls[(size_t)y * pitch + x % nx];
+            if ((zeta_of(c) && (c & F_NEARGHOST)) || (c & CLS_MASK) == CLS_GHOST) f |= 2;
+        }
+    tiles2[t] = f;
+}
+
+size_t node_words_bytes(int nx, int ny) { return (size_t)ny * ((nx + 63) / 64 * 64) * sizeof(uint16_t); }
+size_t tile2_flags_bytes(int nx, int ny) { return (size_t)((nx + 63) / 64) * ((ny + 7) / 8); }
+
+cudaError_t launch_node_words(pflbm_t* h)
+{
+    dim3 b(64, 4), g((h->pitch + 63) / 64, (h->ny + 3) / 4);
+    k_node_words<<<g, b, 0, h->stream>>>(h->cls, h->nword, h->nx, h->ny, h->pitch);
+    const int n = ((h->nx + 63) / 64) * ((h->ny + 7) / 8);
+    k_tile2_flags<<<(n + 127) / 128, 128, 0, h->stream>>>(h->cls, h->tiles, h->tiles2, h->nx, h->ny, h->pitch);
+    return cudaGetLastError();
+}
+
 size_t staged_flags_bytes(int nx, int ny)
 {
     return (size_t)((nx + 31) / 32) * ((ny + 7) / 8) + (size_t)((nx + 63) / 64) * ((ny + 3) / 4);

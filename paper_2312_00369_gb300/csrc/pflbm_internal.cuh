@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <vector>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -139,6 +141,9 @@ struct pflbm {
     // device buffers (sizes: N = ny*pitch nodes)
     uint8_t* cls = nullptr;       // node byte [N]
     uint8_t* tiles = nullptr;     // per step tile: 1 = all nodes within 2 are fluid
+    std::vector<uint8_t> htiles;  // host copy of tiles (filled when a batch first needs it)
+    uint16_t* nword = nullptr;    // two-node step (FP32, 16-bit): node byte | zeta-neighbour bits << 8 [N]
+    uint8_t* tiles2 = nullptr;    // two-node step: per 64 x 8 tile, bit 0 all fluid, bit 1 halo of two
     uint8_t* solid = nullptr;     // user mask [N]
     float* theta = nullptr;       // angle field [N] (degrees)
     void* wet = nullptr;          // a_v sqrt(2 kappa beta) cos(theta) [N] (FP64 or FP32)
@@ -197,10 +202,15 @@ cudaError_t launch_init_populations(pflbm_t* h);
 cudaError_t launch_step(pflbm_t* h);
 // step2.cu: two x-adjacent nodes per thread in packed FP32x2 (FP32, 16-bit)
 cudaError_t launch_step2(pflbm_t* h);
-// two-node kernel over many lattices: (lattice, first 64 x 8 tile) items
-cudaError_t launch_step2_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,
-                               int grid, cudaStream_t stream);
-int step2_batch_ctas_per_sm(int precision);
+size_t node_words_bytes(int nx, int ny);
+size_t tile2_flags_bytes(int nx, int ny);
+cudaError_t launch_node_words(pflbm_t* h);   // nword and tiles2 from cls and tiles
+// two-node kernels over many lattices, split by tile kind (1: all-fluid
+// tiles, 2: tiles with walls), over (lattice, tile column, first tile row,
+// tiles) items of one kind
+cudaError_t launch_step2_split(int precision, int kind, const void* d_args, const int4* d_work, int n_work, int grid,
+                               cudaStream_t stream);
+int step2_split_ctas_per_sm(int precision, int kind);
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p);
 cudaError_t launch_macro_f32(pflbm_t* h, float* phi, float* u, float* p);   // rounded to nearest
 size_t step_args_bytes(int precision);

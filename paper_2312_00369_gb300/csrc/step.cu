@@ -350,6 +350,8 @@ StepArgs<PREC> make_args(pflbm_t* h)
     a.in_copy = h->cur;
     a.sflags[0] = h->sflags;
     a.sflags[1] = h->sflags ? h->sflags + (size_t)((h->nx + 31) / 32) * ((h->ny + 7) / 8) : nullptr;
+    a.nword = h->nword;
+    a.tiles2 = h->tiles2;
     return a;
 }
 

@@ -33,6 +33,7 @@ constexpr int QPW = QX + 4;           // phi tile row (halo 2)
 #define PFLBM_PAIR_EARLY_F 1
 #endif
 
+
 // resident 256-thread CTAs per SM asked of k_step2: 4 with 16-bit storage
 // (64 registers, the pulled populations held as raw pairs), 3 with FP32
 #ifndef PFLBM_STEP2_MINB
@@ -164,117 +165,260 @@ __device__ __forceinline__ F2 phi2(const Hold2<PREC>& v, const int32_t raw[2])
     return F2(T::g0(raw[0]), T::g0(raw[1])) + s;
 }
 
-// Ring positions (width H) around the 64 x 8 tile: phi of one node each.
-template <int PREC, int H, bool WRAP, bool FLUID>
-__device__ __forceinline__ void ring2(const StepArgs<PREC>& a, const uint8_t (*s_cls)[QCW], float (*s_phi)[QPW], int x0,
-                                      int y0, int tid, bool tiny)
+// The one-node ring around an all-fluid 64 x 8 tile: phi of one node each.
+template <int PREC, bool WRAP>
+__device__ __forceinline__ void ring2f(const StepArgs<PREC>& a, float (*s_phi)[QPW], int x0, int y0, int tid, bool tiny)
 {
-    constexpr int RW = QX + 2 * H, NTOP = H * RW, NSIDE = H * QY, NR = 2 * NTOP + 2 * NSIDE;
+    constexpr int RW = QX + 2, NR = 2 * RW + 2 * QY;
     for (int t = tid; t < NR; t += QTX * QY) {
         int py, px;
+        if (t < RW) { py = 1; px = 1 + t; }
+        else if (t < 2 * RW) { py = QY + 2; px = 1 + t - RW; }
+        else if (t < 2 * RW + QY) { py = 2 + t - 2 * RW; px = 1; }
+        else { py = 2 + t - 2 * RW - QY; px = QX + 2; }
+        const int gy = y0 - 2 + py, xr = x0 - 2 + px;
+        const int gx = !WRAP ? xr : (tiny ? wrapn(xr, a.nx) : wrap1(xr, a.nx));
+        s_phi[py][px] = pulled_phi<PREC, false, WRAP, QCW>(a.in, nullptr, 0, 0, gx, gy, a.nx, a.pitch, a.plane);
+    }
+}
+
+// Pull of direction I at node (gx, gy) from its zeta-neighbour bits zm (bit
+// j - 1: zeta(x + c_j)): streaming from x - c_I when that node is a zeta = 1
+// node, else f*_{I'} of x + c_I when that one is, else the node's own
+// f*_{I'} (modified bounce-back, Sec. 2.2.2). The same selection as the
+// class-tile pull (step_core.cuh), one load whatever the lanes select.
+template <int I, int PREC, bool WRAP>
+__device__ __forceinline__ float pullm(const typename Store<PREC>::S* __restrict__ base, unsigned zm, int gx, int gy,
+                                       int nx, int pitch, int plane)
+{
+    using T = Store<PREC>;
+    constexpr int X = cx(I), Y = cy(I), O = opp(I);
+    static_assert(T::template unit<I>() == T::template unit<O>(), "opposite directions share a unit");
+    int src;
+    if constexpr (!WRAP) {
+        const int k = gy * pitch + gx;
+        src = k + O * plane;
+        if (zm & (1u << (I - 1))) src = k + (O * plane + Y * pitch + X);
+        if (zm & (1u << (O - 1))) src = k + (I * plane - Y * pitch - X);
+    } else {
+        src = O * plane + gy * pitch + gx;
+        if (zm & (1u << (I - 1))) src = O * plane + (gy + Y) * pitch + wrap1(gx + X, nx);
+        if (zm & (1u << (O - 1))) src = I * plane + (gy - Y) * pitch + wrap1(gx - X, nx);
+    }
+    return T::template ldp<I>(PFLBM_LD(base, src, 9LL * plane));
+}
+
+template <int PREC, bool WRAP>
+__device__ __forceinline__ void pull_fm(float v[9], const typename Store<PREC>::S* __restrict__ f, unsigned zm, int gx,
+                                        int gy, int nx, int pitch, int plane)
+{
+    using T = Store<PREC>;
+    v[0] = T::template ldp<0>(PFLBM_LD(f, gy * pitch + gx, 9LL * plane));
+    v[1] = pullm<1, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+    v[2] = pullm<2, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+    v[3] = pullm<3, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+    v[4] = pullm<4, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+    v[5] = pullm<5, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+    v[6] = pullm<6, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+    v[7] = pullm<7, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+    v[8] = pullm<8, PREC, WRAP>(f, zm, gx, gy, nx, pitch, plane);
+}
+
+// One node's pulled g (raw g_0 and g_0..g_8); returns phi.
+template <int PREC, bool WRAP>
+__device__ __forceinline__ float pull_gm(float v[9], int32_t& raw, const Planes<PREC>& P, unsigned zm, int gx, int gy,
+                                         int nx, int pitch, int plane)
+{
+    using T = Store<PREC>;
+    raw = PFLBM_LD(P.g0, gy * pitch + gx, plane);
+    v[0] = T::g0(raw);
+    v[1] = pullm<1, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    v[2] = pullm<2, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    v[3] = pullm<3, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    v[4] = pullm<4, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    v[5] = pullm<5, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    v[6] = pullm<6, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    v[7] = pullm<7, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    v[8] = pullm<8, PREC, WRAP>(P.g, zm, gx, gy, nx, pitch, plane);
+    return phi_of<PREC>(v);
+}
+
+// Ring positions (width H) around a tile with walls, one or two per thread:
+// their lattice coordinates, and phi of the node there from its word (0 on
+// nodes that are not zeta = 1 and outside the lattice).
+template <int H>
+struct Ring2 {
+    static constexpr int RW = QX + 2 * H, NTOP = H * RW, NSIDE = H * QY, NR = 2 * NTOP + 2 * NSIDE;
+    static constexpr int N = (NR + QTX * QY - 1) / (QTX * QY);
+    __device__ static __forceinline__ void pos(int t, int& py, int& px)
+    {
         if (t < NTOP) { py = 2 - H + t / RW; px = 2 - H + t % RW; }
         else if (t < 2 * NTOP) { const int u = t - NTOP; py = QY + 2 + u / RW; px = 2 - H + u % RW; }
         else if (t < 2 * NTOP + NSIDE) { const int u = t - 2 * NTOP; py = 2 + u / H; px = 2 - H + u % H; }
         else { const int u = t - 2 * NTOP - NSIDE; py = 2 + u / H; px = QX + 2 + u % H; }
-        const int gy = y0 - 2 + py, xr = x0 - 2 + px;
-        const int gx = !WRAP ? xr : (tiny ? wrapn(xr, a.nx) : wrap1(xr, a.nx));
-        float ph = 0.0f;
-        if (FLUID) {
-            ph = pulled_phi<PREC, false, WRAP, QCW>(a.in, nullptr, 0, 0, gx, gy, a.nx, a.pitch, a.plane);
+    }
+};
+
+// phi-tile positions the ghost fill visits (the tile and one ring) and how
+// many each thread takes
+constexpr int QGW = QX + 2, QGP = QGW * (QY + 2), QNG = (QGP + QTX * QY - 1) / (QTX * QY);
+
+// Prologue of a 64 x 8 tile with walls, phi needed H nodes out. Loads in
+// the order their results are needed: the words of the pair, the ring
+// positions and (H = 2) the ghost-fill positions; the pair's g, selected by
+// its words; the ghost-fill words into shared memory; the ring's g. Then phi, one barrier, the ghost values (H = 2: the
+// zeta-weighted 3 x 3 mean of Sec. 2.2.2, b = 9, or the Robin value of
+// Appendix A cases 1 and 3 on flat walls), another barrier.
+template <int PREC, bool WRAP, int H>
+__device__ __forceinline__ void wall_prologue(const StepArgs<PREC>& a, float (*s_phi)[QPW], uint16_t* s_gw, int x0,
+                                              int y0, Hold2<PREC>& g, int32_t raw[2], uint8_t code[2], unsigned zm[2])
+{
+    using RG = Ring2<H>;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * QTX + tx;
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const bool tiny = nx < QX + 8;
+    auto wx = [&](int x) { return !WRAP ? x : (tiny ? wrapn(x, nx) : wrap1(x, nx)); };
+    const int gxa = x0 + 2 * tx, gy = y0 + ty;
+
+    // words: the pair, the ring positions, the ghost-fill positions
+    uint16_t w[2] = {CLS_OUT, CLS_OUT};
+    if (gy < ny) {
+        if (!WRAP) {
+            const uint32_t wp = PFLBM_LD(reinterpret_cast<const uint32_t*>(a.nword), (gy * pitch + gxa) / 2, a.plane / 2);
+            w[0] = (uint16_t)(wp & 0xffffu);
+            w[1] = (uint16_t)(wp >> 16);
         } else {
-            const int sy = py + 1, sx = px + 1;
-            const uint8_t c = s_cls[sy][sx];
-            if (zeta_of(c)) {
-                if (has_link(c))
-                    ph = pulled_phi<PREC, true, WRAP, QCW>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
-                else
-                    ph = pulled_phi<PREC, false, WRAP, QCW>(a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
-            }
+            w[0] = PFLBM_LD(a.nword, gy * pitch + wx(gxa), a.plane);
+            w[1] = PFLBM_LD(a.nword, gy * pitch + wx(gxa + 1), a.plane);
+        }
+    }
+    uint16_t rw[RG::N];
+#pragma unroll
+    for (int q = 0; q < RG::N; ++q) {
+        rw[q] = CLS_OUT;
+        const int t = tid + q * QTX * QY;
+        if (t < RG::NR) {
+            int py, px;
+            RG::pos(t, py, px);
+            const int yy = y0 - 2 + py;
+            if (yy >= 0 && yy < ny) rw[q] = PFLBM_LD(a.nword, yy * pitch + wx(x0 - 2 + px), a.plane);
+        }
+    }
+    uint16_t gw[QNG];
+#pragma unroll
+    for (int q = 0; q < QNG; ++q) {
+        gw[q] = CLS_OUT;
+        const int p = tid + q * QTX * QY;
+        if (H == 2 && p < QGP) {
+            const int yy = y0 - 1 + p / QGW;
+            if (yy >= 0 && yy < ny) gw[q] = PFLBM_LD(a.nword, yy * pitch + wx(x0 - 1 + p % QGW), a.plane);
+        }
+    }
+
+    // the pair's own pulls
+    float ga[9], gb[9];
+    float pha = 0.0f, phb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ga[i] = gb[i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        code[j] = (uint8_t)(w[j] & 0xffu);
+        zm[j] = w[j] >> 8;
+    }
+    if (gy < ny && zeta_of(code[0])) pha = pull_gm<PREC, WRAP>(ga, raw[0], a.in, zm[0], wx(gxa), gy, nx, pitch, a.plane);
+    if (gy < ny && zeta_of(code[1])) phb = pull_gm<PREC, WRAP>(gb, raw[1], a.in, zm[1], wx(gxa + 1), gy, nx, pitch, a.plane);
+    if (H == 2) {
+#pragma unroll
+        for (int q = 0; q < QNG; ++q) {
+            const int p = tid + q * QTX * QY;
+            if (p < QGP) s_gw[p] = gw[q];
+        }
+    }
+    // the ring's pulls
+#pragma unroll
+    for (int q = 0; q < RG::N; ++q) {
+        const int t = tid + q * QTX * QY;
+        if (t >= RG::NR) break;
+        int py, px;
+        RG::pos(t, py, px);
+        float ph = 0.0f;
+        if (zeta_of((uint8_t)(rw[q] & 0xffu))) {
+            float v[9];
+            int32_t r;
+            ph = pull_gm<PREC, WRAP>(v, r, a.in, rw[q] >> 8, wx(x0 - 2 + px), y0 - 2 + py, nx, pitch, a.plane);
         }
         s_phi[py][px] = ph;
     }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) g.set(i, F2(ga[i], gb[i]));
+    s_phi[ty + 2][2 * tx + 2] = pha;
+    s_phi[ty + 2][2 * tx + 3] = phb;
+    __syncthreads();
+    if (H == 2) {
+        // ghost values; the mean reads only zeta = 1 neighbours, which no
+        // thread writes here
+        for (int p = tid; p < QGP; p += QTX * QY) {
+            const uint16_t wd = s_gw[p];
+            const uint8_t c = (uint8_t)(wd & 0xffu);
+            if (c == CLS_OUT || (c & CLS_MASK) != CLS_GHOST) continue;
+            const int py = p / QGW + 1, px = p % QGW + 1;
+            if (c & (F_GHOST_UP | F_GHOST_DOWN)) {
+                const float pb = s_phi[(c & F_GHOST_UP) ? py + 1 : py - 1][px];
+                s_phi[py][px] = robin_ghost<float>(pb, PFLBM_LD(a.wet, (y0 - 2 + py) * pitch + wx(x0 - 2 + px), a.plane));
+                continue;
+            }
+            const unsigned m = wd >> 8;
+            float num = 0.0f, den = 0.0f;
+#pragma unroll
+            for (int j = 1; j < 9; ++j) {
+                if (m & (1u << (j - 1))) {
+                    num += s_phi[py + cy(j)][px + cx(j)];
+                    den += 1.0f;
+                }
+            }
+            s_phi[py][px] = num / den;
+        }
+        __syncthreads();
+    }
 }
 
-// One scalar node's g (with bounce-back when it has an unknown link).
-template <int PREC, bool WRAP>
-__device__ __forceinline__ float own_g(float v[9], int32_t& raw, const StepArgs<PREC>& a, const uint8_t (*s_cls)[QCW],
-                                       int sy, int sx, int gx, int gy, uint8_t code)
-{
-    if (has_link(code))
-        pull_g<PREC, true, WRAP, QCW>(v, raw, a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
-    else
-        pull_g<PREC, false, WRAP, QCW>(v, raw, a.in, s_cls, sy, sx, gx, gy, a.nx, a.pitch, a.plane);
-    return phi_of<PREC>(v);
-}
-
-template <int PREC, int VV, bool WRAP, bool EARLY_F>
-__device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, uint8_t (*s_cls)[QCW],
-                                      float (*s_phi)[QPW])
+// KIND: 0 reads the tile's flags; 1 a tile known to be all fluid (the wall
+// path is not compiled in); 2 a tile known to have walls. EARLY_F: on an
+// all-fluid tile, pull f with g, before the phi-tile barrier.
+template <int PREC, int VV, bool WRAP, bool EARLY_F, int KIND = 0>
+__device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, float (*s_phi)[QPW], uint16_t* s_gw)
 {
     using T = Store<PREC>;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * QTX + tx;
     const int x0 = bx * QX, y0 = by * QY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
-    const int ntx = tiles_x(nx);
-    // the two 32 x 8 tiles of this one: fluid when both are (or the right
-    // one lies beyond the lattice)
-    const bool fluid = a.tiles[by * ntx + 2 * bx] != 0 && (2 * bx + 1 >= ntx || a.tiles[by * ntx + 2 * bx + 1] != 0);
+    // bit 0: both 32 x 8 halves all fluid; bit 1: phi needed two nodes out
+    const uint8_t tflags = KIND == 1 ? (uint8_t)1 : a.tiles2[by * ((nx + QX - 1) / QX) + bx];
+    const bool fluid = KIND == 1 || (KIND == 0 && (tflags & 1));
     const bool tiny = nx < QX + 8;
     const int gxa = x0 + 2 * tx, gy = y0 + ty;
     Hold2<PREC> g;
     int32_t raw[2] = {0, 0};
     uint8_t code[2] = {CLS_FLUID, CLS_FLUID};
-
+    unsigned zm[2] = {0xffu, 0xffu};
     Hold2<PREC> fearly;
+
     if (fluid) {
-        // ---- prologue of an all-fluid tile: no class tile, no checks ----
+        // ---- prologue of an all-fluid tile: no node words, no checks ----
         pull2_g<PREC, WRAP>(g, raw, a.in, gxa, gy, nx, pitch, a.plane);
         if (EARLY_F) pull2_f<PREC, WRAP>(fearly, a.in.f, gxa, gy, nx, pitch, a.plane);
         const F2 ph = phi2<PREC>(g, raw);
         s_phi[ty + 2][2 * tx + 2] = ph.x;
         s_phi[ty + 2][2 * tx + 3] = ph.y;
-        ring2<PREC, 1, WRAP, true>(a, s_cls, s_phi, x0, y0, tid, tiny);
+        ring2f<PREC, WRAP>(a, s_phi, x0, y0, tid, tiny);
         __syncthreads();
     } else {
-        // ---- general prologue: class tile (halo 3), phi tile, ghosts ----
-        auto wx = [&](int x) { return !WRAP ? x : (tiny ? wrapn(x, nx) : wrap1(x, nx)); };
-        for (int p = tid; p < (QY + 6) * QCW; p += QTX * QY) {
-            const int py = p / QCW, px = p - py * QCW;
-            const int yy = y0 - 3 + py, xx = wx(x0 - 3 + px);
-            s_cls[py][px] = (yy < 0 || yy >= ny) ? (uint8_t)CLS_OUT : PFLBM_LD(a.cls, yy * pitch + xx, a.plane);
-        }
-        __syncthreads();
-        code[0] = s_cls[ty + 3][2 * tx + 3];
-        code[1] = s_cls[ty + 3][2 * tx + 4];
-        bool near_ghost = false;
-        for (int j = 0; j < 2; ++j) {
-            const uint8_t c = code[j];
-            near_ghost |= (gy < ny) && c != CLS_OUT &&
-                          ((zeta_of(c) && (c & F_NEARGHOST)) || (c & CLS_MASK) == CLS_GHOST);
-        }
-        const int halo = __syncthreads_or(near_ghost) ? 2 : 1;
-        float ga[9], gb[9];
-        float pha = 0.0f, phb = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) ga[i] = gb[i] = 0.0f;
-        if (gy < ny && zeta_of(code[0]))
-            pha = own_g<PREC, WRAP>(ga, raw[0], a, s_cls, ty + 3, 2 * tx + 3, wx(gxa), gy, code[0]);
-        if (gy < ny && zeta_of(code[1]))
-            phb = own_g<PREC, WRAP>(gb, raw[1], a, s_cls, ty + 3, 2 * tx + 4, wx(gxa + 1), gy, code[1]);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) g.set(i, F2(ga[i], gb[i]));
-        s_phi[ty + 2][2 * tx + 2] = pha;
-        s_phi[ty + 2][2 * tx + 3] = phb;
-        if (halo == 1) ring2<PREC, 1, WRAP, false>(a, s_cls, s_phi, x0, y0, tid, tiny);
-        else ring2<PREC, 2, WRAP, false>(a, s_cls, s_phi, x0, y0, tid, tiny);
-        __syncthreads();
-        if (halo == 2) {
-            fill_ghosts<float, QX, QY, QPW>(
-                s_phi, [&](int dy, int dx) { return s_cls[dy + 3][dx + 3]; },
-                [&](int dy, int dx) { return PFLBM_LD(a.wet, (y0 + dy) * pitch + wx(x0 + dx), a.plane); }, tid,
-                QTX * QY);
-            __syncthreads();
-        }
+        // ---- tile with walls: each node's word gives its class and its
+        // bounce-back sources; every load is issued before the barrier ----
+        if (tflags & 2)
+            wall_prologue<PREC, WRAP, 2>(a, s_phi, s_gw, x0, y0, g, raw, code, zm);
+        else
+            wall_prologue<PREC, WRAP, 1>(a, s_phi, s_gw, x0, y0, g, raw, code, zm);
     }
 
     // ---- the two nodes ----
@@ -305,26 +449,19 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, u
     node_core<PREC, true, VV>(
         a, lane, Cr[1], gpx, gpy, lap, g,
         [&](Hold2<PREC>& fv) {
-            if (fluid) {
-                if (EARLY_F) fv = fearly;
-                else pull2_f<PREC, WRAP>(fv, a.in.f, gxa, gy, nx, pitch, a.plane);
-                return;
+            if (fluid && EARLY_F) {
+                fv = fearly;
+            } else if (fluid) {
+                pull2_f<PREC, WRAP>(fv, a.in.f, gxa, gy, nx, pitch, a.plane);
+            } else {
+                float fa[9], fb[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fa[i] = fb[i] = 0.0f;
+                if (lane.valid[0]) pull_fm<PREC, WRAP>(fa, a.in.f, zm[0], gxa, gy, nx, pitch, a.plane);
+                if (lane.valid[1]) pull_fm<PREC, WRAP>(fb, a.in.f, zm[1], gxa + 1, gy, nx, pitch, a.plane);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fv.set(i, F2(fa[i], fb[i]));
             }
-            float fa[9], fb[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) fa[i] = fb[i] = 0.0f;
-            auto one = [&](float v[9], int j, int gxj) {
-                if (!lane.valid[j]) return;
-                if (has_link(code[j]))
-                    pull_f<PREC, true, WRAP, QCW>(v, a.in.f, s_cls, ty + 3, 2 * tx + 3 + j, gxj, gy, nx, pitch, a.plane);
-                else
-                    pull_f<PREC, false, WRAP, QCW>(v, a.in.f, s_cls, ty + 3, 2 * tx + 3 + j, gxj, gy, nx, pitch,
-                                                   a.plane);
-            };
-            one(fa, 0, gxa);
-            one(fb, 1, gxa + 1);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) fv.set(i, F2(fa[i], fb[i]));
         },
         [&](int k) {
             const float2 v = PFLBM_LD(reinterpret_cast<const float2*>(a.sprev), k / 2, a.plane / 2);
@@ -336,24 +473,19 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, u
 // L2 prefetch of the rows that the tile (pf_dx, pf_dy) tiles later in launch
 // order reads, as in the one-node kernel: the population planes, g_0 (16-bit
 // storage: its own int32 array), the u.grad(phi) history and, for a tile
-// with walls, the node bytes. A row segment of the 64-node tile is 128 B per
+// with walls, the node words. A row segment of the 64-node tile is 128 B per
 // 16-bit plane and 256 B per 32-bit one; one prefetch per 128 B line. Rows
 // start on a 128 B line (x0 a multiple of 64, the pitch a multiple of 64
 // elements); every address lies inside the lattice's arrays.
 template <int PREC>
-__device__ __forceinline__ void prefetch2_l2(const StepArgs<PREC>& a, int bx, int by)
+__device__ __forceinline__ void prefetch2_rows(const StepArgs<PREC>& a, int px, int py, int tid)
 {
-    const int ntx = gridDim.x, nty = gridDim.y;
-    int px = bx + a.pf_dx, py = by + a.pf_dy;
-    if (px >= ntx) { px -= ntx; ++py; }
-    if (py >= nty) return;
-    const int ntx32 = tiles_x(a.nx);
-    const bool walls = a.tiles[py * ntx32 + 2 * px] == 0 || (2 * px + 1 < ntx32 && a.tiles[py * ntx32 + 2 * px + 1] == 0);
+    const bool walls = (a.tiles2[py * ((a.nx + QX - 1) / QX) + px] & 1) == 0;
     constexpr bool F32 = PREC == PFLBM_FP32;
     // lines per row: populations (FP32: 18 planes x 2 lines; 16-bit: 17 planes
-    // x 1 line and g_0 x 2), history 2, node bytes 1
+    // x 1 line and g_0 x 2), history 2, node words 1
     constexpr int NPOP = F32 ? 36 : 19, NL = NPOP + 3;
-    for (int s = threadIdx.y * QTX + threadIdx.x; s < NL * QY; s += QTX * QY) {
+    for (int s = tid; s < NL * QY; s += QTX * QY) {
         const int q = s / QY, gy = py * QY + (s - q * QY);
         if (gy >= a.ny) continue;
         const int row = gy * a.pitch + px * QX;
@@ -372,55 +504,67 @@ __device__ __forceinline__ void prefetch2_l2(const StepArgs<PREC>& a, int bx, in
             p = reinterpret_cast<const char*>(a.sprev + row) + (q - NPOP) * 128;
         } else {
             if (!walls) continue;
-            p = reinterpret_cast<const char*>(a.cls + row);
+            p = reinterpret_cast<const char*>(a.nword + row);
         }
         asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
     }
 }
 
+template <int PREC>
+__device__ __forceinline__ void prefetch2_l2(const StepArgs<PREC>& a, int bx, int by)
+{
+    const int ntx = gridDim.x, nty = gridDim.y;
+    int px = bx + a.pf_dx, py = by + a.pf_dy;
+    if (px >= ntx) { px -= ntx; ++py; }
+    if (py >= nty) return;
+    prefetch2_rows<PREC>(a, px, py, threadIdx.y * QTX + threadIdx.x);
+}
+
 template <int PREC, int VV>
 __global__ void __launch_bounds__(QTX * QY, PREC == PFLBM_FP32 ? PFLBM_STEP2_MINB32 : PFLBM_STEP2_MINB) k_step2(const __grid_constant__ StepArgs<PREC> a)
 {
-    __shared__ uint8_t s_cls[QY + 6][QCW];
     __shared__ __align__(16) float s_phi[QY + 4][QPW];
+    __shared__ uint16_t s_gw[QGP];
     if (PFLBM_L2_AHEAD2 > 0) prefetch2_l2<PREC>(a, blockIdx.x, blockIdx.y);
     const int x0 = blockIdx.x * QX;
     // every x the tile touches (class tile: three out) inside the lattice
     if (x0 >= 3 && x0 + QX + 3 <= a.nx)
-        tile2<PREC, VV, false, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_cls, s_phi);
+        tile2<PREC, VV, false, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_phi, s_gw);
     else
-        tile2<PREC, VV, true, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_cls, s_phi);
+        tile2<PREC, VV, true, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_phi, s_gw);
 }
 
-// Persistent two-node step over many lattices: work item w = (lattice,
-// first 64 x 8 tile); an item covers `group` tiles of one tile column, top to
-// bottom. CTAs take items w = blockIdx.x, blockIdx.x + gridDim.x, ... The
-// item's lattice descriptor is copied to shared memory and read from there.
-template <int PREC>
+// The batched step split by tile kind: KIND 1 over items of all-fluid
+// tiles, KIND 2 over items of tiles with walls, each kernel compiled for its
+// own path (registers, occupancy, loads issued before the barrier). Item =
+// (lattice, tile column, first tile row, tiles): a run of tiles of one kind
+// down one tile column.
+template <int PREC, int KIND>
 __global__ void __launch_bounds__(QTX * QY, PREC == PFLBM_FP32 ? PFLBM_STEP2_MINB32 : PFLBM_STEP2_MINB)
-    k_step2_batch(const StepArgs<PREC>* __restrict__ args, const int2* __restrict__ work, int n_work, int group)
+    k_step2_split(const StepArgs<PREC>* __restrict__ args, const int4* __restrict__ work, int n_work)
 {
-    __shared__ uint8_t s_cls[QY + 6][QCW];
     __shared__ __align__(16) float s_phi[QY + 4][QPW];
+    __shared__ uint16_t s_gw[QGP];
     __shared__ __align__(16) unsigned char s_args_raw[sizeof(StepArgs<PREC>)];
     const StepArgs<PREC>& a = *reinterpret_cast<const StepArgs<PREC>*>(s_args_raw);
     const int tid = threadIdx.y * QTX + threadIdx.x;
+    int cur = -1;   // lattice whose descriptor is in shared memory
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const int2 it = work[w];
-        {
+        const int4 it = work[w];
+        if (it.x != cur) {   // the end-of-tile barrier has freed the descriptor
             const int* src = reinterpret_cast<const int*>(args + it.x);
             int* dst = reinterpret_cast<int*>(s_args_raw);
             for (int i = tid; i < (int)(sizeof(StepArgs<PREC>) / sizeof(int)); i += QTX * QY) dst[i] = src[i];
+            cur = it.x;
+            __syncthreads();
         }
-        __syncthreads();
-        const int ntx = (a.nx + QX - 1) / QX, nty = (a.ny + QY - 1) / QY;
-        const int bx = it.y % ntx, by0 = it.y / ntx;
-        for (int gi = 0; gi < group && by0 + gi < nty; ++gi) {
-            const int x0 = bx * QX;
-            if (x0 >= 3 && x0 + QX + 3 <= a.nx)
-                tile2<PREC, 2, false, false>(a, bx, by0 + gi, s_cls, s_phi);
+        const int bx = it.y, x0 = bx * QX;
+        const bool inner = x0 >= 3 && x0 + QX + 3 <= a.nx;
+        for (int gi = 0; gi < it.w; ++gi) {
+            if (inner)
+                tile2<PREC, 2, false, false, KIND>(a, bx, it.z + gi, s_phi, s_gw);
             else
-                tile2<PREC, 2, true, false>(a, bx, by0 + gi, s_cls, s_phi);
+                tile2<PREC, 2, true, false, KIND>(a, bx, it.z + gi, s_phi, s_gw);
             __syncthreads();   // the next tile reuses the shared tiles and descriptor
         }
     }
@@ -443,36 +587,46 @@ cudaError_t run2(pflbm_t* h)
 
 }  // namespace
 
-cudaError_t launch_step2_batch(int precision, const void* d_args, const int2* d_work, int n_work, int group,
-                               int grid, cudaStream_t stream)
+template <int PREC>
+cudaError_t split2(int kind, const void* d_args, const int4* d_work, int n_work, int grid, cudaStream_t stream)
 {
-    dim3 b(QTX, QY);
-    switch (precision) {
-        case PFLBM_FP32:
-            k_step2_batch<PFLBM_FP32><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_FP32>*)d_args, d_work, n_work, group);
-            break;
-        case PFLBM_BF16:
-            k_step2_batch<PFLBM_BF16><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_BF16>*)d_args, d_work, n_work, group);
-            break;
-        case PFLBM_FP16:
-            k_step2_batch<PFLBM_FP16><<<grid, b, 0, stream>>>((const StepArgs<PFLBM_FP16>*)d_args, d_work, n_work, group);
-            break;
-        default: return cudaErrorInvalidValue;
-    }
+    const dim3 b(QTX, QY);
+    const auto* args = (const StepArgs<PREC>*)d_args;
+    if (kind == 1) k_step2_split<PREC, 1><<<grid, b, 0, stream>>>(args, d_work, n_work);
+    else k_step2_split<PREC, 2><<<grid, b, 0, stream>>>(args, d_work, n_work);
     return cudaGetLastError();
 }
 
-int step2_batch_ctas_per_sm(int precision)
+template <int PREC>
+int split2_ctas_per_sm(int kind)
 {
     int n = 0;
-    cudaError_t e;
+    const cudaError_t e = kind == 1
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_split<PREC, 1>, QTX * QY, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_split<PREC, 2>, QTX * QY, 0);
+    return e == cudaSuccess ? n : 1;
+}
+
+cudaError_t launch_step2_split(int precision, int kind, const void* d_args, const int4* d_work, int n_work, int grid,
+                               cudaStream_t stream)
+{
+    if (n_work <= 0) return cudaSuccess;
     switch (precision) {
-        case PFLBM_FP32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_batch<PFLBM_FP32>, QTX * QY, 0); break;
-        case PFLBM_BF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_batch<PFLBM_BF16>, QTX * QY, 0); break;
-        case PFLBM_FP16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_batch<PFLBM_FP16>, QTX * QY, 0); break;
+        case PFLBM_FP32: return split2<PFLBM_FP32>(kind, d_args, d_work, n_work, grid, stream);
+        case PFLBM_BF16: return split2<PFLBM_BF16>(kind, d_args, d_work, n_work, grid, stream);
+        case PFLBM_FP16: return split2<PFLBM_FP16>(kind, d_args, d_work, n_work, grid, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int step2_split_ctas_per_sm(int precision, int kind)
+{
+    switch (precision) {
+        case PFLBM_FP32: return split2_ctas_per_sm<PFLBM_FP32>(kind);
+        case PFLBM_BF16: return split2_ctas_per_sm<PFLBM_BF16>(kind);
+        case PFLBM_FP16: return split2_ctas_per_sm<PFLBM_FP16>(kind);
         default: return 1;
     }
-    return e == cudaSuccess ? n : 1;
 }
 
 cudaError_t launch_step2(pflbm_t* h)

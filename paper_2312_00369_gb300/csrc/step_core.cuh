@@ -77,6 +77,8 @@ struct StepArgs {
     int pf_dx, pf_dy;    // k_step L2 prefetch target: PFLBM_L2_AHEAD CTAs on, in tiles
     const TmaSet* tma;   // staged step: tensor maps [tile shape][population copy]
     const uint8_t* sflags[2];   // staged step: tile flags of each shape (fluid, ring of two)
+    const uint16_t* nword;      // two-node step: node byte | zeta-neighbour bits << 8
+    const uint8_t* tiles2;      // two-node step: 64 x 8 tile flags (all fluid, ring of two)
     int in_copy;         // which population copy `in` is (index into tma)
     int* status;
     // macroscopic output (read-back kernel only), dense [ny][nx]
