@@ -255,13 +255,14 @@ typedef struct {
     int order;           /* 0: lattice by lattice; 1: largest lattices first,
                             items interleaved across lattices                 */
     int use_graph;       /* replay step pairs from a captured CUDA graph      */
-    int kernel;          /* 0: default (3 for 16-bit storage, else 1); 1:
-                            global-load kernel, 32 x 8 tiles; 2: staged
-                            kernel (TMA ring) with the size classes below;
-                            3: two-node kernel (two x-adjacent nodes per
-                            thread in packed FP32x2 arithmetic), 64 x 8
-                            tiles, all-fluid tiles and tiles with walls in
-                            two launches. FP64 batches always use 1.        */
+    int kernel;          /* 0: default (3); 1: global-load kernel, 32 x 8
+                            tiles; 2: staged kernel (TMA ring) with the
+                            size classes below; 3: two-node kernel (two
+                            x-adjacent nodes per thread in packed FP32x2
+                            arithmetic), 64 x 8 tiles, all-fluid tiles and
+                            tiles with walls in two launches, tiles without
+                            a zeta = 1 node left out. FP64 batches always
+                            use 1.                                          */
     /* Staged kernel, per size class: a lattice with nx * ny <=
      * class_max_nodes[k] (first such k < n_classes) runs with tile shape
      * class_shape[k] (0: 32 x 8, 1: 64 x 4) and class_tiles[k] tiles per

@@ -121,43 +121,45 @@ std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedu
     return order_items(per, s.order);
 }
 
-// Host copy of a lattice's tile flags (computed on the device at create;
-// the geometry does not change afterwards).
-int host_tiles(pflbm_t* h)
+// Host copy of a lattice's 64 x 8 tile flags (computed on the device at
+// create; the geometry does not change afterwards).
+int host_tiles2(pflbm_t* h)
 {
-    if (!h->htiles.empty()) return PFLBM_OK;
-    const size_t n = (size_t)tiles_x(h->nx) * tiles_y(h->ny);
+    if (!h->htiles2.empty()) return PFLBM_OK;
+    const size_t n = tile2_flags_bytes(h->nx, h->ny);
     std::vector<uint8_t> t(n);
-    cudaError_t e = cudaMemcpyAsync(t.data(), h->tiles, n, cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(t.data(), h->tiles2, n, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
-    h->htiles.swap(t);
+    h->htiles2.swap(t);
     return PFLBM_OK;
 }
 
 // Two-node kernels split by tile kind: per 64-wide tile column, runs of
 // all-fluid tiles and runs of tiles with walls, each cut into items of at
 // most tiles_per_item tiles: (lattice, tile column, first tile row, tiles).
-// The fluid items come first; *n_fluid counts them.
+// Tiles without a zeta = 1 node are left out (they store nothing). The fluid
+// items come first; *n_fluid counts them.
 int build_work_split(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s, std::vector<int4>& w, int* n_fluid)
 {
     const int G = std::max(1, s.tiles_per_item);
     std::vector<std::vector<int4>> per_f(hs.size()), per_w(hs.size());
     for (size_t i = 0; i < hs.size(); ++i) {
         pflbm_t* h = hs[i];
-        if (int rc = host_tiles(h)) return rc;
-        const int ntx = tiles_x(h->nx), nty = tiles_y(h->ny), ntx2 = (h->nx + 63) / 64;
+        if (int rc = host_tiles2(h)) return rc;
+        const int nty = tiles_y(h->ny), ntx2 = (h->nx + 63) / 64;
+        // 0: skipped, 1: all fluid, 2: walls
+        auto kind = [&](int bx, int y) {
+            const uint8_t t = h->htiles2[(size_t)y * ntx2 + bx];
+            return !(t & 4) ? 0 : ((t & 1) ? 1 : 2);
+        };
         for (int bx = 0; bx < ntx2; ++bx) {
             int by = 0;
             while (by < nty) {
-                auto fluid = [&](int y) {
-                    return h->htiles[(size_t)y * ntx + 2 * bx] != 0 &&
-                           (2 * bx + 1 >= ntx || h->htiles[(size_t)y * ntx + 2 * bx + 1] != 0);
-                };
-                const bool f = fluid(by);
+                const int k = kind(bx, by);
                 int n = 1;
-                while (by + n < nty && n < G && fluid(by + n) == f) ++n;
-                (f ? per_f : per_w)[i].push_back(make_int4((int)i, bx, by, n));
+                while (by + n < nty && n < G && kind(bx, by + n) == k) ++n;
+                if (k) (k == 1 ? per_f : per_w)[i].push_back(make_int4((int)i, bx, by, n));
                 by += n;
             }
         }
@@ -209,10 +211,9 @@ int upload(pflbm_batch_t* b)
     b->staged = b->precision != PFLBM_FP64 && b->sched.kernel == 2;
     for (pflbm_t* h : b->hs)
         if (!h->tma) b->staged = false;
-    // the default kernel is the two-node one for 16-bit storage (measured
-    // fastest on mixes of small lattices), the global-load one otherwise
-    const bool sixteen = b->precision == PFLBM_BF16 || b->precision == PFLBM_FP16;
-    b->split = b->precision != PFLBM_FP64 && (b->sched.kernel == 3 || (b->sched.kernel == 0 && sixteen));
+    // the default kernel is the two-node one split by tile kind (measured
+    // fastest on mixes of small lattices in FP32 and 16-bit storage)
+    b->split = b->precision != PFLBM_FP64 && (b->sched.kernel == 3 || b->sched.kernel == 0);
     std::vector<unsigned char> wbytes;
     size_t item = (b->staged || b->split) ? sizeof(int4) : sizeof(int2);
     b->n_fluid = 0;

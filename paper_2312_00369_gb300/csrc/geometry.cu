@@ -261,7 +261,9 @@ __global__ void k_node_words(const uint8_t* __restrict__ cls, uint16_t* __restri
 // Flags of the two-node step's 64 x 8 tiles: bit 0 both 32 x 8 halves are
 // all-fluid tiles (a right half past the lattice counts as fluid); bit 1 the
 // tile needs phi two nodes out (a zeta = 1 node next to a ghost, or a ghost
-// node, among its nodes, a column past nx - 1 standing for its periodic image).
+// node, among its nodes, a column past nx - 1 standing for its periodic
+// image); bit 2 the tile has a zeta = 1 node (x < nx): a tile without one
+// stores nothing, and the step skips it.
 __global__ void k_tile2_flags(const uint8_t* __restrict__ cls, const uint8_t* __restrict__ tiles,
                               uint8_t* __restrict__ tiles2, int nx, int ny, int pitch)
 {
@@ -274,6 +276,7 @@ __global__ void k_tile2_flags(const uint8_t* __restrict__ cls, const uint8_t* __
         for (int x = bx * 64; x < bx * 64 + 64; ++x) {
             const uint8_t c = cls[(size_t)y * pitch + x % nx];
             if ((zeta_of(c) && (c & F_NEARGHOST)) || (c & CLS_MASK) == CLS_GHOST) f |= 2;
+            if (x < nx && zeta_of(c)) f |= 4;
         }
     tiles2[t] = f;
 }

@@ -141,9 +141,10 @@ struct pflbm {
     // device buffers (sizes: N = ny*pitch nodes)
     uint8_t* cls = nullptr;       // node byte [N]
     uint8_t* tiles = nullptr;     // per step tile: 1 = all nodes within 2 are fluid
-    std::vector<uint8_t> htiles;  // host copy of tiles (filled when a batch first needs it)
     uint16_t* nword = nullptr;    // two-node step (FP32, 16-bit): node byte | zeta-neighbour bits << 8 [N]
-    uint8_t* tiles2 = nullptr;    // two-node step: per 64 x 8 tile, bit 0 all fluid, bit 1 halo of two
+    uint8_t* tiles2 = nullptr;    // two-node step: per 64 x 8 tile, bit 0 all fluid, bit 1 halo of two,
+                                  // bit 2 has a zeta = 1 node
+    std::vector<uint8_t> htiles2; // host copy of tiles2 (filled when a batch first needs it)
     uint8_t* solid = nullptr;     // user mask [N]
     float* theta = nullptr;       // angle field [N] (degrees)
     void* wet = nullptr;          // a_v sqrt(2 kappa beta) cos(theta) [N] (FP64 or FP32)

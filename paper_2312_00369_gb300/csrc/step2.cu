@@ -392,8 +392,10 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, f
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * QTX + tx;
     const int x0 = bx * QX, y0 = by * QY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
-    // bit 0: both 32 x 8 halves all fluid; bit 1: phi needed two nodes out
-    const uint8_t tflags = KIND == 1 ? (uint8_t)1 : a.tiles2[by * ((nx + QX - 1) / QX) + bx];
+    // bit 0: both 32 x 8 halves all fluid; bit 1: phi needed two nodes out;
+    // bit 2: a zeta = 1 node
+    const uint8_t tflags = KIND == 1 ? (uint8_t)5 : a.tiles2[by * ((nx + QX - 1) / QX) + bx];
+    if (!(tflags & 4)) return;   // no zeta = 1 node: nothing to store (the whole CTA leaves)
     const bool fluid = KIND == 1 || (KIND == 0 && (tflags & 1));
     const bool tiny = nx < QX + 8;
     const int gxa = x0 + 2 * tx, gy = y0 + ty;
