@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpflbm.so")
 LIB_BOUNDS = os.path.join(HERE, "libpflbm_bounds.so")
 # translation units whose accesses the index-checked build checks
-BOUNDS_SRCS = ("step.cu", "step_tma.cu", "capi.cu")
+BOUNDS_SRCS = ("step.cu", "step2.cu", "step_tma.cu", "capi.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit multiply-add contraction; the kernels write their
 # fused multiply-adds explicitly, so every kernel that inlines a formula

@@ -464,7 +464,7 @@ int pflbm_debug_bounds(int* enabled, unsigned* violations)
 #else
     if (enabled) *enabled = 0;
 #endif
-    if (violations) *violations = bounds_violations_step() + bounds_violations_tma();
+    if (violations) *violations = bounds_violations_step() + bounds_violations_tma() + bounds_violations_step2();
     return PFLBM_OK;
 }
 

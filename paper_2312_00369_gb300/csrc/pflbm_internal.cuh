@@ -232,6 +232,7 @@ int staged_batch_ctas_per_sm(int precision);
 // index-checked build: out-of-range accesses counted in step.cu / step_tma.cu
 unsigned bounds_violations_step();
 unsigned bounds_violations_tma();
+unsigned bounds_violations_step2();
 
 // diag.cu
 cudaError_t launch_mass(pflbm_t* h, double* d_out);

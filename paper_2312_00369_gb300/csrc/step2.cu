@@ -631,6 +631,17 @@ int step2_split_ctas_per_sm(int precision, int kind)
     }
 }
 
+#ifdef PFLBM_BOUNDS
+unsigned bounds_violations_step2()
+{
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_bounds_viol, sizeof(v));
+    return v;
+}
+#else
+unsigned bounds_violations_step2() { return 0; }
+#endif
+
 cudaError_t launch_step2(pflbm_t* h)
 {
     switch (h->precision) {

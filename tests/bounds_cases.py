@@ -2,8 +2,8 @@
 
 Run as a script in its own process (the library is loaded once per process):
     PFLBM_LIBRARY=.../libpflbm_bounds.so python tests/bounds_cases.py
-Every step kernel (global loads; staged, both tile shapes) and the batched
-kernels step the cases; the script prints one JSON line with the number of
+Every step kernel (global loads; staged, both tile shapes; two nodes per
+thread) and the batched kernels step the cases; the script prints one JSON line with the number of
 refused accesses and the FP32 error against the FP64 oracle, and exits 1 if
 the build is not the index-checked one.
 """
@@ -34,7 +34,7 @@ def main():
         ref = oj.run_case(name, steps)
         errs = {}
         for prec in ("fp32", "bf16"):
-            for kernel in ("global", "staged32x8", "staged64x4"):
+            for kernel in ("global", "staged32x8", "staged64x4", "pair"):
                 s = pflbm.Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
                                  precision=prec, step_kernel=kernel, step_chunk=3, **case.physical(),
                                  **oj.solver_options(case))
@@ -46,10 +46,10 @@ def main():
                 s.close()
                 errs[f"{prec}/{kernel}"] = float(np.max(np.abs(phi - ref["phi"])))
         out["cases"][name] = errs
-    # batches of uneven lattices, both batched kernels
+    # batches of uneven lattices, every batched kernel
     stream = torch.cuda.Stream()
     cases = wl.batched_instances(count=6, seed=11)
-    for kernel in (1, 2):
+    for kernel in (1, 2, 3):
         members = []
         for c in cases:
             s = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision="bf16", stream=stream, **c.physical())
