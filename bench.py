@@ -320,9 +320,9 @@ def batched_line(args, torch, world, local, steps, warmup, plain=True, precision
         "plain_fp32_one_launch_per_lattice_mlups": plain_mlups,
         "speedup_vs_plain": (value / plain_mlups) if plain_mlups else None,
         "autotune_ms_per_step": timings,
-        # the two-node batched kernel runs as two launches per step (all-fluid
-        # tiles, tiles with walls); the others as one
-        "gpu_launches": (2 if kernel == 3 else 1) * steps, "clocks": clocks,
+        # the two-node batched kernel runs one launch per group of same-size
+        # lattices each step (batch info's grid); the others one launch
+        "gpu_launches": (info["grid"] if kernel == 3 else 1) * steps, "clocks": clocks,
     }
 
 

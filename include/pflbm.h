@@ -259,10 +259,11 @@ typedef struct {
                             tiles; 2: staged kernel (TMA ring) with the
                             size classes below; 3: two-node kernel (two
                             x-adjacent nodes per thread in packed FP32x2
-                            arithmetic), 64 x 8 tiles, all-fluid tiles and
-                            tiles with walls in two launches, tiles without
-                            a zeta = 1 node left out. FP64 batches always
-                            use 1.                                          */
+                            arithmetic), one launch per group of lattices
+                            of one size, one 64 x 8 tile per CTA, the
+                            groups' launches side by side (tiles_per_item,
+                            order and ctas_per_sm do not apply). FP64
+                            batches always use 1.                           */
     /* Staged kernel, per size class: a lattice with nx * ny <=
      * class_max_nodes[k] (first such k < n_classes) runs with tile shape
      * class_shape[k] (0: 32 x 8, 1: 64 x 4) and class_tiles[k] tiles per
@@ -291,7 +292,9 @@ int pflbm_batch_set(pflbm_batch_t* b, pflbm_t* const* hs, int count);
 int pflbm_batch_step(pflbm_batch_t* b, int64_t n);
 /* The step kernel the batch runs (1 global loads, 2 staged, 3 two-node). */
 int pflbm_batch_kernel(const pflbm_batch_t* b);
-/* Work items, persistent grid size and total nodes of the batch. */
+/* Work items, persistent grid size and total nodes of the batch (kernel 3:
+ * the CTAs of all launches, one 64 x 8 tile each, and the number of
+ * launches per step). */
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes);
 void pflbm_batch_destroy(pflbm_batch_t* b);
 

@@ -5,19 +5,19 @@ The batched step has three kernels and several knobs (``pflbm_schedule_t``):
 * the global-load kernel (32 x 8 tiles): persistent CTAs per SM, tiles of one
   tile column per work item, item order;
 * the two-node kernel (64 x 8 tiles, two x-adjacent nodes per thread in
-  packed FP32x2 arithmetic; all-fluid tiles and tiles with walls in two
-  launches): tiles per work item, item order;
+  packed FP32x2 arithmetic; one launch per group of same-size lattices,
+  side by side): no knobs, one candidate;
 * the staged kernel (TMA ring): per size class of the mix, the tile shape
   (32 x 8 or 64 x 4) and the tiles a CTA marches down per work item.
 
 The best choice depends on the mix of lattice sizes and on the GPU, so it is
 measured. Every candidate runs a few batched steps on scratch copies of the
 lattices (same geometry and parameters, so the real solves are not
-advanced), timed with CUDA events. The global-load and two-node kernels'
-knobs are swept as a grid; the staged kernel's per-class shape and item
-length are chosen by coordinate descent over the classes, largest total
-node count first. The
-fastest schedule is cached per (GPU, precision, size mix) in a JSON file.
+advanced), timed with CUDA events. The global-load kernel's knobs are
+swept as a grid; the staged kernel's per-class shape and item length are
+chosen by coordinate descent over the classes, largest total node count
+first. The fastest schedule is cached per (GPU, precision, size mix) in a
+JSON file.
 """
 from __future__ import annotations
 
@@ -30,8 +30,7 @@ from . import pflbm
 
 GLOBAL_CANDIDATES = [dict(kernel=1, ctas_per_sm=c, tiles_per_item=g, order=o, use_graph=1)
                      for c in (0, 4) for g in (1, 2, 4, 8) for o in (0, 1)]
-PAIR_CANDIDATES = [dict(kernel=3, ctas_per_sm=0, tiles_per_item=g, order=o, use_graph=1)
-                   for g in (1, 2, 4, 8) for o in (0, 1)]
+PAIR_CANDIDATES = [dict(kernel=3, ctas_per_sm=0, tiles_per_item=1, order=0, use_graph=1)]
 STAGED_OPTIONS = [(shape, tiles) for shape in (0, 1) for tiles in (2, 4, 8, 16)]
 
 
@@ -43,7 +42,7 @@ def cache_path():
 def signature(cases, precision, device_name):
     sizes = sorted((int(c.nx), int(c.ny)) for c in cases)
     h = hashlib.sha1(json.dumps(sizes).encode()).hexdigest()[:16]
-    return f"v3|{device_name}|{precision}|{len(sizes)}|{h}"
+    return f"v4|{device_name}|{precision}|{len(sizes)}|{h}"
 
 
 def _load_cache():
@@ -68,7 +67,7 @@ def _save_cache(d):
 
 def name_of(sched):
     if sched.get("kernel", 1) == 3:
-        return "pair_g{tiles_per_item}_o{order}".format(**sched)
+        return "pair_by_size"
     if sched.get("kernel", 1) == 2:
         cls = ",".join(f"{m}:{'32x8' if s == 0 else '64x4'}/{t}" for m, s, t in sched["classes"])
         return f"staged[{cls}]"

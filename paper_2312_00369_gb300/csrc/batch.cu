@@ -11,6 +11,7 @@
 // launches of two steps (set p, set 1 - p) are captured once in a CUDA graph
 // and replayed.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -37,9 +38,17 @@ struct pflbm_batch {
     int cap_lattices = 0, cap_work = 0;
     void* d_args[2] = {nullptr, nullptr};
     bool staged = false;          // staged (TMA ring) kernel, int4 items; else int2 items
-    bool split = false;           // two-node kernels split by tile kind: int4 items, fluid first
-    int n_fluid = 0;              // split: items of all-fluid tiles (the rest have walls)
-    int grid_w = 0;               // split: grid of the wall-tile kernel (grid: the fluid one's)
+    bool by_class = false;        // two-node kernel, one launch per group of same-size lattices
+    struct ClassLaunch {
+        int vv, nx, ny, count;
+        std::vector<unsigned char> descs[2];   // count step descriptors of each set (host)
+    };
+    std::vector<ClassLaunch> classes;
+    // per-class launches run side by side: forked from the batch's stream to
+    // these streams and joined back (in the captured graph as well)
+    static constexpr int kForks = 4;
+    cudaStream_t fork_stream[kForks] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kForks] = {};
     void* d_work = nullptr;
     int n_work = 0;
     int grid = 0;
@@ -121,56 +130,6 @@ std::vector<int2> build_work(const std::vector<pflbm_t*>& hs, const pflbm_schedu
     return order_items(per, s.order);
 }
 
-// Host copy of a lattice's 64 x 8 tile flags (computed on the device at
-// create; the geometry does not change afterwards).
-int host_tiles2(pflbm_t* h)
-{
-    if (!h->htiles2.empty()) return PFLBM_OK;
-    const size_t n = tile2_flags_bytes(h->nx, h->ny);
-    std::vector<uint8_t> t(n);
-    cudaError_t e = cudaMemcpyAsync(t.data(), h->tiles2, n, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e));
-    h->htiles2.swap(t);
-    return PFLBM_OK;
-}
-
-// Two-node kernels split by tile kind: per 64-wide tile column, runs of
-// all-fluid tiles and runs of tiles with walls, each cut into items of at
-// most tiles_per_item tiles: (lattice, tile column, first tile row, tiles).
-// Tiles without a zeta = 1 node are left out (they store nothing). The fluid
-// items come first; *n_fluid counts them.
-int build_work_split(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s, std::vector<int4>& w, int* n_fluid)
-{
-    const int G = std::max(1, s.tiles_per_item);
-    std::vector<std::vector<int4>> per_f(hs.size()), per_w(hs.size());
-    for (size_t i = 0; i < hs.size(); ++i) {
-        pflbm_t* h = hs[i];
-        if (int rc = host_tiles2(h)) return rc;
-        const int nty = tiles_y(h->ny), ntx2 = (h->nx + 63) / 64;
-        // 0: skipped, 1: all fluid, 2: walls
-        auto kind = [&](int bx, int y) {
-            const uint8_t t = h->htiles2[(size_t)y * ntx2 + bx];
-            return !(t & 4) ? 0 : ((t & 1) ? 1 : 2);
-        };
-        for (int bx = 0; bx < ntx2; ++bx) {
-            int by = 0;
-            while (by < nty) {
-                const int k = kind(bx, by);
-                int n = 1;
-                while (by + n < nty && n < G && kind(bx, by + n) == k) ++n;
-                if (k) (k == 1 ? per_f : per_w)[i].push_back(make_int4((int)i, bx, by, n));
-                by += n;
-            }
-        }
-    }
-    w = order_items(per_f, s.order);
-    *n_fluid = (int)w.size();
-    std::vector<int4> ww = order_items(per_w, s.order);
-    w.insert(w.end(), ww.begin(), ww.end());
-    return PFLBM_OK;
-}
-
 // Staged kernel: (lattice, strip, first block, blocks | shape << 16) items,
 // shape and blocks per item by size class.
 std::vector<int4> build_work_staged(const std::vector<pflbm_t*>& hs, const pflbm_schedule_t& s)
@@ -211,17 +170,50 @@ int upload(pflbm_batch_t* b)
     b->staged = b->precision != PFLBM_FP64 && b->sched.kernel == 2;
     for (pflbm_t* h : b->hs)
         if (!h->tma) b->staged = false;
-    // the default kernel is the two-node one split by tile kind (measured
-    // fastest on mixes of small lattices in FP32 and 16-bit storage)
-    b->split = b->precision != PFLBM_FP64 && (b->sched.kernel == 3 || b->sched.kernel == 0);
+    // the default kernel is the two-node one, one launch per group of
+    // same-size lattices (measured fastest on mixes of small lattices in
+    // FP32 and 16-bit storage)
+    b->by_class = b->precision != PFLBM_FP64 && (b->sched.kernel == 3 || b->sched.kernel == 0);
+    b->classes.clear();
+    if (b->by_class) {
+        // groups of lattices with the same size and viscosity mode, largest
+        // first, each cut into launches of at most step2_class_capacity()
+        const int K = step2_class_capacity(b->precision);
+        std::vector<int> idx(n);
+        for (int i = 0; i < n; ++i) idx[i] = i;
+        auto vv = [&](int i) { return (b->hs[i]->prm.nu_l > 0 && b->hs[i]->prm.nu_g > 0) ? 1 : 0; };
+        std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) {
+            const long long np = (long long)b->hs[p]->nx * b->hs[p]->ny, nq = (long long)b->hs[q]->nx * b->hs[q]->ny;
+            if (np != nq) return np > nq;
+            if (b->hs[p]->nx != b->hs[q]->nx) return b->hs[p]->nx > b->hs[q]->nx;
+            return vv(p) < vv(q);
+        });
+        for (int j = 0; j < n;) {
+            const pflbm_t* h0 = b->hs[idx[j]];
+            int e = j;
+            while (e < n && e - j < K && b->hs[idx[e]]->nx == h0->nx && b->hs[idx[e]]->ny == h0->ny &&
+                   vv(idx[e]) == vv(idx[j]))
+                ++e;
+            pflbm_batch::ClassLaunch cl;
+            cl.vv = vv(idx[j]);
+            cl.nx = h0->nx;
+            cl.ny = h0->ny;
+            cl.count = e - j;
+            for (int set = 0; set < 2; ++set) {
+                const std::vector<unsigned char>& src = set ? a1 : a0;
+                cl.descs[set].resize(b->args_bytes * cl.count);
+                for (int m = 0; m < cl.count; ++m)
+                    std::memcpy(cl.descs[set].data() + b->args_bytes * m, src.data() + b->args_bytes * idx[j + m],
+                                b->args_bytes);
+            }
+            b->classes.push_back(std::move(cl));
+            j = e;
+        }
+    }
     std::vector<unsigned char> wbytes;
-    size_t item = (b->staged || b->split) ? sizeof(int4) : sizeof(int2);
-    b->n_fluid = 0;
-    if (b->split) {
-        std::vector<int4> w4;
-        if (int rc = build_work_split(b->hs, b->sched, w4, &b->n_fluid)) return rc;
-        wbytes.resize(w4.size() * item);
-        if (!w4.empty()) std::memcpy(wbytes.data(), w4.data(), wbytes.size());
+    size_t item = b->staged ? sizeof(int4) : sizeof(int2);
+    if (b->by_class) {
+        // no work list: each launch's grid is (tiles, lattices)
     } else if (b->staged) {
         std::vector<int4> w4 = build_work_staged(b->hs, b->sched);
         wbytes.resize(w4.size() * item);
@@ -268,14 +260,28 @@ int upload(pflbm_batch_t* b)
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     b->grid = std::max(1, std::min(b->n_work, std::max(1, per_sm) * std::max(1, sms)));
-    if (b->split) {
-        int pf = step2_split_ctas_per_sm(b->precision, 1), pw = step2_split_ctas_per_sm(b->precision, 2);
-        if (b->sched.ctas_per_sm > 0) {
-            pf = std::min(pf, b->sched.ctas_per_sm);
-            pw = std::min(pw, b->sched.ctas_per_sm);
+    if (b->by_class) {
+        // info: the CTAs (one 64 x 8 tile each) of all launches, and the launches
+        long long ctas = 0;
+        for (const auto& cl : b->classes) ctas += (long long)cl.count * ((cl.nx + 63) / 64) * ((cl.ny + 7) / 8);
+        b->n_work = (int)std::min(ctas, (long long)INT_MAX);
+        b->grid = (int)b->classes.size();
+    }
+    if (b->by_class && b->classes.size() > 1) {
+        // the forked streams and events of the per-class launches (made here,
+        // outside any stream capture)
+        const int nf = std::min((int)b->classes.size(), (int)pflbm_batch::kForks);
+        for (int k = 0; k < nf; ++k) {
+            cudaError_t e2 = cudaSuccess;
+            if (!b->fork_stream[k]) e2 = cudaStreamCreateWithFlags(&b->fork_stream[k], cudaStreamNonBlocking);
+            if (e2 == cudaSuccess && !b->join_ev[k])
+                e2 = cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
+            if (e2 != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e2));
         }
-        b->grid = std::max(1, std::min(b->n_fluid, std::max(1, pf) * std::max(1, sms)));
-        b->grid_w = std::max(1, std::min(b->n_work - b->n_fluid, std::max(1, pw) * std::max(1, sms)));
+        if (!b->fork_ev) {
+            cudaError_t e2 = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+            if (e2 != cudaSuccess) return set_error(PFLBM_ECUDA, cudaGetErrorString(e2));
+        }
     }
     return PFLBM_OK;
 }
@@ -297,12 +303,23 @@ cudaError_t launch_set(pflbm_batch_t* b, int set)
     if (b->staged)
         return launch_step_staged_batch(b->precision, b->d_args[set], (const int4*)b->d_work, b->n_work, b->grid,
                                         b->stream);
-    if (b->split) {
-        const int4* w = (const int4*)b->d_work;
-        cudaError_t e = launch_step2_split(b->precision, 1, b->d_args[set], w, b->n_fluid, b->grid, b->stream);
-        if (e != cudaSuccess) return e;
-        return launch_step2_split(b->precision, 2, b->d_args[set], w + b->n_fluid, b->n_work - b->n_fluid, b->grid_w,
-                                  b->stream);
+    if (b->by_class) {
+        const int nc = (int)b->classes.size();
+        if (nc == 1)
+            return launch_step2_class(b->precision, b->classes[0].vv, b->classes[0].descs[set].data(),
+                                      b->classes[0].count, b->classes[0].nx, b->classes[0].ny, b->stream);
+        const int nf = std::min(nc, (int)pflbm_batch::kForks);   // streams made by upload()
+        cudaError_t e = cudaEventRecord(b->fork_ev, b->stream);
+        for (int k = 0; k < nf && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->fork_stream[k], b->fork_ev, 0);
+        // largest groups first, dealt round-robin over the forked streams
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+            const auto& cl = b->classes[c];
+            e = launch_step2_class(b->precision, cl.vv, cl.descs[set].data(), cl.count, cl.nx, cl.ny,
+                                   b->fork_stream[c % nf]);
+        }
+        for (int k = 0; k < nf && e == cudaSuccess; ++k) e = cudaEventRecord(b->join_ev[k], b->fork_stream[k]);
+        for (int k = 0; k < nf && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->stream, b->join_ev[k], 0);
+        return e;
     }
     return launch_step_batch(b->precision, b->d_args[set], (const int2*)b->d_work, b->n_work,
                              std::max(1, b->sched.tiles_per_item), b->grid, b->stream);
@@ -437,7 +454,7 @@ int pflbm_batch_step(pflbm_batch_t* b, int64_t n)
 int pflbm_batch_kernel(const pflbm_batch_t* b)
 {
     if (!b) return set_error(PFLBM_EINVAL, "batch: NULL batch");
-    return b->staged ? 2 : (b->split ? 3 : 1);
+    return b->staged ? 2 : (b->by_class ? 3 : 1);
 }
 
 int pflbm_batch_info(const pflbm_batch_t* b, int* n_work, int* grid, int64_t* nodes)
@@ -455,6 +472,14 @@ void pflbm_batch_destroy(pflbm_batch_t* b)
     DeviceGuard g(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
+    for (int k = 0; k < pflbm_batch::kForks; ++k) {
+        if (b->fork_stream[k]) {
+            cudaStreamSynchronize(b->fork_stream[k]);
+            cudaStreamDestroy(b->fork_stream[k]);
+        }
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     for (int k = 0; k < 2; ++k) bfree(b, b->d_args[k], b->args_bytes * b->cap_lattices);
     bfree(b, b->d_work, sizeof(int4) * b->cap_work);
     delete b;

@@ -144,7 +144,6 @@ struct pflbm {
     uint16_t* nword = nullptr;    // two-node step (FP32, 16-bit): node byte | zeta-neighbour bits << 8 [N]
     uint8_t* tiles2 = nullptr;    // two-node step: per 64 x 8 tile, bit 0 all fluid, bit 1 halo of two,
                                   // bit 2 has a zeta = 1 node
-    std::vector<uint8_t> htiles2; // host copy of tiles2 (filled when a batch first needs it)
     uint8_t* solid = nullptr;     // user mask [N]
     float* theta = nullptr;       // angle field [N] (degrees)
     void* wet = nullptr;          // a_v sqrt(2 kappa beta) cos(theta) [N] (FP64 or FP32)
@@ -206,12 +205,12 @@ cudaError_t launch_step2(pflbm_t* h);
 size_t node_words_bytes(int nx, int ny);
 size_t tile2_flags_bytes(int nx, int ny);
 cudaError_t launch_node_words(pflbm_t* h);   // nword and tiles2 from cls and tiles
-// two-node kernels over many lattices, split by tile kind (1: all-fluid
-// tiles, 2: tiles with walls), over (lattice, tile column, first tile row,
-// tiles) items of one kind
-cudaError_t launch_step2_split(int precision, int kind, const void* d_args, const int4* d_work, int n_work, int grid,
+// two-node kernel over up to step2_class_capacity() lattices of one size
+// (nx, ny) and one viscosity mode: descs holds their step descriptors
+// (count x step_args_bytes, host memory, copied into the launch)
+int step2_class_capacity(int precision);
+cudaError_t launch_step2_class(int precision, int vv, const unsigned char* descs, int count, int nx, int ny,
                                cudaStream_t stream);
-int step2_split_ctas_per_sm(int precision, int kind);
 cudaError_t launch_macro(pflbm_t* h, double* phi, double* u, double* p);
 cudaError_t launch_macro_f32(pflbm_t* h, float* phi, float* u, float* p);   // rounded to nearest
 size_t step_args_bytes(int precision);

@@ -14,6 +14,7 @@
 // an x component are one aligned load for both nodes.
 #include "step_core.cuh"
 
+#include <cstring>
 #include <type_traits>
 
 namespace pfk {
@@ -536,40 +537,56 @@ __global__ void __launch_bounds__(QTX * QY, PREC == PFLBM_FP32 ? PFLBM_STEP2_MIN
         tile2<PREC, VV, true, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_phi, s_gw);
 }
 
-// The batched step split by tile kind: KIND 1 over items of all-fluid
-// tiles, KIND 2 over items of tiles with walls, each kernel compiled for its
-// own path (registers, occupancy, loads issued before the barrier). Item =
-// (lattice, tile column, first tile row, tiles): a run of tiles of one kind
-// down one tile column.
-template <int PREC, int KIND>
+// Lattices of one size in one launch: grid (tiles of one lattice, lattices),
+// the lattices' step descriptors in the kernel's parameter space (read like
+// the single-lattice kernel's, through uniform indexing by blockIdx.y), and
+// each CTA one 64 x 8 tile with the single-lattice tile body: the tile's
+// kind read from its flags, tiles without a zeta = 1 node left at once, f
+// pulled with g on all-fluid tiles, and an L2 prefetch of the tile that a
+// CTA PFLBM_L2_AHEAD2 later in launch order reads.
+template <int PREC>
+struct ClassArgs2 {
+    static constexpr int K = (30 * 1024) / (int)sizeof(StepArgs<PREC>);
+    int count, ntx2, ntiles, pad;
+    StepArgs<PREC> a[K];
+};
+
+template <int PREC, int VV>
 __global__ void __launch_bounds__(QTX * QY, PREC == PFLBM_FP32 ? PFLBM_STEP2_MINB32 : PFLBM_STEP2_MINB)
-    k_step2_split(const StepArgs<PREC>* __restrict__ args, const int4* __restrict__ work, int n_work)
+    k_step2_class(const __grid_constant__ ClassArgs2<PREC> P)
 {
     __shared__ __align__(16) float s_phi[QY + 4][QPW];
     __shared__ uint16_t s_gw[QGP];
-    __shared__ __align__(16) unsigned char s_args_raw[sizeof(StepArgs<PREC>)];
-    const StepArgs<PREC>& a = *reinterpret_cast<const StepArgs<PREC>*>(s_args_raw);
-    const int tid = threadIdx.y * QTX + threadIdx.x;
-    int cur = -1;   // lattice whose descriptor is in shared memory
-    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const int4 it = work[w];
-        if (it.x != cur) {   // the end-of-tile barrier has freed the descriptor
-            const int* src = reinterpret_cast<const int*>(args + it.x);
-            int* dst = reinterpret_cast<int*>(s_args_raw);
-            for (int i = tid; i < (int)(sizeof(StepArgs<PREC>) / sizeof(int)); i += QTX * QY) dst[i] = src[i];
-            cur = it.x;
-            __syncthreads();
-        }
-        const int bx = it.y, x0 = bx * QX;
-        const bool inner = x0 >= 3 && x0 + QX + 3 <= a.nx;
-        for (int gi = 0; gi < it.w; ++gi) {
-            if (inner)
-                tile2<PREC, 2, false, false, KIND>(a, bx, it.z + gi, s_phi, s_gw);
-            else
-                tile2<PREC, 2, true, false, KIND>(a, bx, it.z + gi, s_phi, s_gw);
-            __syncthreads();   // the next tile reuses the shared tiles and descriptor
+    const StepArgs<PREC>& a = P.a[blockIdx.y];
+    if (PFLBM_L2_AHEAD2 > 0) {
+        const int t = blockIdx.y * P.ntiles + blockIdx.x + PFLBM_L2_AHEAD2;
+        if (t < P.count * P.ntiles) {
+            const int l = t / P.ntiles, tt = t - l * P.ntiles;
+            prefetch2_rows<PREC>(P.a[l], tt % P.ntx2, tt / P.ntx2, threadIdx.y * QTX + threadIdx.x);
         }
     }
+    const int bx = blockIdx.x % P.ntx2, by = blockIdx.x / P.ntx2, x0 = bx * QX;
+    if (x0 >= 3 && x0 + QX + 3 <= a.nx)
+        tile2<PREC, VV, false, PFLBM_PAIR_EARLY_F != 0>(a, bx, by, s_phi, s_gw);
+    else
+        tile2<PREC, VV, true, PFLBM_PAIR_EARLY_F != 0>(a, bx, by, s_phi, s_gw);
+}
+
+template <int PREC>
+cudaError_t class2(int vv, const unsigned char* descs, int count, int nx, int ny, cudaStream_t stream)
+{
+    using P = ClassArgs2<PREC>;
+    if (count < 1 || count > P::K) return cudaErrorInvalidValue;
+    static thread_local P p;   // 30 KB: off the stack; the launch copies it
+    p.count = count;
+    p.ntx2 = (nx + QX - 1) / QX;
+    p.ntiles = p.ntx2 * ((ny + QY - 1) / QY);
+    p.pad = 0;
+    std::memcpy(p.a, descs, (size_t)count * sizeof(StepArgs<PREC>));
+    const dim3 g(p.ntiles, count), b(QTX, QY);
+    if (vv) k_step2_class<PREC, 1><<<g, b, 0, stream>>>(p);
+    else k_step2_class<PREC, 0><<<g, b, 0, stream>>>(p);
+    return cudaGetLastError();
 }
 
 template <int PREC>
@@ -589,48 +606,6 @@ cudaError_t run2(pflbm_t* h)
 
 }  // namespace
 
-template <int PREC>
-cudaError_t split2(int kind, const void* d_args, const int4* d_work, int n_work, int grid, cudaStream_t stream)
-{
-    const dim3 b(QTX, QY);
-    const auto* args = (const StepArgs<PREC>*)d_args;
-    if (kind == 1) k_step2_split<PREC, 1><<<grid, b, 0, stream>>>(args, d_work, n_work);
-    else k_step2_split<PREC, 2><<<grid, b, 0, stream>>>(args, d_work, n_work);
-    return cudaGetLastError();
-}
-
-template <int PREC>
-int split2_ctas_per_sm(int kind)
-{
-    int n = 0;
-    const cudaError_t e = kind == 1
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_split<PREC, 1>, QTX * QY, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_split<PREC, 2>, QTX * QY, 0);
-    return e == cudaSuccess ? n : 1;
-}
-
-cudaError_t launch_step2_split(int precision, int kind, const void* d_args, const int4* d_work, int n_work, int grid,
-                               cudaStream_t stream)
-{
-    if (n_work <= 0) return cudaSuccess;
-    switch (precision) {
-        case PFLBM_FP32: return split2<PFLBM_FP32>(kind, d_args, d_work, n_work, grid, stream);
-        case PFLBM_BF16: return split2<PFLBM_BF16>(kind, d_args, d_work, n_work, grid, stream);
-        case PFLBM_FP16: return split2<PFLBM_FP16>(kind, d_args, d_work, n_work, grid, stream);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-int step2_split_ctas_per_sm(int precision, int kind)
-{
-    switch (precision) {
-        case PFLBM_FP32: return split2_ctas_per_sm<PFLBM_FP32>(kind);
-        case PFLBM_BF16: return split2_ctas_per_sm<PFLBM_BF16>(kind);
-        case PFLBM_FP16: return split2_ctas_per_sm<PFLBM_FP16>(kind);
-        default: return 1;
-    }
-}
-
 #ifdef PFLBM_BOUNDS
 unsigned bounds_violations_step2()
 {
@@ -641,6 +616,27 @@ unsigned bounds_violations_step2()
 #else
 unsigned bounds_violations_step2() { return 0; }
 #endif
+
+int step2_class_capacity(int precision)
+{
+    switch (precision) {
+        case PFLBM_FP32: return ClassArgs2<PFLBM_FP32>::K;
+        case PFLBM_BF16: return ClassArgs2<PFLBM_BF16>::K;
+        case PFLBM_FP16: return ClassArgs2<PFLBM_FP16>::K;
+        default: return 0;
+    }
+}
+
+cudaError_t launch_step2_class(int precision, int vv, const unsigned char* descs, int count, int nx, int ny,
+                               cudaStream_t stream)
+{
+    switch (precision) {
+        case PFLBM_FP32: return class2<PFLBM_FP32>(vv, descs, count, nx, ny, stream);
+        case PFLBM_BF16: return class2<PFLBM_BF16>(vv, descs, count, nx, ny, stream);
+        case PFLBM_FP16: return class2<PFLBM_FP16>(vv, descs, count, nx, ny, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_step2(pflbm_t* h)
 {

@@ -112,11 +112,11 @@ def test_staged_batch_with_mixed_shapes_equals_single(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
-@pytest.mark.parametrize("tiles_per_item", [1, 3])
-def test_pair_batch_equals_single(precision, tiles_per_item):
-    # the two-node kernel over a mix of lattice sizes and wall types (flat,
-    # inclined, cylinder) in one persistent launch: each member equals its
-    # own single-lattice run with the global-load kernel
+def test_pair_batch_equals_single(precision):
+    # the two-node batched kernel over a mix of lattice sizes and wall types
+    # (flat, inclined, cylinder), one launch per size, the launches side by
+    # side: each member equals its own single-lattice run with the
+    # global-load kernel
     from paper_2312_00369_gb300 import pflbm, workloads as wl
     cases = wl.batched_instances(count=12, seed=11)
     stream = torch.cuda.Stream()
@@ -126,7 +126,7 @@ def test_pair_batch_equals_single(precision, tiles_per_item):
         for d in c.droplets:
             s.init_droplet(*d)
         members.append(s)
-    b = pflbm.Batch(members, pflbm.schedule(tiles_per_item=tiles_per_item, kernel=3))
+    b = pflbm.Batch(members, pflbm.schedule(kernel=3))
     assert b.kernel == 3
     b.step(23)
     for c, s in zip(cases, members):
