@@ -3,13 +3,14 @@
 //
 // A batch holds, in device memory, one step descriptor per lattice for each
 // parity of the ping-pong state (set 0: in = current copy, out = the other;
-// set 1: swapped) and a work list. Each step is one launch over the work
-// list: k_step_batch over (lattice, first tile) items; or the staged kernel;
-// or (the default for 16-bit storage) two launches of the two-node kernel,
-// one over the items of all-fluid 64 x 8 tiles and one over the items of
-// tiles with walls, each compiled for its own path. With use_graph the
-// launches of two steps (set p, set 1 - p) are captured once in a CUDA graph
-// and replayed.
+// set 1: swapped). A step is, by schedule kernel: 1, one launch of
+// k_step_batch over a work list of (lattice, first tile) items; 2, one launch
+// of the staged kernel over its work list; 3 (the default for FP32 and 16-bit
+// storage), one launch of the two-node kernel per group of lattices of one
+// size and viscosity mode, its descriptors passed in the launch's parameters
+// (grid = tiles x lattices), the groups' launches forked onto side streams and
+// joined back. With use_graph the launches of two steps (set p, set 1 - p)
+// are captured once in a CUDA graph and replayed.
 #include <algorithm>
 #include <climits>
 #include <cstring>

@@ -1,17 +1,23 @@
 // step2.cu -- the time step with two x-adjacent nodes per thread, in packed
-// FP32x2 arithmetic (FP32 and 16-bit storage).
+// FP32x2 arithmetic (FP32 and 16-bit storage), for one lattice (k_step2) and
+// for groups of same-size lattices in one launch (k_step2_class).
 //
 // A CTA of 32 x 8 threads takes a 64 x 8 tile: thread (tx, ty) owns the
-// nodes x0 + 2 tx and x0 + 2 tx + 1 of row y0 + ty. The prologue is that of
-// the one-node kernel on a wider tile (phi tile with a ring of one, or two
-// next to ghosts; ghost values; bounce-back pulls decided per warp), and the
-// per-node arithmetic is node_core (step_core.cuh) on F2 lanes: every
-// operation of the two nodes is one packed instruction (add/sub/mul/fma.rn
-// on .f32x2), each lane rounding exactly as the scalar code, so
-// the results equal the one-node kernel's bit for bit. The two nodes' values
-// leave as one 32-bit (16-bit storage) or 64-bit (FP32) store per plane, and
-// on tiles away from the periodic seam the pulls of the directions without
-// an x component are one aligned load for both nodes.
+// nodes x0 + 2 tx and x0 + 2 tx + 1 of row y0 + ty. The per-node arithmetic
+// is node_core (step_core.cuh) on F2 lanes: every operation of the two nodes
+// is one packed instruction (add/sub/mul/fma.rn on .f32x2), each lane
+// rounding exactly as the scalar code, so the results equal the one-node
+// kernel's bit for bit. The pulled populations are held as raw 16-bit pairs
+// (16-bit storage) and converted where used. The two nodes' values leave as
+// one 32-bit (16-bit storage) or 64-bit (FP32) store per plane.
+//
+// All-fluid tiles: phi on a ring of one, no checks; on tiles away from the
+// periodic seam the pulls of the directions without an x component are one
+// aligned load for both nodes. Tiles with walls: each node's 16-bit word
+// (node byte and the zeta bits of its 8 neighbours, geometry.cu) selects its
+// bounce-back sources and gives a ghost node's neighbour mean, so no class
+// tile is loaded; the tile's flags (k_tile2_flags) say whether phi is needed
+// two nodes out and whether the tile has a zeta = 1 node at all.
 #include "step_core.cuh"
 
 #include <cstring>
@@ -22,20 +28,16 @@ namespace {
 
 constexpr int QX = 64, QY = 8;        // tile (nodes)
 constexpr int QTX = QX / 2;           // threads in x
-constexpr int QCW = QX + 6;           // class tile row (halo 3)
+constexpr int QCW = QX + 6;           // row width of a class tile for the shared pulls (never read here)
 constexpr int QPW = QX + 4;           // phi tile row (halo 2)
 
-// L2 prefetch distance in CTAs of launch order (0: off): a quarter of the
-// 3 x 152 resident CTAs, the same node distance as the one-node kernel's
-// single-lattice kernel, fluid tiles: pull f with g, before the phi-tile
-// barrier (twice the loads in flight per thread, for 9 more registers;
-// measured faster there, slower in the batched kernel, which spills)
+// all-fluid tiles: pull f with g, before the phi-tile barrier (twice the
+// loads in flight per thread, for 9 more registers)
 #ifndef PFLBM_PAIR_EARLY_F
 #define PFLBM_PAIR_EARLY_F 1
 #endif
 
-
-// resident 256-thread CTAs per SM asked of k_step2: 4 with 16-bit storage
+// resident 256-thread CTAs per SM asked of the kernels: 4 with 16-bit storage
 // (64 registers, the pulled populations held as raw pairs), 3 with FP32
 #ifndef PFLBM_STEP2_MINB
 #define PFLBM_STEP2_MINB 4
@@ -43,6 +45,9 @@ constexpr int QPW = QX + 4;           // phi tile row (halo 2)
 #ifndef PFLBM_STEP2_MINB32
 #define PFLBM_STEP2_MINB32 3
 #endif
+
+// L2 prefetch distance in CTAs of launch order (0: off): about a quarter of
+// the 4 x 152 resident CTAs (distances of 76 to 228 measured within 1 %)
 #ifndef PFLBM_L2_AHEAD2
 #define PFLBM_L2_AHEAD2 114
 #endif
