@@ -141,3 +141,41 @@ def test_pair_batch_equals_single(precision):
     b.close()
     for s in members:
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_pair_batch_groups_by_size_and_viscosity(precision):
+    # the two-node batched kernel groups lattices by size and viscosity mode,
+    # one launch per group of at most one launch's descriptor capacity: 300
+    # lattices of one size (more than one launch holds), same-size lattices
+    # with and without variable viscosity and a body force, and a lone size;
+    # every member equals its own single-lattice run with the global-load kernel
+    from paper_2312_00369_gb300 import pflbm, workloads as wl
+    rng = np.random.default_rng(5)
+    specs = [(64, 32, 0, 0.0)] * 300 + [(128, 64, 1, 0.0), (128, 64, 1, 0.3), (128, 64, 2, 0.3), (256, 128, 0, 0.0)]
+    stream = torch.cuda.Stream()
+    members, refs = [], []
+    for i, (nx, ny, wt, nu) in enumerate(specs):
+        c = wl.batch_instance(rng, nx, ny, wt, float(rng.uniform(30.0, 150.0)), 100)
+        extra = dict(nu_l=nu, nu_g=nu / 6.0, gx=1e-6, gy=-2e-6) if nu else {}
+        s = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision=precision, stream=stream, **c.physical(), **extra)
+        for d in c.droplets:
+            s.init_droplet(*d)
+        members.append(s)
+        if i % 50 == 0 or i >= 300:     # check a sample of the large group and every other member
+            r = pflbm.Solver(c.solid, theta_deg=c.theta_deg, precision=precision, step_kernel="global",
+                             **c.physical(), **extra)
+            for d in c.droplets:
+                r.init_droplet(*d)
+            refs.append((i, r))
+    b = pflbm.Batch(members, pflbm.schedule(kernel=3))
+    assert b.kernel == 3 and b.info()["grid"] >= 5     # launches: the large group takes at least two
+    b.step(17)
+    for i, r in refs:
+        r.step(17)
+        for x, y in zip(_state(r), _state(members[i])):
+            assert np.array_equal(x, y), specs[i]
+        r.close()
+    b.close()
+    for s in members:
+        s.close()
