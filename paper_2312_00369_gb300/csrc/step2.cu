@@ -64,12 +64,14 @@ __device__ __forceinline__ F2 pull2(const typename Store<PREC>::S* __restrict__ 
         const int idx = gy * pitch + gx + (I * plane - Y * pitch - X);
         if constexpr (X == 0) {
             // aligned pair: gx is even and every plane and row starts on an
-            // even element
+            // even element (pair indices here and below are non-negative
+            // element indices halved by a shift, which a signed division by
+            // two would have to sign-correct)
             if constexpr (PREC == PFLBM_FP32) {
-                const float2 v = PFLBM_LD(reinterpret_cast<const float2*>(base), idx / 2, 9LL * plane / 2);
+                const float2 v = PFLBM_LD(reinterpret_cast<const float2*>(base), idx >> 1, 9LL * plane / 2);
                 return F2(v.x, v.y);
             } else {
-                const uint32_t u = PFLBM_LD(reinterpret_cast<const uint32_t*>(base), idx / 2, 9LL * plane / 2);
+                const uint32_t u = PFLBM_LD(reinterpret_cast<const uint32_t*>(base), idx >> 1, 9LL * plane / 2);
                 typename T::S lo, hi;
                 const uint16_t l16 = (uint16_t)(u & 0xffffu), h16 = (uint16_t)(u >> 16);
                 memcpy(&lo, &l16, 2);
@@ -100,7 +102,7 @@ __device__ __forceinline__ uint32_t pull2_raw(const typename Store<PREC>::S* __r
     if constexpr (!WRAP) {
         const int idx = gy * pitch + gx + (I * plane - Y * pitch - X);
         if constexpr (X == 0)
-            return PFLBM_LD(reinterpret_cast<const uint32_t*>(base), idx / 2, 9LL * plane / 2);
+            return PFLBM_LD(reinterpret_cast<const uint32_t*>(base), idx >> 1, 9LL * plane / 2);
         else
             return (uint32_t)PFLBM_LD(b, idx, 9LL * plane) | ((uint32_t)PFLBM_LD(b, idx + 1, 9LL * plane) << 16);
     } else {
@@ -140,7 +142,7 @@ __device__ __forceinline__ void pull2_g(Hold2<PREC>& v, int32_t raw[2], const Pl
                                         int pitch, int plane)
 {
     if constexpr (!WRAP) {
-        const int2 r = PFLBM_LD(reinterpret_cast<const int2*>(P.g0), (gy * pitch + gx) / 2, plane / 2);
+        const int2 r = PFLBM_LD(reinterpret_cast<const int2*>(P.g0), (gy * pitch + gx) >> 1, plane / 2);
         raw[0] = r.x;
         raw[1] = r.y;
     } else {
@@ -290,7 +292,7 @@ __device__ __forceinline__ void wall_prologue(const StepArgs<PREC>& a, float (*s
     uint16_t w[2] = {CLS_OUT, CLS_OUT};
     if (gy < ny) {
         if (!WRAP) {
-            const uint32_t wp = PFLBM_LD(reinterpret_cast<const uint32_t*>(a.nword), (gy * pitch + gxa) / 2, a.plane / 2);
+            const uint32_t wp = PFLBM_LD(reinterpret_cast<const uint32_t*>(a.nword), (gy * pitch + gxa) >> 1, a.plane / 2);
             w[0] = (uint16_t)(wp & 0xffffu);
             w[1] = (uint16_t)(wp >> 16);
         } else {
@@ -447,7 +449,7 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, f
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const float2* row = reinterpret_cast<const float2*>(&s_phi[py - 1 + r][0]);
-        const float2 l = row[px / 2 - 1], m = row[px / 2], rr = row[px / 2 + 1];
+        const float2 l = row[(px >> 1) - 1], m = row[px >> 1], rr = row[(px >> 1) + 1];
         Wr[r] = F2(l.y, m.x);
         Cr[r] = F2(m.x, m.y);
         Er[r] = F2(m.y, rr.x);
@@ -472,7 +474,7 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, f
             }
         },
         [&](int k) {
-            const float2 v = PFLBM_LD(reinterpret_cast<const float2*>(a.sprev), k / 2, a.plane / 2);
+            const float2 v = PFLBM_LD(reinterpret_cast<const float2*>(a.sprev), k >> 1, a.plane / 2);
             return F2(v.x, v.y);
         },
         [](F2, F2, F2, F2) {});

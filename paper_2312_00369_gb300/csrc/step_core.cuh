@@ -414,19 +414,19 @@ struct Lane2 {
     __device__ __forceinline__ void store_f(const StepArgs<PREC>& a, C v) const
     {
         if constexpr (PREC == PFLBM_FP32)
-            PFLBM_ST(reinterpret_cast<float2*>(a.out.f), (I * a.plane + k) / 2, 9LL * a.plane / 2, f2v(v));
+            PFLBM_ST(reinterpret_cast<float2*>(a.out.f), (I * a.plane + k) >> 1, 9LL * a.plane / 2, f2v(v));
         else
-            PFLBM_ST(reinterpret_cast<uint32_t*>(a.out.f), (I * a.plane + k) / 2, 9LL * a.plane / 2, pack(v));
+            PFLBM_ST(reinterpret_cast<uint32_t*>(a.out.f), (I * a.plane + k) >> 1, 9LL * a.plane / 2, pack(v));
     }
     template <int I>
     __device__ __forceinline__ C store_g(const StepArgs<PREC>& a, C v) const
     {
         if constexpr (PREC == PFLBM_FP32) {
-            PFLBM_ST(reinterpret_cast<float2*>(a.out.g), (I * a.plane + k) / 2, 9LL * a.plane / 2, f2v(v));
+            PFLBM_ST(reinterpret_cast<float2*>(a.out.g), (I * a.plane + k) >> 1, 9LL * a.plane / 2, f2v(v));
             return C(0);
         } else {
             const uint32_t s = pack(v);
-            PFLBM_ST(reinterpret_cast<uint32_t*>(a.out.g), (I * a.plane + k) / 2, 9LL * a.plane / 2, s);
+            PFLBM_ST(reinterpret_cast<uint32_t*>(a.out.g), (I * a.plane + k) >> 1, 9LL * a.plane / 2, s);
             return v - unpack(s);
         }
     }
@@ -444,11 +444,11 @@ struct Lane2 {
     __device__ __forceinline__ void store_g0(const StepArgs<PREC>& a, C d) const
     {
         const int2 v = make_int2(g0_lane(g0raw[0], d.x, valid[0], a), g0_lane(g0raw[1], d.y, valid[1], a));
-        PFLBM_ST(reinterpret_cast<int2*>(a.out.g0), k / 2, a.plane / 2, v);
+        PFLBM_ST(reinterpret_cast<int2*>(a.out.g0), k >> 1, a.plane / 2, v);
     }
     __device__ __forceinline__ void store_sprev(const StepArgs<PREC>& a, C s) const
     {
-        PFLBM_ST(reinterpret_cast<float2*>(a.sprev), k / 2, a.plane / 2, f2v(s));
+        PFLBM_ST(reinterpret_cast<float2*>(a.sprev), k >> 1, a.plane / 2, f2v(s));
     }
 };
 
