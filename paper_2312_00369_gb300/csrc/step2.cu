@@ -537,7 +537,8 @@ __global__ void __launch_bounds__(QTX * QY, PREC == PFLBM_FP32 ? PFLBM_STEP2_MIN
     __shared__ uint16_t s_gw[QGP];
     if (PFLBM_L2_AHEAD2 > 0) prefetch2_l2<PREC>(a, blockIdx.x, blockIdx.y);
     const int x0 = blockIdx.x * QX;
-    // every x the tile touches (class tile: three out) inside the lattice
+    // every x the tile touches inside the lattice (the pulls of the second
+    // phi ring reach three nodes out)
     if (x0 >= 3 && x0 + QX + 3 <= a.nx)
         tile2<PREC, VV, false, PFLBM_PAIR_EARLY_F != 0>(a, blockIdx.x, blockIdx.y, s_phi, s_gw);
     else
