@@ -345,7 +345,7 @@ class Solver:
 
     def set_step_kernel(self, step_kernel, step_chunk=0):
         """Switch the step kernel ("default", "global", "staged32x8",
-        "staged64x4" or 0..3); results are the same bit for bit."""
+        "staged64x4", "pair" or 0..4); results are the same bit for bit."""
         k = STEP_KERNELS.get(step_kernel, step_kernel) if isinstance(step_kernel, str) else int(step_kernel)
         _check(lib().pflbm_set_step_kernel(self._h, int(k), int(step_chunk)))
 
