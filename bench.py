@@ -671,6 +671,7 @@ def extra_block(args, torch, world, local, case, stream):
                    device=local, stream=stream, **case.physical())
         for d in case.droplets:
             s.init_droplet(*d)
+        kernel16 = s.step_kernel
         s.step(20)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -689,12 +690,13 @@ def extra_block(args, torch, world, local, case, stream):
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
-            t = json.load(open(tfile)).get("many_flat:bf16")
+            t = json.load(open(tfile)).get(f"many_flat:bf16:{kernel16}")
             if t and t.get("step_source_sha256") == step_source_sha256():
                 traffic = t["bytes_per_launch"]
         except Exception:
             traffic = None
     out["bf16_many_flat"] = {"value": N / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": k,
+                             "step_kernel": kernel16,
                              "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                           "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                                           "bytes_per_lu": BYTES_PER_LU["bf16"]}}
@@ -824,10 +826,10 @@ def main():
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
-        # DRAM bytes per launch from one ncu capture; null once the step
-        # kernel's source differs from the one that was captured
+        # DRAM bytes per launch from one ncu capture of the step kernel this
+        # run used; null once the step sources differ from the captured ones
         try:
-            t = json.load(open(tfile)).get(f"{args.workload}:{args.precision}")
+            t = json.load(open(tfile)).get(f"{args.workload}:{args.precision}:{step_kernel_used}")
             if t and t.get("step_source_sha256") == step_source_sha256():
                 traffic = t["bytes_per_launch"]
         except Exception:

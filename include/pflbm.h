@@ -97,7 +97,9 @@ typedef struct {
      * term 0 times (case 1) or twice (case 3). */
     int chi_case;
     /* Step kernel (results are identical bit for bit; only the speed
-     * differs). 0: the library's default (4 for 16-bit storage, else 1);
+     * differs). 0: the library's default, by the measured crossover: 4 for
+     * 16-bit storage on lattices of at least 2^19 nodes and for FP32 on
+     * lattices of at least 2^21 nodes, else 1;
      * 1: populations pulled from global memory, 32 x 8 tiles; 2:
      * populations staged in shared memory by TMA, 32 x 8 tiles; 3: staged,
      * 64 x 4 tiles; 4: global loads, two x-adjacent nodes per thread in

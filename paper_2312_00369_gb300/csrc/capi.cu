@@ -202,16 +202,27 @@ int ensure_out(pflbm_t* h)
     return PFLBM_OK;
 }
 
-// Step kernel of a handle (pflbm_params_t.step_kernel): 0 picks the default,
-// the global-load kernel, which measured fastest for every precision on the
-// single-lattice workloads (the staged kernel issues about 6 % more
-// instructions per node and runs at 4 instead of 6 resident CTAs per SM).
+// Step kernel of a handle (pflbm_params_t.step_kernel). 0 picks the default
+// by storage and lattice size, from the measured crossover on lattices of 5k
+// to 8.4M nodes (warm, MLUPS):
+// - 16-bit storage: the two-node kernel from 2^19 nodes (6 to 24 % faster
+//   there; 5 to 25 % slower at 2^18 nodes and below);
+// - FP32: the two-node kernel from 2^21 nodes (0.1 to 1.4 % faster there;
+//   0.5 to 25 % slower at 2^20 nodes and below);
+// - otherwise, and for FP64, the one-node global-load kernel: its 32 x 8
+//   tiles give a small lattice twice the CTAs, and each CTA does half the
+//   work. The staged kernel was slower on every workload (about 6 % more
+//   instructions per node, 4 instead of 6 resident CTAs per SM).
+constexpr long long kPairMinNodes16 = 1LL << 19, kPairMinNodes32 = 1LL << 21;
+
 int select_step_kernel(pflbm_t* h, int kernel, int chunk)
 {
     if (kernel < 0 || kernel > 4) return fail(PFLBM_EINVAL, "step_kernel must be 0, 1, 2, 3 or 4");
-    // default: the two-node kernel for 16-bit storage (the fastest there),
-    // the one-node global-load kernel for FP32 and FP64
-    if (kernel == 0) kernel = (h->precision == PFLBM_BF16 || h->precision == PFLBM_FP16) ? 4 : 1;
+    if (kernel == 0) {
+        const long long nodes = (long long)h->nx * h->ny;
+        const bool b16 = h->precision == PFLBM_BF16 || h->precision == PFLBM_FP16;
+        kernel = (b16 && nodes >= kPairMinNodes16) || (h->precision == PFLBM_FP32 && nodes >= kPairMinNodes32) ? 4 : 1;
+    }
     if (kernel == 4) {
         if (h->precision == PFLBM_FP64) return fail(PFLBM_EINVAL, "the two-node step kernel needs FP32 or 16-bit storage");
         h->step_shape = -2;

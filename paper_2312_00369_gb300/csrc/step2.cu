@@ -173,12 +173,17 @@ __device__ __forceinline__ F2 phi2(const Hold2<PREC>& v, const int32_t raw[2])
     return F2(T::g0(raw[0]), T::g0(raw[1])) + s;
 }
 
-// The one-node ring around an all-fluid 64 x 8 tile: phi of one node each.
+// The one-node ring around an all-fluid 64 x 8 tile: phi of one node each,
+// for the first 148 threads. Called after the pair's own pulls are issued
+// and before their phi is summed, so that the ring's loads are in flight
+// together with the pair's (measured 0.7 to 1.4 % faster than after).
 template <int PREC, bool WRAP>
 __device__ __forceinline__ void ring2f(const StepArgs<PREC>& a, float (*s_phi)[QPW], int x0, int y0, int tid, bool tiny)
 {
     constexpr int RW = QX + 2, NR = 2 * RW + 2 * QY;
-    for (int t = tid; t < NR; t += QTX * QY) {
+    static_assert(NR <= QTX * QY, "one ring node per thread at most");
+    if (tid < NR) {
+        const int t = tid;
         int py, px;
         if (t < RW) { py = 1; px = 1 + t; }
         else if (t < 2 * RW) { py = QY + 2; px = 1 + t - RW; }
@@ -417,10 +422,10 @@ __device__ __forceinline__ void tile2(const StepArgs<PREC>& a, int bx, int by, f
         // ---- prologue of an all-fluid tile: no node words, no checks ----
         pull2_g<PREC, WRAP>(g, raw, a.in, gxa, gy, nx, pitch, a.plane);
         if (EARLY_F) pull2_f<PREC, WRAP>(fearly, a.in.f, gxa, gy, nx, pitch, a.plane);
+        ring2f<PREC, WRAP>(a, s_phi, x0, y0, tid, tiny);
         const F2 ph = phi2<PREC>(g, raw);
         s_phi[ty + 2][2 * tx + 2] = ph.x;
         s_phi[ty + 2][2 * tx + 3] = ph.y;
-        ring2f<PREC, WRAP>(a, s_phi, x0, y0, tid, tiny);
         __syncthreads();
     } else {
         // ---- tile with walls: each node's word gives its class and its

@@ -58,10 +58,10 @@ def ref(name):
     return _futures[name].get(timeout=1800)
 
 
-def solver(case, precision, init=True):
+def solver(case, precision, init=True, step_kernel="default"):
     from paper_2312_00369_gb300.pflbm import Solver
     s = Solver(case.solid, theta_deg=case.theta_deg, theta_field=case.theta_field,
-               precision=precision, **case.physical(), **oj.solver_options(case))
+               precision=precision, step_kernel=step_kernel, **case.physical(), **oj.solver_options(case))
     if init:
         for d in case.droplets:
             s.init_droplet(*d)
@@ -142,12 +142,15 @@ def test_parity_cases(name, precision):
     compare(name, precision)
 
 
-def test_full_size_many_droplets_sampled_columns():
+@pytest.mark.parametrize("kernel", ["default", "global"])
+def test_full_size_many_droplets_sampled_columns(kernel):
     # 4096 x 2048, 64 droplets, per-node theta, FP32, the benchmark's launch
-    # configuration: columns compared with oracle windows of the same input
+    # configuration (the default picks the two-node kernel at this size) and
+    # the one-node kernel: columns compared with oracle windows of the same input
     from paper_2312_00369_gb300 import workloads as wl
     case = wl.many_droplets_flat(**FULL)
-    s = solver(case, "fp32")
+    s = solver(case, "fp32", step_kernel=kernel)
+    assert s.step_kernel == ("pair" if kernel == "default" else kernel)
     s.step(WIN_STEPS)
     phi, u, p = s.get()
     for x in WIN_X:
@@ -217,15 +220,15 @@ def test_edge_cases_2d():
     e.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_largest_accepted_lattice(precision):
+@pytest.mark.parametrize("precision,kernel", [("fp32", "global"), ("fp32", "pair"), ("bf16", "pair")])
+def test_largest_accepted_lattice(precision, kernel):
     # 16384 x 7280 (18 * ny * pitch just below 2^31): the highest population
-    # indices (FP32: the one-node kernel; BF16: the two-node kernel's pair
-    # indices). A droplet hangs from the top wall at the far corner; its
+    # indices, in the one-node kernel and in the two-node kernel's halved
+    # pair indices. A droplet hangs from the top wall at the far corner; its
     # column is compared with an oracle window of the same input.
     case = oj.max2d_case()
-    s = solver(case, precision)
-    assert s.step_kernel == ("pair" if precision == "bf16" else "global")
+    s = solver(case, precision, step_kernel=kernel)
+    assert s.step_kernel == kernel
     s.step(case.steps)
     s.check()
     ny, nx = case.solid.shape

@@ -179,3 +179,21 @@ def test_pair_batch_groups_by_size_and_viscosity(precision):
     b.close()
     for s in members:
         s.close()
+
+
+@pytest.mark.parametrize("precision,nx,ny,want", [
+    ("fp32", 1024, 1023, "global"), ("fp32", 2048, 1024, "pair"),
+    ("bf16", 1024, 511, "global"), ("bf16", 1024, 512, "pair"),
+    ("fp16", 512, 512, "global"), ("fp16", 2048, 256, "pair"),
+    ("fp64", 4096, 1024, "global")])
+def test_default_kernel_by_lattice_size(precision, nx, ny, want):
+    # the default step kernel: the two-node kernel from 2^19 nodes (16-bit
+    # storage) and 2^21 nodes (FP32), else the one-node kernel
+    from paper_2312_00369_gb300 import workloads as wl
+    from paper_2312_00369_gb300.pflbm import Solver
+    solid, _ = wl.flat_channel(nx, ny)
+    s = Solver(solid, theta_deg=60.0, precision=precision)
+    assert s.step_kernel == want
+    s.set_step_kernel("default")
+    assert s.step_kernel == want
+    s.close()
