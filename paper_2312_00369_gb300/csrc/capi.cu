@@ -205,10 +205,10 @@ int ensure_out(pflbm_t* h)
 // Step kernel of a handle (pflbm_params_t.step_kernel). 0 picks the default
 // by storage and lattice size, from the measured crossover on lattices of 5k
 // to 8.4M nodes (warm, MLUPS):
-// - 16-bit storage: the two-node kernel from 2^19 nodes (6 to 24 % faster
+// - 16-bit storage: the two-node kernel from 2^19 nodes (6 to 32 % faster
 //   there; 5 to 25 % slower at 2^18 nodes and below);
-// - FP32: the two-node kernel from 2^21 nodes (0.1 to 1.4 % faster there;
-//   0.5 to 25 % slower at 2^20 nodes and below);
+// - FP32: the two-node kernel from 2^21 nodes (2 to 4 % faster there; within
+//   0.5 % at 2^20 nodes, 0.2 to 25 % slower at 2^19 nodes and below);
 // - otherwise, and for FP64, the one-node global-load kernel: its 32 x 8
 //   tiles give a small lattice twice the CTAs, and each CTA does half the
 //   work. The staged kernel was slower on every workload (about 6 % more
@@ -414,7 +414,17 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
     CKR(launch_classify(h));
     CKR(launch_tile_flags(h));
     CKR(launch_wet(h));
-    // tensor maps of the staged step (FP32 and 16-bit storage)
+    // node words and 64 x 8 tile flags of the two-node step (before the
+    // tensor maps, which address the node words)
+    if (h->precision != PFLBM_FP64) {
+        if ((rc = dalloc(h, &p, node_words_bytes(nx, ny)))) { release(h); return rc; }
+        h->nword = (uint16_t*)p;
+        if ((rc = dalloc(h, &p, tile2_flags_bytes(nx, ny)))) { release(h); return rc; }
+        h->tiles2 = (uint8_t*)p;
+        CKR(launch_node_words(h));
+    }
+    // tensor maps of the staged step and of the two-node step's prefetch
+    // (FP32 and 16-bit storage)
     std::vector<unsigned char> maps;
     if (h->precision != PFLBM_FP64) {
         maps.resize(tma_sets_bytes() + 64);
@@ -427,12 +437,6 @@ int pflbm_create_ex(pflbm_t** out, const pflbm_params_t* prm)
             h->sflags = (uint8_t*)p;
             CKR(launch_staged_flags(h));
         }
-        // node words and 64 x 8 tile flags of the two-node step
-        if ((rc = dalloc(h, &p, node_words_bytes(nx, ny)))) { release(h); return rc; }
-        h->nword = (uint16_t*)p;
-        if ((rc = dalloc(h, &p, tile2_flags_bytes(nx, ny)))) { release(h); return rc; }
-        h->tiles2 = (uint8_t*)p;
-        CKR(launch_node_words(h));
     }
     CKR(cudaStreamSynchronize(h->stream));
 #undef CKR

@@ -222,7 +222,7 @@ int batch_max_ctas_per_sm(int precision);
 // step_tma.cu: the staged step (TMA ring, tile shapes 0: 32 x 8, 1: 64 x 4)
 constexpr int kStagedShapes = 2;
 struct TmaSet;
-size_t tma_sets_bytes();                                    // kStagedShapes x 2 copies
+size_t tma_sets_bytes();   // kStagedShapes x 2 copies of TmaSet, then 2 copies of PfMaps
 bool encode_tma_sets(const pflbm_t* h, TmaSet* host);      // false: staged step unavailable
 cudaError_t launch_step_staged(pflbm_t* h, int shape, int blocks_per_item, int ctas_per_sm);
 cudaError_t launch_step_staged_batch(int precision, const void* d_args, const int4* d_work, int n_work, int grid,

@@ -54,6 +54,18 @@ struct alignas(64) TmaSet {
     unsigned char cls[128];   // node bytes [ny][nx], box [WC][TYT + 6]
 };
 
+// Tensor maps of one population copy for the two-node step's L2 prefetch of
+// a later 64 x 8 tile: one box prefetch each. They follow the staged step's
+// sets in the same device array (kPfMapsAt TmaSet entries in).
+struct alignas(64) PfMaps {
+    unsigned char pop[128];   // planes of [18][ny][nx]: box [64][8][9] (f from plane 0; FP32 g from plane 9)
+    unsigned char g16[128];   // 16-bit formats: box [64][8][8], g_1..g_8 from plane 10
+    unsigned char g0[128];    // 16-bit formats: the int32 g_0 plane [ny][nx], box [64][8]
+    unsigned char hist[128];  // the u.grad(phi) history [ny][nx], box [64][8]
+    unsigned char nword[128]; // the two-node step's node words [ny][nx], box [64][8]
+};
+constexpr int kPfMapsAt = 4;
+
 __device__ __forceinline__ int wrap1(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
 __device__ __forceinline__ int wrapn(int x, int nx) { int r = x % nx; return r < 0 ? r + nx : r; }
 

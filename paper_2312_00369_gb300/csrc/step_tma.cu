@@ -634,12 +634,50 @@ bool encode_set(const pflbm_t* h, int copy, TmaSet* out)
 }
 
 template <int PREC>
+bool encode_pf(const pflbm_t* h, int copy, PfMaps* out)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    constexpr bool F32 = PREC == PFLBM_FP32;
+    constexpr cuuint64_t ES = F32 ? 4 : 2;
+    const CUtensorMapDataType dt = F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t nx = (cuuint64_t)h->nx, ny = (cuuint64_t)h->ny, pitch = (cuuint64_t)h->pitch;
+    const cuuint64_t plane = ny * pitch;
+    const cuuint32_t one[3] = {1, 1, 1};
+    auto map = [&](void* m, CUtensorMapDataType t, cuuint32_t rank, void* base, const cuuint64_t* dims,
+                   const cuuint64_t* strides, const cuuint32_t* box) {
+        return enc((CUtensorMap*)m, t, rank, base, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    std::memset(out, 0, sizeof(*out));
+    const cuuint64_t d3[3] = {nx, ny, 18}, s3[2] = {pitch * ES, plane * ES};
+    const cuuint32_t b9[3] = {64, 8, 9}, b8[3] = {64, 8, 8}, b2[2] = {64, 8};
+    const cuuint64_t d2[2] = {nx, ny};
+    if (!map(out->pop, dt, 3, h->pop[copy], d3, s3, b9)) return false;
+    if (!F32) {
+        if (!map(out->g16, dt, 3, h->pop[copy], d3, s3, b8)) return false;
+        const cuuint64_t s4[1] = {pitch * 4};
+        if (!map(out->g0, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, (char*)h->pop[copy] + 18 * plane * ES, d2, s4, b2))
+            return false;
+    }
+    const cuuint64_t sh[1] = {pitch * 4}, sw[1] = {pitch * 2};
+    if (!map(out->hist, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->sprev, d2, sh, b2)) return false;
+    if (!map(out->nword, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->nword, d2, sw, b2)) return false;
+    return true;
+}
+
+template <int PREC>
 bool encode_all(const pflbm_t* h, TmaSet* host)
 {
     for (int c = 0; c < 2; ++c) {
         if (!encode_set<PREC, 32, 8>(h, c, host + 0 * 2 + c)) return false;
         if (!encode_set<PREC, 64, 4>(h, c, host + 1 * 2 + c)) return false;
     }
+    static_assert(kPfMapsAt == kStagedShapes * 2, "prefetch maps follow the staged sets");
+    PfMaps* pf = reinterpret_cast<PfMaps*>(host + kPfMapsAt);
+    for (int c = 0; c < 2; ++c)
+        if (!encode_pf<PREC>(h, c, pf + c)) return false;
     return true;
 }
 
@@ -734,7 +772,7 @@ int batch_per_sm()
 
 }  // namespace
 
-size_t tma_sets_bytes() { return (size_t)kStagedShapes * 2 * sizeof(TmaSet); }
+size_t tma_sets_bytes() { return (size_t)kStagedShapes * 2 * sizeof(TmaSet) + 2 * sizeof(PfMaps); }
 
 bool encode_tma_sets(const pflbm_t* h, TmaSet* host)
 {
