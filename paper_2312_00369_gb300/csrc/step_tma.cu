@@ -26,6 +26,10 @@
 // Waits on an mbarrier give up after about 2^31 clock cycles: the kernel then
 // sets bit 4 of the status word (reported as PFLBM_ETIMEOUT), waits once more
 // (bounded) for the copies it issued and returns.
+//
+// The host side here also encodes, after the staged step's tensor maps, the
+// two-node step's prefetch maps (PfMaps, step_core.cuh): boxes of 64 x 8
+// nodes that its CTAs prefetch into L2 with cp.async.bulk.prefetch.tensor.
 #include <cuda.h>
 
 #include <cstring>
