@@ -244,8 +244,9 @@ int pflbm_load(pflbm_t* h, const void* buf, size_t len);
 
 /* ---- many lattices per launch ------------------------------------------
  * A batch advances several handles (of any sizes) together: each time step
- * is one persistent launch over a work list of (lattice, tile) items, and
- * pairs of steps can be replayed from a captured CUDA graph. The per-node
+ * is one persistent launch over a work list of (lattice, tile) items (or,
+ * with kernel 3, one launch per group of same-size lattices), and runs of 8
+ * steps can be replayed from a captured CUDA graph. The per-node
  * update is exactly that of pflbm_step; the paper has no batching. All
  * handles of a batch must share precision, device and stream; the batch runs
  * on that stream and keeps no copy of the handles' state. */
@@ -256,7 +257,7 @@ typedef struct {
                             no size class below covers)                       */
     int order;           /* 0: lattice by lattice; 1: largest lattices first,
                             items interleaved across lattices                 */
-    int use_graph;       /* replay step pairs from a captured CUDA graph      */
+    int use_graph;       /* replay runs of 8 steps from a captured CUDA graph */
     int kernel;          /* 0: default (3); 1: global-load kernel, 32 x 8
                             tiles; 2: staged kernel (TMA ring) with the
                             size classes below; 3: two-node kernel (two
