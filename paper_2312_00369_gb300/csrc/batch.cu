@@ -302,7 +302,9 @@ int check_members(pflbm_t* const* hs, int count, int precision, int device, cuda
 
 // Steps per captured graph (even). One graph replay runs each size group's
 // steps back to back: measured on 256 small lattices (BF16, MLUPS) 46.8k with
-// a join after every step, 47.6k at 2 steps per graph, 48.3k at 8, 47.9k at 32.
+// a join after every step, 47.6k at 2 steps per graph, 48.3k at 8, 47.9k at 32
+// (300 steps), and over 400 steps 48.55k at 8 against 48.7k at 16. 8 divides
+// the 200-step ticks of the server.
 #ifndef PFLBM_BATCH_GRAPH_STEPS
 #define PFLBM_BATCH_GRAPH_STEPS 8
 #endif
