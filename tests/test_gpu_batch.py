@@ -79,6 +79,31 @@ def test_batch_equals_alone_bitwise(precision, sched):
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_graph_replays_from_odd_phase(precision):
+    # the captured graph holds 8 steps per replay, each size group's steps
+    # back to back on its own stream: 3 steps (phase 1), then 21 (one single
+    # step back to phase 0, two replays, 4 single steps), then 16 (two
+    # replays), against each lattice stepped alone
+    from paper_2312_00369_gb300.pflbm import Batch
+    cases = mix(seed=11, n=10)
+    stream = torch.cuda.Stream()
+    alone = make(cases, precision, stream)
+    for s in alone:
+        s.step(40)
+    together = make(cases, precision, stream)
+    b = Batch(together)
+    assert b.kernel == 3
+    for n in (3, 21, 16):
+        b.step(n)
+    for a, t in zip(alone, together):
+        assert t.steps == 40
+        pa, ua, qa = a.get()
+        pt, ut, qt = t.get()
+        assert np.array_equal(pa, pt) and np.array_equal(ua, ut) and np.array_equal(qa, qt)
+    b.close()
+
+
 def test_batch_phase_membership_and_individual_steps():
     from paper_2312_00369_gb300.pflbm import Batch
     cases = mix(seed=9, n=5)
